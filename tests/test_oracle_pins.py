@@ -1,0 +1,321 @@
+"""Pins of the FP64 oracle against mathematics it does not itself implement: the SE(2)
+group law as 3x3 matrices, the matrix exponential, closed forms, symmetries, library
+convolutions and brute-force dense Sinkhorn.  CPU only."""
+import math
+
+import numpy as np
+import pytest
+import scipy.ndimage
+
+import oracle
+from tests import refmath
+
+W = (1.0, 3.0, 0.5)
+RNG = np.random.default_rng(1234)
+
+
+# ---------------------------------------------------------------- group law (Sec. 2.3)
+def test_group_law_matches_matrices():
+    for _ in range(200):
+        a = np.array([RNG.uniform(-2, 2), RNG.uniform(-2, 2), RNG.uniform(-math.pi, math.pi)])
+        b = np.array([RNG.uniform(-2, 2), RNG.uniform(-2, 2), RNG.uniform(-math.pi, math.pi)])
+        ab = oracle.group_mul(a, b)
+        ref = refmath.coords(refmath.mat(a) @ refmath.mat(b))
+        np.testing.assert_allclose(ab[:2], ref[:2], atol=1e-13)
+        dth = (ab[2] - ref[2] + math.pi) % (2 * math.pi) - math.pi
+        assert abs(dth) < 1e-13
+        ai = oracle.group_inv(a)
+        ref = refmath.coords(np.linalg.inv(refmath.mat(a)))
+        np.testing.assert_allclose(ai[:2], ref[:2], atol=1e-13)
+        assert -math.pi <= ai[2] < math.pi
+
+
+def test_group_associativity_and_identity():
+    for _ in range(50):
+        a, b, c = (np.array([RNG.uniform(-1, 1), RNG.uniform(-1, 1), RNG.uniform(-3, 3)])
+                   for _ in range(3))
+        l = oracle.group_mul(oracle.group_mul(a, b), c)
+        r = oracle.group_mul(a, oracle.group_mul(b, c))
+        np.testing.assert_allclose(l[:2], r[:2], atol=1e-13)
+        e = oracle.group_mul(a, oracle.group_inv(a))
+        np.testing.assert_allclose(e, 0.0, atol=1e-13)
+
+
+# ------------------------------------------------------------- rho_b (Sec. 4.3, Eq. rho_b)
+def test_rho_b_half_angle_coordinates_from_matrix_exponential():
+    """For g = exp(c1 A1 + c2 A2 + c3 A3), |c3| < pi, the half-angle coordinates are
+    (c1, c2, c3) scaled by sin(c3/2)/(c3/2) in the spatial part: rotating the translation of
+    g back by half its angle undoes the exponential's chord factor."""
+    for _ in range(300):
+        c1, c2 = RNG.uniform(-0.5, 0.5, size=2)
+        c3 = RNG.uniform(-3.1, 3.1)
+        w = RNG.uniform(0.3, 4.0, size=3)
+        g = refmath.coords(refmath.expm_algebra(c1, c2, c3))
+        s = math.sin(c3 / 2) / (c3 / 2)
+        want = (w[0] * s * c1) ** 2 + (w[1] * s * c2) ** 2 + (w[2] * c3) ** 2
+        got = oracle.rho_b2(g[0], g[1], g[2], w)
+        assert abs(got - want) <= 1e-12 * max(1.0, want)
+
+
+def test_rho_b_special_values():
+    for _ in range(100):
+        th = RNG.uniform(-math.pi, math.pi)
+        x, y = RNG.uniform(-1, 1, size=2)
+        assert abs(oracle.rho_b2(0, 0, th, W) - (W[2] * th) ** 2) < 1e-14
+        assert abs(oracle.rho_b2(x, y, 0, W) - (W[0] ** 2 * x * x + W[1] ** 2 * y * y)) < 1e-14
+        iso = (2.0, 2.0, 0.7)
+        want = iso[0] ** 2 * (x * x + y * y) + (iso[2] * th) ** 2
+        assert abs(oracle.rho_b2(x, y, th, iso) - want) < 1e-13
+    assert oracle.rho_b2(0, 0, 0, W) == 0.0
+
+
+def test_rho_b_symmetries():
+    for _ in range(200):
+        g = np.array([RNG.uniform(-1, 1), RNG.uniform(-1, 1), RNG.uniform(-math.pi, math.pi)])
+        w = RNG.uniform(0.3, 4.0, size=3)
+        base = oracle.rho_b2(*g, w)
+        gi = oracle.group_inv(g)
+        assert abs(oracle.rho_b2(*gi, w) - base) < 1e-12 * max(1, base)
+        assert abs(oracle.rho_b2(g[0], -g[1], -g[2], w) - base) < 1e-12 * max(1, base)
+        assert abs(oracle.rho_b2(-g[0], g[1], -g[2], w) - base) < 1e-12 * max(1, base)
+
+
+def test_rho_b_continuous_across_pi():
+    for _ in range(50):
+        x, y = RNG.uniform(-1, 1, size=2)
+        a = oracle.rho_b2(x, y, math.pi - 1e-9, W)
+        b = oracle.rho_b2(x, y, -math.pi, W)
+        assert abs(a - b) < 1e-7
+
+
+# ------------------------------------------------------- kernel and convolution (Sec. 4.2)
+def _rho2(x, y, t):
+    return oracle.rho_b2(x, y, t, W)
+
+
+@pytest.mark.parametrize("nx,ny,nth,r,eps,periodic", [
+    (5, 5, 4, 2, 0.05, False),
+    (6, 6, 8, 2, 0.05, False),
+    (7, 5, 4, 2, 0.08, False),
+    (6, 6, 4, 2, 0.05, True),
+    (5, 7, 1, 2, 0.02, False),
+])
+def test_conv_equals_dense_group_kernel(nx, ny, nth, r, eps, periodic):
+    g = oracle.Grid(nx, ny, nth, r, W, eps, periodic)
+    LK = refmath.dense_log_kernel(nx, ny, nth, r, _rho2, eps, periodic)
+    K = np.exp(LK)
+    f = RNG.uniform(0.1, 1.0, size=g.shape)
+    want = (K @ f.reshape(-1)).reshape(g.shape)
+    got = oracle.conv_lin(g, f)
+    np.testing.assert_allclose(got, want, rtol=1e-13, atol=0)
+    # symmetric kernel (K_gh = K_hg because rho_b(u^-1) = rho_b(u))
+    np.testing.assert_allclose(K, K.T, rtol=1e-12, atol=0)
+
+
+def test_taps_identity_and_symmetry():
+    g = oracle.Grid(16, 16, 8, 3, W, 1e-3)
+    lk = oracle.taps(g)
+    r = g.r
+    for o in range(8):
+        assert lk[o, o, r, r] == 0.0
+    # F[o][i](d) = F[i][o](-d)  <=>  k(u^-1) = k(u)
+    np.testing.assert_allclose(lk, np.flip(np.transpose(lk, (1, 0, 2, 3)), axis=(2, 3)),
+                               rtol=1e-12)
+
+
+@pytest.mark.parametrize("periodic", [False, True])
+def test_single_orientation_is_separable_gaussian(periodic):
+    """nth = 1: the kernel is exp(-(w1^2 dx^2 + w2^2 dy^2)/eps), a product of two 1-D
+    Gaussians; compare with two 1-D library correlations."""
+    nx, ny, r, eps = 23, 17, 4, 3e-3
+    g = oracle.Grid(nx, ny, 1, r, W, eps, periodic)
+    f = RNG.uniform(0.0, 1.0, size=g.shape)
+    kx = np.exp(-(W[0] * np.arange(-r, r + 1) / nx) ** 2 / eps)
+    ky = np.exp(-(W[1] * np.arange(-r, r + 1) / ny) ** 2 / eps)
+    mode = "wrap" if periodic else "constant"
+    want = scipy.ndimage.correlate1d(f[:, :, 0], kx, axis=1, mode=mode, cval=0.0)
+    want = scipy.ndimage.correlate1d(want, ky, axis=0, mode=mode, cval=0.0)
+    np.testing.assert_allclose(oracle.conv_lin(g, f)[:, :, 0], want, rtol=1e-13)
+
+
+def test_conv_commutes_with_rotation_and_mirror():
+    g = oracle.Grid(12, 12, 8, 3, W, 4e-3)
+    f = RNG.uniform(0.0, 1.0, size=g.shape)
+    Kf = oracle.conv_lin(g, f)
+    np.testing.assert_allclose(oracle.conv_lin(g, refmath.rot90(f)), refmath.rot90(Kf),
+                               rtol=1e-12)
+    np.testing.assert_allclose(oracle.conv_lin(g, refmath.mirror_y(f)), refmath.mirror_y(Kf),
+                               rtol=1e-12)
+
+
+def test_log_conv_matches_linear_and_is_shift_covariant():
+    g = oracle.Grid(10, 9, 8, 3, W, 5e-3)
+    f = RNG.uniform(0.05, 1.0, size=g.shape)
+    np.testing.assert_allclose(np.exp(oracle.conv_log(g, np.log(f))), oracle.conv_lin(g, f),
+                               rtol=1e-13)
+    lf = np.log(f) + 900.0           # exp() of this overflows; the log conv does not care
+    np.testing.assert_allclose(oracle.conv_log(g, lf) - 900.0, oracle.conv_log(g, np.log(f)),
+                               atol=1e-11)
+    # a zero density (log = -inf) is a missing term, not a NaN
+    lf = np.log(f)
+    lf[3, 4, :] = -np.inf
+    f0 = f.copy()
+    f0[3, 4, :] = 0.0
+    np.testing.assert_allclose(np.exp(oracle.conv_log(g, lf)), oracle.conv_lin(g, f0), rtol=1e-13)
+
+
+# -------------------------------------------------------- barycenter (Appendix A)
+def _dense_K(g):
+    return np.exp(refmath.dense_log_kernel(g.nx, g.ny, g.nth, g.r,
+                                           lambda x, y, t: oracle.rho_b2(x, y, t, (g.w1, g.w2, g.w3)),
+                                           g.eps, g.periodic))
+
+
+def _inputs(g, n, seed):
+    rng = np.random.default_rng(seed)
+    mu = rng.uniform(0.05, 1.0, size=(n,) + g.shape)
+    return mu / mu.sum(axis=(1, 2, 3), keepdims=True)
+
+
+@pytest.mark.parametrize("iters", [1, 3, 17])
+def test_one_hot_weights_closed_form(iters):
+    """lambda = (1, 0, ...): v_1 stays 1, so mu = K (mu_1 / K 1) at every iteration."""
+    g = oracle.Grid(6, 6, 4, 2, W, 0.05)
+    K = _dense_K(g)
+    mu = _inputs(g, 3, 7)
+    want = K @ (mu[0].reshape(-1) / (K @ np.ones(g.V)))
+    for fn in (oracle.barycenter_lin, oracle.barycenter_log):
+        got = fn(g, mu, [1.0, 0.0, 0.0], iters)
+        np.testing.assert_allclose(got.reshape(-1), want, rtol=1e-12)
+
+
+def test_identical_inputs_closed_form():
+    g = oracle.Grid(6, 5, 4, 2, W, 0.05)
+    K = _dense_K(g)
+    nu = _inputs(g, 1, 3)[0]
+    want = K @ (nu.reshape(-1) / (K @ np.ones(g.V)))
+    got = oracle.barycenter_log(g, np.stack([nu] * 3), [0.2, 0.3, 0.5], 9)
+    np.testing.assert_allclose(got.reshape(-1), want, rtol=1e-12)
+
+
+def test_homogeneity_and_invariants():
+    g = oracle.Grid(8, 8, 4, 2, W, 0.02)
+    mu = _inputs(g, 3, 11)
+    lam = [0.5, 0.3, 0.2]
+    b, st = oracle.barycenter_log(g, mu, lam, 12, want_state=True)
+    b3 = oracle.barycenter_log(g, 3.7 * mu, lam, 12)
+    np.testing.assert_allclose(b3, 3.7 * b, rtol=1e-11)
+    # sum_g d_i = sum_g mu_i = 1 (K symmetric), every iteration
+    for i in range(3):
+        assert abs(np.exp(st["ld"][i]).sum() - 1.0) < 1e-12
+    # weighted AM-GM: mass(mu) <= 1
+    assert b.sum() <= 1.0 + 1e-12
+    # dual optimality: sum_i lambda_i log v_i stays 0 under the v-update
+    np.testing.assert_allclose(sum(l * st["lv"][i] for i, l in enumerate(lam)), 0.0, atol=1e-11)
+    # after the v-update, v_i (K w_i) = mu with the w_i of the same iteration
+    K = _dense_K(g)
+    for i in range(3):
+        vKw = np.exp(st["lv"][i]).reshape(-1) * (K @ np.exp(st["lw"][i]).reshape(-1))
+        np.testing.assert_allclose(vKw, b.reshape(-1), rtol=1e-11)
+
+
+def test_barycenter_equivariance():
+    g = oracle.Grid(12, 12, 8, 3, W, 6e-3)
+    mu = _inputs(g, 3, 5)
+    lam = [0.2, 0.5, 0.3]
+    b = oracle.barycenter_log(g, mu, lam, 15)
+    np.testing.assert_allclose(oracle.barycenter_log(g, refmath.rot90(mu), lam, 15),
+                               refmath.rot90(b), rtol=1e-11)
+    np.testing.assert_allclose(oracle.barycenter_log(g, refmath.mirror_y(mu), lam, 15),
+                               refmath.mirror_y(b), rtol=1e-11)
+    # periodic grid: integer translation commutes too
+    gp = oracle.Grid(12, 12, 8, 3, W, 6e-3, periodic=True)
+    bp = oracle.barycenter_log(gp, mu, lam, 15)
+    sh = lambda a: np.roll(a, (3, -5), axis=(-3, -2))
+    np.testing.assert_allclose(oracle.barycenter_log(gp, sh(mu), lam, 15), sh(bp), rtol=1e-11)
+
+
+def test_half_weights_and_half_turn_symmetric_input():
+    """lambda = (1/2, 1/2) and mu_2 = mu_1 rotated by 180 degrees: the barycenter is
+    invariant under that rotation (the rotation squared is the identity and swaps the inputs)."""
+    g = oracle.Grid(10, 10, 8, 3, W, 6e-3)
+    m1 = _inputs(g, 1, 9)[0]
+    m2 = refmath.rot90(refmath.rot90(m1))
+    b = oracle.barycenter_log(g, np.stack([m1, m2]), [0.5, 0.5], 11)
+    np.testing.assert_allclose(refmath.rot90(refmath.rot90(b)), b, rtol=1e-11)
+
+
+def test_log_and_linear_barycenters_agree():
+    g = oracle.Grid(9, 8, 4, 2, W, 0.03)
+    mu = _inputs(g, 3, 21)
+    lam = [0.6, 0.1, 0.3]
+    np.testing.assert_allclose(oracle.barycenter_log(g, mu, lam, 25),
+                               oracle.barycenter_lin(g, mu, lam, 25), rtol=1e-11)
+
+
+def test_converged_plans_have_the_prescribed_marginals():
+    """Large eps, tiny grid: run to convergence, then the explicit plans
+    pi_i = diag(v_i) K diag(w_i) have column sums mu_i and row sums mu; compare the oracle's
+    barycenter with a brute-force dense Sinkhorn barycenter run to the same point."""
+    g = oracle.Grid(5, 5, 4, 2, W, 0.2)
+    K = _dense_K(g)
+    mu = _inputs(g, 2, 4)
+    lam = [0.35, 0.65]
+    iters = 400
+    b, st = oracle.barycenter_log(g, mu, lam, iters, want_state=True)
+    assert st["viol"] < 1e-12
+    for i in range(2):
+        v = np.exp(st["lv"][i]).reshape(-1)
+        w = np.exp(st["lw"][i]).reshape(-1)
+        P = v[:, None] * K * w[None, :]
+        np.testing.assert_allclose(P.sum(axis=0), mu[i].reshape(-1), rtol=1e-10)
+        np.testing.assert_allclose(P.sum(axis=1), b.reshape(-1), rtol=1e-10)
+    # brute force: Bregman projections on the explicit plans (no convolution structure)
+    V = g.V
+    Ps = [K.copy() for _ in range(2)]
+    for _ in range(4000):
+        for i in range(2):
+            Ps[i] *= (mu[i].reshape(-1) / Ps[i].sum(axis=0))[None, :]
+        rows = [P.sum(axis=1) for P in Ps]
+        m = np.exp(sum(l * np.log(rw) for l, rw in zip(lam, rows)))
+        for i in range(2):
+            Ps[i] *= (m / rows[i])[:, None]
+    np.testing.assert_allclose(b.reshape(-1), m, rtol=1e-9)
+
+
+def test_single_orientation_barycenter_is_euclidean():
+    """nth = 1 reduces to the Euclidean convolutional barycenter with a separable Gaussian
+    kernel; compare against a loop whose convolutions are library 1-D correlations."""
+    nx, ny, r, eps = 14, 11, 3, 8e-3
+    g = oracle.Grid(nx, ny, 1, r, W, eps)
+    kx = np.exp(-(W[0] * np.arange(-r, r + 1) / nx) ** 2 / eps)
+    ky = np.exp(-(W[1] * np.arange(-r, r + 1) / ny) ** 2 / eps)
+
+    def Kc(a):
+        a = scipy.ndimage.correlate1d(a, kx, axis=1, mode="constant")
+        return scipy.ndimage.correlate1d(a, ky, axis=0, mode="constant")
+
+    mu = _inputs(g, 2, 8)[:, :, :, 0]
+    lam = [0.4, 0.6]
+    v = [np.ones((ny, nx)) for _ in range(2)]
+    for _ in range(20):
+        d = []
+        for i in range(2):
+            w = mu[i] / Kc(v[i])
+            d.append(v[i] * Kc(w))
+        m = np.exp(sum(l * np.log(di) for l, di in zip(lam, d)))
+        for i in range(2):
+            v[i] = v[i] * m / d[i]
+    got = oracle.barycenter_log(g, mu[..., None], lam, 20)[:, :, 0]
+    np.testing.assert_allclose(got, m, rtol=1e-11)
+
+
+def test_interpolation_endpoints():
+    g = oracle.Grid(6, 6, 4, 2, W, 0.05)
+    K = _dense_K(g)
+    mu = _inputs(g, 2, 13)
+    one = K @ np.ones(g.V)
+    for t, idx in ((0.0, 0), (1.0, 1)):
+        want = K @ (mu[idx].reshape(-1) / one)
+        got = oracle.interpolate_log(g, mu[0], mu[1], t, 6)
+        np.testing.assert_allclose(got.reshape(-1), want, rtol=1e-12)
