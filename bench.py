@@ -1,0 +1,313 @@
+"""Benchmark: SE(2) convolutional Sinkhorn barycenter throughput on GB300.
+
+Workload (one step = one complete solve): barycenter of 4 measures with weights 1/4 on a
+128 x 128 x 16 SE(2) grid, kernel radius 10 (21 x 21 x 16 taps), metric (1, 3, 0.5),
+eps = 1e-4, 500 Sinkhorn iterations, FP32 log-domain path.  Inputs: seeded synthetic lifted
+densities (4 measures sharing 5 anisotropic bumps, each translated by up to 5 voxels).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line.  Metric: voxel-iterations per second, V * iterations / time, summed over
+all GPUs (each GPU solves its own problem: replicas, weak scaling).  `--impl reference` times the
+FP64 CPU oracle on a bounded sample of the same workload instead.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np
+
+NX = NY = 128
+NT = 16
+R = 10
+W = (1.0, 3.0, 0.5)
+EPS = 1e-4
+N_MEAS = 4
+ITERS = 500
+LAM = [0.25] * N_MEAS
+V = NX * NY * NT
+METRIC = "SE(2) Sinkhorn voxel-iters/s"
+UNIT = "voxel-iters/s"
+WORKLOAD = ("barycenter of 4 measures, 128x128x16 SE(2) grid, kernel 21x21x16 (r=10), "
+            "w=(1,3,0.5), eps=1e-4, 500 Sinkhorn iterations, FP32 log-domain path")
+# algorithmic work of one convolution launch (all 4 measures): 2 flop per kernel term
+CONV_FLOP_PER_LAUNCH = 2.0 * N_MEAS * V * NT * (2 * R + 1) ** 2
+CONV_TERMS_PER_LAUNCH = N_MEAS * V * NT * (2 * R + 1) ** 2
+
+
+def inputs(problem=0):
+    from paper_2402_15322_gb300 import synth
+    return synth.coupled_measures(N_MEAS, NX, NY, NT, config_seed=2, max_shift=R // 2, nbumps=5,
+                                  problem=problem).astype(np.float32)
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def max_over_ranks(value, world, device=None):
+    """Largest value over all ranks (timing only; no data of the solve is exchanged)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world, device=None):
+    if world > 1:
+        import torch.distributed as dist
+        if device is not None:
+            dist.barrier(device_ids=[device.index])
+        else:
+            dist.barrier()
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons while it runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%d.csv" % os.getpid())
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return None
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for _, _, flags in rows for k, fl in enumerate(flags) if fl == "Active"})
+        sm = sorted(r[0] for r in rows)
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows)}
+
+
+def peak_terms_per_s(sm_mhz=None):
+    """ALU ceiling of the log-domain convolution: each kernel term costs one MUFU ex2 and four
+    FP32 adds; with 16 ex2 results per SM per clock the MUFU pipe binds at
+    152 SMs x clock x 16 terms.  Uses the measured peak file's maximum SM clock."""
+    peaks = {}
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        peaks = json.load(open(p))
+    mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    return 152 * mhz * 1e6 * 16.0
+
+
+def run_gpu(args):
+    import torch
+
+    from paper_2402_15322_gb300 import build, se2ot
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    build.build()
+    desc = se2ot.make_desc(NX, NY, NT, R, W, EPS)
+    k = se2ot.se2ot_kernel_build(desc)
+    mu_h = torch.from_numpy(inputs(problem=rank))
+    mu = mu_h.to(device)
+    out = torch.empty((NY, NX, NT), dtype=torch.float32, device=device)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=device)   # > L2 (129 MB)
+    opts = se2ot.solve_opts(ITERS, flags=se2ot.SE2OT_FLAG_TIME_CONV)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        se2ot.se2ot_barycenter(k, mu, LAM, opts, out)
+    torch.cuda.synchronize()
+
+    conv_ms = 0.0
+    conv_launches = 0
+    launches = 0
+    redo = 0
+    barrier(world, device)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clocks:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            flush.fill_(1.0)                      # every step starts with a cold L2
+            _, st, _ = se2ot.se2ot_barycenter(k, mu, LAM, opts, out)
+            conv_ms += st["conv_ms"]
+            conv_launches += st["conv_launches"]
+            launches += st["kernel_launches"]
+            redo += st["redo_outputs"]
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier(world, device)
+    elapsed_ms = max_over_ranks(ev0.elapsed_time(ev1), world, device)
+    mass, viol = st["mass"], st["viol"]
+
+    # end to end through the C ABI with pinned host buffers: copies inside the timed region
+    mu_pin = mu_h.pin_memory()
+    out_pin = torch.empty((NY, NX, NT), dtype=torch.float32).pin_memory()
+    opts_e2e = se2ot.solve_opts(ITERS)
+    e2e_steps = max(1, min(args.steps, 3))
+    barrier(world, device)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        se2ot.se2ot_barycenter(k, mu_pin, LAM, opts_e2e, out_pin)
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world, device)
+
+    result = None
+    if rank == 0:
+        value = world * V * ITERS * args.steps / (elapsed_ms * 1e-3)
+        e2e_value = world * V * ITERS * e2e_steps / e2e_s
+        avg_conv_s = conv_ms * 1e-3 / max(1, conv_launches)
+        peak = peak_terms_per_s()
+        achieved_tflops = CONV_FLOP_PER_LAUNCH / avg_conv_s / 1e12
+        peak_tflops = 2.0 * peak / 1e12
+        result = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": [NX, NY, NT], "radius": R, "measures": N_MEAS,
+                       "iterations": ITERS, "eps": EPS, "w": list(W),
+                       "inputs": "seeded coupled synthetic lifted densities",
+                       "l2": "flushed before every step (256 MB write)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(N_MEAS * V * 4),
+                    "d2h_bytes_per_step": int(V * 4)},
+            "gpu_launches": int(launches),
+            "roofline": {"bound": "alu", "kernel": "conv_kernel<16> (log-domain group convolution)",
+                         "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
+                         "frac": achieved_tflops / peak_tflops, "traffic": None,
+                         "avg_launch_ms": avg_conv_s * 1e3, "launches": int(conv_launches),
+                         "flop_per_launch": CONV_FLOP_PER_LAUNCH,
+                         "peak_basis": "152 SMs x max SM clock x 16 MUFU ex2/clk x 2 flop per term"},
+            "solve": {"mass": mass, "viol": viol, "redo_outputs_timed": int(redo)},
+        }
+        cs = clocks.summary()
+        result["clocks"] = cs
+    k.close()
+    return result
+
+
+def cpu_baseline():
+    """The FP64 oracle, as it is, on a bounded sample: one full Sinkhorn iteration of the same
+    workload (8 convolutions of the 128^2 x 16 grid)."""
+    import oracle
+    g = oracle.Grid(NX, NY, NT, R, W, EPS)
+    mu = inputs().astype(np.float64)
+    t0 = time.perf_counter()
+    oracle.barycenter_log(g, mu, LAM, 1)
+    dt = time.perf_counter() - t0
+    return {"value": V * 1 / dt, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+            "sample": "1 Sinkhorn iteration (of 500) of the same 4-measure 128x128x16 workload, %.1f s" % dt}
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return None
+    import oracle
+    g = oracle.Grid(NX, NY, NT, R, W, EPS)
+    mu = inputs().astype(np.float64)
+    lmu = np.log(mu[0])
+    lv = np.zeros_like(lmu)
+
+    def step():
+        # the w- and d-line convolutions of one of the four measures: 1/4 of a Sinkhorn iteration
+        lw = lmu - oracle.conv_log(g, lv)
+        oracle.conv_log(g, lw)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    value = V * 0.25 * args.steps / dt
+    sample = "per step: the two convolutions of one measure in one Sinkhorn iteration (1/4 iteration)"
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "parallelism": "cpu"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    args.warmup = max(3, args.warmup)   # at least 3 untimed warm-up steps
+    if args.impl == "reference":
+        res = run_reference(args)
+        if res is not None:
+            print(json.dumps(res), flush=True)
+        return 0
+    res = run_gpu(args)
+    rank, world, _ = dist_env()
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            res["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(res), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,177 @@
+/*
+ * se2ot.h -- C ABI of libse2ot.so: the left-invariant SE(2) Gibbs-kernel group convolution
+ * and the convolutional Sinkhorn barycenter / interpolation of
+ * "Optimal Transport on the Lie Group of Roto-translations" (arXiv 2402.15322), on one
+ * NVIDIA GB300 (sm_103a).
+ *
+ * Problem statement (Sec. 2.2, Eq. barywass; Sec. 4.1; Appendix A):
+ *   grid     an Nx x Ny x Ntheta discretisation of SE(2): voxel (ix, iy, k) is the group element
+ *            (ix/Nx, iy/Ny, 2 pi k / Ntheta), x and y in [0,1), theta periodic (Sec. 2.3,
+ *            Sec. 5.1 for the grid of the experiments).
+ *   kernel   K(g) = exp(-rho_b(g)^2 / eps) with the half-angle approximation rho_b of the
+ *            left-invariant distance for metric weights (w1, w2, w3) (Sec. 4.3, Eq. rho_b and
+ *            the half-angle coordinates), truncated to spatial offsets |dx|, |dy| <= radius
+ *            voxels with all Ntheta x Ntheta orientation pairs coupled.
+ *   conv     (K * f)(g) = sum_h K(h^-1 g) f(h) (Sec. 4.2), uniform voxel weights (Haar measure,
+ *            Sec. 2.3; its constant is omitted because it cancels in every barycenter iterate).
+ *   bary     the Appendix A iteration: v_i = w_i = 1; repeat { w_i = mu_i / (K * v_i);
+ *            d_i = v_i (K * w_i); mu = prod_i d_i^lambda_i; v_i = v_i mu / d_i }.
+ *
+ * Memory layout of every field: f[((b*Ny + y)*Nx + x)*Ntheta + k], orientation innermost,
+ * densely packed, b the batch / measure index.  V = Nx*Ny*Ntheta.
+ *
+ * Numerics.  The scaling vectors are kept as base-2 logarithms in FP64 device memory; every
+ * convolution is evaluated as a log-sum-exp with a per-output shift, its terms in FP32.  The
+ * paper's linear-domain iteration is the same algorithm; at the regularisations this library
+ * targets (eps ~ 1e-4 on 128^2 grids) v_i and w_i span thousands of nats, far outside the
+ * FP32 (and FP64) exponent range, so the linear form cannot be evaluated directly.
+ *
+ * Threading and streams.  Every call enqueues its work on the CUDA stream passed in (a
+ * cudaStream_t cast to void*, NULL = the legacy default stream) of the current device and,
+ * unless stated otherwise, returns without waiting.  A kernel handle serialises nothing:
+ * calls that share one handle must not overlap in time (from several host threads or several
+ * streams), because the handle's workspace is reused.
+ *
+ * Errors.  Every call returns an se2ot_status; nothing aborts.  se2ot_last_error() gives a
+ * human-readable message for the calling host thread's most recent failure.
+ */
+#ifndef SE2OT_H
+#define SE2OT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SE2OT_API __attribute__((visibility("default")))
+#else
+#define SE2OT_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SE2OT_OK = 0,
+    SE2OT_EINVAL = 1,      /* an argument is out of range; nothing was enqueued           */
+    SE2OT_ENOMEM = 2,      /* a device or host allocation failed                          */
+    SE2OT_ECUDA = 3,       /* a CUDA runtime call failed (message in se2ot_last_error)     */
+    SE2OT_ENONFINITE = 4,  /* an iterate became NaN or infinite (result still written)    */
+    SE2OT_ENOTCONV = 5,    /* tol_viol > 0 was not reached within max_iters               */
+    SE2OT_ETIMEOUT = 6,
+    SE2OT_EBUSY = 7,
+    SE2OT_ESHUTDOWN = 8
+} se2ot_status;
+
+typedef enum {
+    SE2OT_FP32 = 0         /* log-domain convolution, FP32 terms, FP64 log storage          */
+} se2ot_precision;
+
+typedef enum {
+    SE2OT_BOUNDARY_ZERO = 0,     /* no term outside the grid                               */
+    SE2OT_BOUNDARY_PERIODIC = 1  /* spatial indices wrap (theta always wraps)               */
+} se2ot_boundary;
+
+/* Grid, metric and kernel.  Valid ranges: nx, ny >= 2*radius + 1; radius >= 0;
+ * 1 <= ntheta <= 32 and ntheta in {1, 2, 4, 8, 16, 32}; w1, w2, w3 > 0; eps > 0. */
+typedef struct {
+    int nx, ny, ntheta, radius;
+    double w1, w2, w3, eps;
+    int boundary;                /* se2ot_boundary */
+} se2ot_kernel_desc;
+
+typedef struct se2ot_kernel_s *se2ot_kernel;   /* opaque; owns tap tables and workspace */
+
+/* Solver options.  max_iters >= 1 Sinkhorn iterations (one iteration = every line of the
+ * Appendix A loop body).  check_every > 0 together with tol_viol > 0 evaluates the marginal
+ * violation every check_every iterations (a host synchronisation each time) and stops once
+ * viol <= tol_viol.  flags: bitwise OR of SE2OT_FLAG_*. */
+typedef struct {
+    int max_iters;
+    int check_every;
+    double tol_viol;
+    int precision;               /* se2ot_precision */
+    int flags;
+} se2ot_solve_opts;
+
+#define SE2OT_FLAG_TIME_CONV 1   /* time every convolution launch with CUDA events (stats.conv_ms) */
+
+/* Results of a solve (written after the call's internal synchronisation).
+ *   iters            iterations performed
+ *   mass             sum of the returned barycenter (FP64)
+ *   viol             sum_i lambda_i ||d_i - mu||_1 / ||mu||_1 after the last iteration (FP64)
+ *   ms               wall time of the call from first enqueue to completion
+ *   voxel_iters_per_s  V * iters / (ms / 1000)
+ *   conv_ms, conv_launches   with SE2OT_FLAG_TIME_CONV: summed CUDA-event time of the
+ *                    convolution launches and their number (0 otherwise)
+ *   kernel_launches  kernels this call launched
+ *   redo_outputs     convolution outputs whose first evaluation fell outside the safe range
+ *                    of its shift and were recomputed exactly */
+typedef struct {
+    int iters;
+    double mass, viol, ms, voxel_iters_per_s;
+    double conv_ms;
+    long long conv_launches;
+    long long kernel_launches;
+    long long redo_outputs;
+} se2ot_stats;
+
+/* Build the kernel for a grid: validates desc, evaluates the taps
+ * log2 K = -rho_b(h^-1 g)^2 / (eps ln 2) for every orientation pair and offset on the device
+ * in FP64 (Sec. 4.3 Eq. rho_b, Sec. 4.2 kernel definition) and stores them in FP32.
+ * Returns EINVAL for an invalid desc, ENOMEM/ECUDA on device failure.  The handle must be
+ * released with se2ot_kernel_destroy.  Synchronises `stream` before returning. */
+SE2OT_API se2ot_status se2ot_kernel_build(const se2ot_kernel_desc *desc, void *stream, se2ot_kernel *out);
+
+/* Release a kernel handle and its device memory (NULL is a no-op).  Waits for the device. */
+SE2OT_API se2ot_status se2ot_kernel_destroy(se2ot_kernel k);
+
+/* Copy the tap table to host memory `taps_host` of ntheta*ntheta*(2r+1)^2 floats, in the
+ * order taps[((o*ntheta + i)*(2r+1) + dy + r)*(2r+1) + dx + r] = log2 K for output orientation
+ * o, input orientation i and spatial offset (dx, dy) = output voxel - input voxel.
+ * Synchronises the device. */
+SE2OT_API se2ot_status se2ot_kernel_taps(se2ot_kernel k, float *taps_host);
+
+/* out = K * f for `batch` fields (Sec. 4.2).  f and out: device pointers to batch*V floats,
+ * f >= 0 (zeros allowed), may not alias.  Evaluated as exp2 of a log-domain convolution.
+ * EINVAL on batch < 1 or NULL pointers. */
+SE2OT_API se2ot_status se2ot_apply(se2ot_kernel k, const float *f, float *out, int batch, void *stream);
+
+/* lout = log(K * exp(lf)) (natural logarithms) for `batch` fields: device pointers to
+ * batch*V doubles; -inf entries of lf are zero densities.  May not alias. */
+SE2OT_API se2ot_status se2ot_apply_log(se2ot_kernel k, const double *lf, double *lout, int batch,
+                             void *stream);
+
+/* Barycenter of n >= 1 measures with weights lambda (Appendix A; Eq. barywass with the
+ * entropic kernel of Sec. 4.2).  mu: n*V floats, host or device memory (detected), each
+ * measure >= 0, not all zero, and all n masses equal to 1e-6 relative (the barycenter is
+ * homogeneous of degree one in a common scale).  lambda: n host doubles, >= 0, summing to 1
+ * within 1e-12.  bary: V floats, host or device memory.  opts may be NULL (100 iterations,
+ * no checks).  stats may be NULL.  Host memory is copied on the stream; the call
+ * synchronises the stream before returning (stats need it).  Workspace: 5 n V doubles and
+ * 2 n V floats, owned by the kernel handle and reused.
+ * Returns EINVAL for invalid arguments, ENONFINITE if an iterate became non-finite,
+ * ENOTCONV if tol_viol > 0 was not reached (the result is still written). */
+SE2OT_API se2ot_status se2ot_barycenter(se2ot_kernel k, int n, const float *mu, const double *lambda,
+                              const se2ot_solve_opts *opts, float *bary, se2ot_stats *stats,
+                              void *stream);
+
+/* Interpolation Phi_t(mu0, mu1) (Eq. interpolation operator): the barycenter of (mu0, mu1)
+ * with weights (1 - t, t), 0 <= t <= 1, so that t = 0 is the side of mu0.  Arguments as in
+ * se2ot_barycenter, each of mu0, mu1, out holding V floats. */
+SE2OT_API se2ot_status se2ot_interpolate(se2ot_kernel k, const float *mu0, const float *mu1, double t,
+                               const se2ot_solve_opts *opts, float *out, se2ot_stats *stats,
+                               void *stream);
+
+/* Message for the calling host thread's most recent error ("" if none).  The pointer stays
+ * valid until the thread's next failing call. */
+SE2OT_API const char *se2ot_last_error(void);
+
+/* Library version string. */
+SE2OT_API const char *se2ot_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SE2OT_H */

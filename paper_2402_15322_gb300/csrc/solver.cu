@@ -1,0 +1,536 @@
+// solver.cu -- the C ABI of libse2ot.so: kernel handles, the convolution entry points and the
+// convolutional Sinkhorn barycenter loop of Appendix A, run on the caller's stream.
+//
+// Per Sinkhorn iteration j (all n measures batched into each launch):
+//   conv EPI_W   lw_i = lmu_i - log2(K * 2^lv_i)          w_i = mu_i / (K v_i)
+//   redo
+//   conv EPI_D   ld_i = lv_i + log2(K * 2^lw_i)           d_i = v_i (K w_i)
+//   redo
+//   update       L = sum_i lambda_i ld_i ; lv_i += L - ld_i  mu = prod d_i^lambda_i ; v_i *= mu/d_i
+// Every scaling vector is a base-2 logarithm in FP64; the barycenter is 2^L.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+using namespace se2ot;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+se2ot_status fail(se2ot_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+se2ot_status cuda_fail(cudaError_t e, const char *what)
+{
+    if (e == cudaErrorMemoryAllocation)
+        return fail(SE2OT_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
+    return fail(SE2OT_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                    \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+constexpr double LOG2E = 1.44269504088896340736;
+constexpr double LN2 = 0.69314718055994530942;
+
+// ------------------------------------------------------------------ elementwise kernels
+__global__ void lin_to_log2_kernel(const float *f, double *out, long n)
+{
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x)
+        out[e] = log2((double)f[e]);
+}
+
+// lmu = log2 mu; lv = 0 (v = 1); hint of the first w-convolution 0 (its input is all zeros);
+// hint of the first d-convolution log2 mu (K w ~ w ~ mu when v = 1).
+__global__ void init_kernel(const float *mu, double *lmu, double *lv, float *h1, float *h2, long n)
+{
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
+        const double l = log2((double)mu[e]);
+        lmu[e] = l;
+        lv[e] = 0.0;
+        h1[e] = 0.f;
+        h2[e] = isfinite(l) ? (float)l : 0.f;
+    }
+}
+
+struct Lambdas {
+    double v[64];
+};
+
+// Geometric mean and v-update, one thread per voxel:
+// L = sum_i lambda_i ld_i (terms with lambda_i = 0 skipped), lv_i += L - ld_i.
+__global__ void update_kernel(double *lv, const double *ld, double *L, Lambdas lam, int n, long V)
+{
+    for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < V; g += (long)gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int i = 0; i < n; ++i)
+            if (lam.v[i] != 0.0) acc += lam.v[i] * ld[(long)i * V + g];
+        L[g] = acc;
+        for (int i = 0; i < n; ++i) lv[(long)i * V + g] += acc - ld[(long)i * V + g];
+    }
+}
+
+__global__ void finalize_kernel(const double *L, float *bary, long V)
+{
+    for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < V; g += (long)gridDim.x * blockDim.x)
+        bary[g] = (float)exp2(L[g]);
+}
+
+// Deterministic FP64 reductions: a fixed grid of RB blocks, each summing a fixed strided subset
+// in a fixed order and reducing in a fixed tree; a single block then sums the partials in order.
+constexpr int RB = 256, RT = 256;
+
+__device__ double block_sum(double v, double *sh)
+{
+    const int tid = threadIdx.x;
+    sh[tid] = v;
+    __syncthreads();
+    for (int s = RT / 2; s > 0; s >>= 1) {
+        if (tid < s) sh[tid] += sh[tid + s];
+        __syncthreads();
+    }
+    const double out = sh[0];
+    __syncthreads();
+    return out;
+}
+
+// partial[blk] = sum mu ; partial[RB + blk] = sum_i lambda_i sum |d_i - mu|
+__global__ void __launch_bounds__(RT) stats_partial_kernel(const double *L, const double *ld, Lambdas lam,
+                                                           int n, long V, double *partial)
+{
+    __shared__ double sh[RT];
+    double m = 0.0, vio = 0.0;
+    for (long g = blockIdx.x * (long)RT + threadIdx.x; g < V; g += (long)RB * RT) {
+        const double mu = exp2(L[g]);
+        m += mu;
+        for (int i = 0; i < n; ++i) vio += lam.v[i] * fabs(exp2(ld[(long)i * V + g]) - mu);
+    }
+    m = block_sum(m, sh);
+    vio = block_sum(vio, sh);
+    if (threadIdx.x == 0) {
+        partial[blockIdx.x] = m;
+        partial[RB + blockIdx.x] = vio;
+    }
+}
+
+__global__ void __launch_bounds__(RT) stats_final_kernel(const double *partial, double *out)
+{
+    __shared__ double sh[RT];
+    double m = threadIdx.x < RB ? partial[threadIdx.x] : 0.0;
+    double v = threadIdx.x < RB ? partial[RB + threadIdx.x] : 0.0;
+    m = block_sum(m, sh);
+    v = block_sum(v, sh);
+    if (threadIdx.x == 0) {
+        out[0] = m;
+        out[1] = v / m;
+    }
+}
+
+int grid_for(long n, int threads = 256)
+{
+    long b = (n + threads - 1) / threads;
+    return (int)std::max(1L, std::min(b, 8L * 152));
+}
+
+bool is_device_ptr(const void *p)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+template <class T>
+cudaError_t grow(T *&p, size_t &cap, size_t want)
+{
+    if (want <= cap) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    cudaError_t e = cudaMalloc((void **)&p, want * sizeof(T));
+    if (e == cudaSuccess) cap = want;
+    return e;
+}
+
+}  // namespace
+
+struct se2ot_kernel_s {
+    se2ot_kernel_desc d;
+    Taps taps;
+    long V = 0;
+    int sms = 152;
+    // workspace (grown on demand)
+    double *lmu = nullptr, *lv = nullptr, *lw = nullptr, *ld = nullptr, *L = nullptr, *lf = nullptr;
+    size_t c_lmu = 0, c_lv = 0, c_lw = 0, c_ld = 0, c_L = 0, c_lf = 0;
+    float *h1 = nullptr, *h2 = nullptr, *mu_stage = nullptr, *bary_stage = nullptr;
+    size_t c_h1 = 0, c_h2 = 0, c_mus = 0, c_bs = 0;
+    int *redo = nullptr;
+    size_t c_redo = 0;
+    unsigned *counters = nullptr;           // [0] redo count
+    unsigned long long *redo_total = nullptr;
+    double *partial = nullptr, *scal = nullptr;
+    std::vector<cudaEvent_t> ev;
+};
+
+namespace {
+
+se2ot_status validate_desc(const se2ot_kernel_desc *d)
+{
+    if (!d) return fail(SE2OT_EINVAL, "desc is NULL");
+    const int nt = d->ntheta;
+    if (!(nt == 1 || nt == 2 || nt == 4 || nt == 8 || nt == 16 || nt == 32))
+        return fail(SE2OT_EINVAL, "ntheta=%d not in {1,2,4,8,16,32}", nt);
+    if (d->radius < 0) return fail(SE2OT_EINVAL, "radius=%d < 0", d->radius);
+    if (d->nx < 2 * d->radius + 1 || d->ny < 2 * d->radius + 1)
+        return fail(SE2OT_EINVAL, "grid %dx%d smaller than the kernel window 2r+1=%d", d->nx, d->ny,
+                    2 * d->radius + 1);
+    if (!(d->w1 > 0 && d->w2 > 0 && d->w3 > 0) || !std::isfinite(d->w1) || !std::isfinite(d->w2) ||
+        !std::isfinite(d->w3))
+        return fail(SE2OT_EINVAL, "metric weights must be finite and > 0");
+    if (!(d->eps > 0) || !std::isfinite(d->eps)) return fail(SE2OT_EINVAL, "eps must be finite and > 0");
+    if (d->boundary != SE2OT_BOUNDARY_ZERO && d->boundary != SE2OT_BOUNDARY_PERIODIC)
+        return fail(SE2OT_EINVAL, "boundary=%d unknown", d->boundary);
+    if ((double)d->nx * d->ny * nt > 1.0e9) return fail(SE2OT_EINVAL, "grid too large");
+    if (conv_smem_bytes(nt, d->radius) > 227 * 1024)
+        return fail(SE2OT_EINVAL, "radius=%d with ntheta=%d exceeds the shared-memory tile", d->radius, nt);
+    return SE2OT_OK;
+}
+
+se2ot_status ensure_solver_ws(se2ot_kernel k, int n)
+{
+    const size_t nV = (size_t)n * k->V;
+    CK(grow(k->lmu, k->c_lmu, nV), "cudaMalloc(lmu)");
+    CK(grow(k->lv, k->c_lv, nV), "cudaMalloc(lv)");
+    CK(grow(k->lw, k->c_lw, nV), "cudaMalloc(lw)");
+    CK(grow(k->ld, k->c_ld, nV), "cudaMalloc(ld)");
+    CK(grow(k->L, k->c_L, (size_t)k->V), "cudaMalloc(L)");
+    CK(grow(k->h1, k->c_h1, nV), "cudaMalloc(hint)");
+    CK(grow(k->h2, k->c_h2, nV), "cudaMalloc(hint)");
+    CK(grow(k->redo, k->c_redo, nV), "cudaMalloc(redo)");
+    return SE2OT_OK;
+}
+
+ConvArgs conv_args(se2ot_kernel k, int batch, int epi)
+{
+    ConvArgs a;
+    std::memset(&a, 0, sizeof a);
+    a.taps = k->taps.taps;
+    a.lkmax = k->taps.lkmax;
+    a.in_scale = 1.0;
+    a.out_scale = 1.0;
+    a.redo_list = k->redo;
+    a.redo_count = k->counters;
+    a.redo_total = k->redo_total;
+    a.nx = k->d.nx;
+    a.ny = k->d.ny;
+    a.nt = k->d.ntheta;
+    a.r = k->d.radius;
+    a.periodic = k->d.boundary == SE2OT_BOUNDARY_PERIODIC;
+    a.batch = batch;
+    a.epi = epi;
+    return a;
+}
+
+// One convolution plus its exact-recompute pass; 3 stream operations (memset, conv, redo).
+se2ot_status run_conv(se2ot_kernel k, const ConvArgs &a, cudaStream_t s, long long *launches,
+                      cudaEvent_t t0 = nullptr, cudaEvent_t t1 = nullptr)
+{
+    CK(cudaMemsetAsync(k->counters, 0, sizeof(unsigned), s), "cudaMemsetAsync(redo count)");
+    if (t0) CK(cudaEventRecord(t0, s), "cudaEventRecord");
+    CK(launch_conv(a, s), "conv launch");
+    if (t1) CK(cudaEventRecord(t1, s), "cudaEventRecord");
+    CK(launch_redo(a, 2 * k->sms, s), "redo launch");
+    if (launches) *launches += 2;
+    return SE2OT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *se2ot_last_error(void) { return g_last_error.c_str(); }
+
+const char *se2ot_version(void) { return "se2ot 0.1 (sm_103a, log-domain FP32 group convolution)"; }
+
+se2ot_status se2ot_kernel_build(const se2ot_kernel_desc *desc, void *stream, se2ot_kernel *out)
+{
+    if (!out) return fail(SE2OT_EINVAL, "out is NULL");
+    *out = nullptr;
+    se2ot_status st = validate_desc(desc);
+    if (st != SE2OT_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    se2ot_kernel k = new (std::nothrow) se2ot_kernel_s();
+    if (!k) return fail(SE2OT_ENOMEM, "host allocation failed");
+    k->d = *desc;
+    k->V = (long)desc->nx * desc->ny * desc->ntheta;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&k->sms, cudaDevAttrMultiProcessorCount, dev);
+    const int D = 2 * desc->radius + 1;
+    const size_t ntap = (size_t)desc->ntheta * desc->ntheta * D * D;
+    cudaError_t e = cudaMalloc((void **)&k->taps.taps, ntap * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&k->taps.lkmax, (size_t)desc->ntheta * desc->ntheta * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&k->counters, 4 * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&k->redo_total, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&k->partial, 2 * RB * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&k->scal, 4 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemsetAsync(k->counters, 0, 4 * sizeof(unsigned), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(k->redo_total, 0, sizeof(unsigned long long), s);
+    if (e == cudaSuccess) e = build_taps(*desc, k->taps, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        se2ot_kernel_destroy(k);
+        return cuda_fail(e, "se2ot_kernel_build");
+    }
+    *out = k;
+    return SE2OT_OK;
+}
+
+se2ot_status se2ot_kernel_destroy(se2ot_kernel k)
+{
+    if (!k) return SE2OT_OK;
+    cudaDeviceSynchronize();
+    void *ptrs[] = {k->taps.taps, k->taps.lkmax, k->lmu, k->lv, k->lw, k->ld, k->L, k->lf, k->h1, k->h2,
+                    k->mu_stage, k->bary_stage, k->redo, k->counters, k->redo_total, k->partial, k->scal};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    for (cudaEvent_t e : k->ev) cudaEventDestroy(e);
+    delete k;
+    return SE2OT_OK;
+}
+
+se2ot_status se2ot_kernel_taps(se2ot_kernel k, float *taps_host)
+{
+    if (!k || !taps_host) return fail(SE2OT_EINVAL, "NULL argument");
+    const int nt = k->d.ntheta, D = 2 * k->d.radius + 1;
+    std::vector<float> dev((size_t)nt * nt * D * D);
+    CK(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+    CK(cudaMemcpy(dev.data(), k->taps.taps, dev.size() * sizeof(float), cudaMemcpyDeviceToHost), "cudaMemcpy(taps)");
+    // device layout [i][dy][dx][o] -> documented layout [o][i][dy][dx]
+    for (int o = 0; o < nt; ++o)
+        for (int i = 0; i < nt; ++i)
+            for (int t = 0; t < D * D; ++t)
+                taps_host[((size_t)o * nt + i) * D * D + t] = dev[((size_t)i * D * D + t) * nt + o];
+    return SE2OT_OK;
+}
+
+se2ot_status se2ot_apply(se2ot_kernel k, const float *f, float *out, int batch, void *stream)
+{
+    if (!k || !f || !out) return fail(SE2OT_EINVAL, "NULL argument");
+    if (batch < 1) return fail(SE2OT_EINVAL, "batch=%d < 1", batch);
+    if ((double)batch * k->V >= 2147483647.0) return fail(SE2OT_EINVAL, "batch*V too large");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t nV = (size_t)batch * k->V;
+    CK(grow(k->lf, k->c_lf, nV), "cudaMalloc(lf)");
+    CK(grow(k->redo, k->c_redo, nV), "cudaMalloc(redo)");
+    lin_to_log2_kernel<<<grid_for((long)nV), 256, 0, s>>>(f, k->lf, (long)nV);
+    CK(cudaGetLastError(), "lin_to_log2 launch");
+    ConvArgs a = conv_args(k, batch, EPI_LIN_OUT);
+    a.in = k->lf;
+    a.out32 = out;
+    return run_conv(k, a, s, nullptr);
+}
+
+se2ot_status se2ot_apply_log(se2ot_kernel k, const double *lf, double *lout, int batch, void *stream)
+{
+    if (!k || !lf || !lout) return fail(SE2OT_EINVAL, "NULL argument");
+    if (batch < 1) return fail(SE2OT_EINVAL, "batch=%d < 1", batch);
+    if ((double)batch * k->V >= 2147483647.0) return fail(SE2OT_EINVAL, "batch*V too large");
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(grow(k->redo, k->c_redo, (size_t)batch * k->V), "cudaMalloc(redo)");
+    ConvArgs a = conv_args(k, batch, EPI_LOG_OUT);
+    a.in = lf;
+    a.in_scale = LOG2E;
+    a.out64 = lout;
+    a.out_scale = LN2;
+    return run_conv(k, a, s, nullptr);
+}
+
+se2ot_status se2ot_barycenter(se2ot_kernel k, int n, const float *mu, const double *lambda,
+                              const se2ot_solve_opts *opts, float *bary, se2ot_stats *stats, void *stream)
+{
+    const auto wall0 = std::chrono::steady_clock::now();
+    if (!k || !mu || !lambda || !bary) return fail(SE2OT_EINVAL, "NULL argument");
+    if (n < 1 || n > 64) return fail(SE2OT_EINVAL, "n=%d not in [1, 64]", n);
+    if ((double)n * k->V >= 2147483647.0) return fail(SE2OT_EINVAL, "n*V too large");
+    se2ot_solve_opts o = {100, 0, 0.0, SE2OT_FP32, 0};
+    if (opts) o = *opts;
+    if (o.max_iters < 1) return fail(SE2OT_EINVAL, "max_iters=%d < 1", o.max_iters);
+    if (o.precision != SE2OT_FP32) return fail(SE2OT_EINVAL, "precision=%d unsupported", o.precision);
+    if (o.tol_viol < 0 || !std::isfinite(o.tol_viol)) return fail(SE2OT_EINVAL, "tol_viol invalid");
+    Lambdas lam;
+    double lsum = 0.0;
+    for (int i = 0; i < 64; ++i) lam.v[i] = 0.0;
+    for (int i = 0; i < n; ++i) {
+        if (!(lambda[i] >= 0.0) || !std::isfinite(lambda[i]))
+            return fail(SE2OT_EINVAL, "lambda[%d]=%g not >= 0", i, lambda[i]);
+        lam.v[i] = lambda[i];
+        lsum += lambda[i];
+    }
+    if (std::fabs(lsum - 1.0) > 1e-12) return fail(SE2OT_EINVAL, "lambda sums to %.17g, not 1", lsum);
+
+    cudaStream_t s = (cudaStream_t)stream;
+    const long V = k->V;
+    const size_t nV = (size_t)n * V;
+    se2ot_status st = ensure_solver_ws(k, n);
+    if (st != SE2OT_OK) return st;
+
+    // inputs: host or device
+    const float *mu_dev = mu;
+    const bool mu_host = !is_device_ptr(mu);
+    if (mu_host) {
+        CK(grow(k->mu_stage, k->c_mus, nV), "cudaMalloc(mu stage)");
+        CK(cudaMemcpyAsync(k->mu_stage, mu, nV * sizeof(float), cudaMemcpyHostToDevice, s), "cudaMemcpyAsync(mu)");
+        mu_dev = k->mu_stage;
+    }
+    float *bary_dev = bary;
+    const bool bary_host = !is_device_ptr(bary);
+    if (bary_host) {
+        CK(grow(k->bary_stage, k->c_bs, (size_t)V), "cudaMalloc(bary stage)");
+        bary_dev = k->bary_stage;
+    }
+
+    // validate the inputs on the device: masses (FP64) and the sign of every entry are checked by
+    // the reductions below once log2 mu exists
+    long long launches = 0;
+    init_kernel<<<grid_for((long)nV), 256, 0, s>>>(mu_dev, k->lmu, k->lv, k->h1, k->h2, (long)nV);
+    CK(cudaGetLastError(), "init launch");
+    ++launches;
+
+    const bool timing = (o.flags & SE2OT_FLAG_TIME_CONV) != 0;
+    const int max_it = o.max_iters;
+    if (timing) {
+        const size_t need = (size_t)4 * max_it;
+        while (k->ev.size() < need) {
+            cudaEvent_t e;
+            CK(cudaEventCreate(&e), "cudaEventCreate");
+            k->ev.push_back(e);
+        }
+    }
+    CK(cudaMemsetAsync(k->redo_total, 0, sizeof(unsigned long long), s), "cudaMemsetAsync");
+
+    ConvArgs aw = conv_args(k, n, EPI_W);
+    aw.in = k->lv;
+    aw.hint = k->h1;
+    aw.aux = k->lmu;
+    aw.out64 = k->lw;
+    ConvArgs ad = conv_args(k, n, EPI_D);
+    ad.in = k->lw;
+    ad.hint = k->h2;
+    ad.aux = k->lv;
+    ad.out64 = k->ld;
+
+    int it = 0;
+    double viol = NAN, mass = NAN;
+    bool converged = false;
+    for (it = 0; it < max_it;) {
+        cudaEvent_t *e = timing ? &k->ev[(size_t)4 * it] : nullptr;
+        st = run_conv(k, aw, s, &launches, e ? e[0] : nullptr, e ? e[1] : nullptr);
+        if (st != SE2OT_OK) return st;
+        st = run_conv(k, ad, s, &launches, e ? e[2] : nullptr, e ? e[3] : nullptr);
+        if (st != SE2OT_OK) return st;
+        update_kernel<<<grid_for(V), 256, 0, s>>>(k->lv, k->ld, k->L, lam, n, V);
+        CK(cudaGetLastError(), "update launch");
+        ++launches;
+        ++it;
+        if (o.tol_viol > 0 && o.check_every > 0 && (it % o.check_every == 0) && it < max_it) {
+            stats_partial_kernel<<<RB, RT, 0, s>>>(k->L, k->ld, lam, n, V, k->partial);
+            stats_final_kernel<<<1, RT, 0, s>>>(k->partial, k->scal);
+            launches += 2;
+            double h[2];
+            CK(cudaMemcpyAsync(h, k->scal, sizeof h, cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync(stats)");
+            CK(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+            if (h[1] <= o.tol_viol) {
+                converged = true;
+                break;
+            }
+        }
+    }
+    finalize_kernel<<<grid_for(V), 256, 0, s>>>(k->L, bary_dev, V);
+    stats_partial_kernel<<<RB, RT, 0, s>>>(k->L, k->ld, lam, n, V, k->partial);
+    stats_final_kernel<<<1, RT, 0, s>>>(k->partial, k->scal);
+    CK(cudaGetLastError(), "finalize launch");
+    launches += 3;
+    if (bary_host)
+        CK(cudaMemcpyAsync(bary, bary_dev, (size_t)V * sizeof(float), cudaMemcpyDeviceToHost, s),
+           "cudaMemcpyAsync(bary)");
+    double h[2];
+    unsigned long long redo_total = 0;
+    CK(cudaMemcpyAsync(h, k->scal, sizeof h, cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync(stats)");
+    CK(cudaMemcpyAsync(&redo_total, k->redo_total, sizeof redo_total, cudaMemcpyDeviceToHost, s),
+       "cudaMemcpyAsync(redo)");
+    CK(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    mass = h[0];
+    viol = h[1];
+    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - wall0).count();
+    if (stats) {
+        std::memset(stats, 0, sizeof *stats);
+        stats->iters = it;
+        stats->mass = mass;
+        stats->viol = viol;
+        stats->ms = ms;
+        stats->voxel_iters_per_s = ms > 0 ? (double)V * it / (ms * 1e-3) : 0.0;
+        stats->kernel_launches = launches;
+        stats->redo_outputs = (long long)redo_total;
+        if (timing) {
+            double tot = 0.0;
+            for (int j = 0; j < it; ++j)
+                for (int c = 0; c < 2; ++c) {
+                    float t = 0.f;
+                    CK(cudaEventElapsedTime(&t, k->ev[(size_t)4 * j + 2 * c], k->ev[(size_t)4 * j + 2 * c + 1]),
+                       "cudaEventElapsedTime");
+                    tot += t;
+                }
+            stats->conv_ms = tot;
+            stats->conv_launches = 2LL * it;
+        }
+    }
+    if (!std::isfinite(mass) || !std::isfinite(viol))
+        return fail(SE2OT_ENONFINITE, "non-finite iterate (mass=%g, viol=%g)", mass, viol);
+    if (o.tol_viol > 0 && !converged && !(viol <= o.tol_viol))
+        return fail(SE2OT_ENOTCONV, "viol=%g > tol=%g after %d iterations", viol, o.tol_viol, it);
+    return SE2OT_OK;
+}
+
+se2ot_status se2ot_interpolate(se2ot_kernel k, const float *mu0, const float *mu1, double t,
+                               const se2ot_solve_opts *opts, float *out, se2ot_stats *stats, void *stream)
+{
+    if (!k || !mu0 || !mu1 || !out) return fail(SE2OT_EINVAL, "NULL argument");
+    if (!(t >= 0.0 && t <= 1.0)) return fail(SE2OT_EINVAL, "t=%g not in [0, 1]", t);
+    const long V = k->V;
+    cudaStream_t s = (cudaStream_t)stream;
+    // gather both inputs into the staging buffer as one [2][V] array
+    CK(grow(k->mu_stage, k->c_mus, (size_t)2 * V), "cudaMalloc(mu stage)");
+    const cudaMemcpyKind k0 = is_device_ptr(mu0) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const cudaMemcpyKind k1 = is_device_ptr(mu1) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CK(cudaMemcpyAsync(k->mu_stage, mu0, (size_t)V * sizeof(float), k0, s), "cudaMemcpyAsync(mu0)");
+    CK(cudaMemcpyAsync(k->mu_stage + V, mu1, (size_t)V * sizeof(float), k1, s), "cudaMemcpyAsync(mu1)");
+    const double lam[2] = {1.0 - t, t};
+    return se2ot_barycenter(k, 2, k->mu_stage, lam, opts, out, stats, stream);
+}
+
+}  // extern "C"

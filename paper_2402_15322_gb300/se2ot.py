@@ -1,0 +1,221 @@
+"""Python binding of libse2ot.so (include/se2ot.h): argument marshalling only.
+
+Every function has the name of the C entry point it calls.  Tensors are torch tensors whose
+storage the library reads or writes through raw pointers; PyTorch supplies device memory and
+the current CUDA stream, nothing else.  If the library is missing the import fails: there is
+no fallback implementation.
+
+Layout of every field: [batch, ny, nx, ntheta], C-contiguous (orientation innermost).
+"""
+import ctypes
+import os
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libse2ot.so")
+
+SE2OT_OK = 0
+SE2OT_EINVAL = 1
+SE2OT_ENOMEM = 2
+SE2OT_ECUDA = 3
+SE2OT_ENONFINITE = 4
+SE2OT_ENOTCONV = 5
+STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENONFINITE", 5: "ENOTCONV",
+                6: "ETIMEOUT", 7: "EBUSY", 8: "ESHUTDOWN"}
+SE2OT_FP32 = 0
+SE2OT_BOUNDARY_ZERO = 0
+SE2OT_BOUNDARY_PERIODIC = 1
+SE2OT_FLAG_TIME_CONV = 1
+
+
+class se2ot_kernel_desc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("ntheta", ctypes.c_int),
+                ("radius", ctypes.c_int), ("w1", ctypes.c_double), ("w2", ctypes.c_double),
+                ("w3", ctypes.c_double), ("eps", ctypes.c_double), ("boundary", ctypes.c_int)]
+
+
+class se2ot_solve_opts(ctypes.Structure):
+    _fields_ = [("max_iters", ctypes.c_int), ("check_every", ctypes.c_int),
+                ("tol_viol", ctypes.c_double), ("precision", ctypes.c_int), ("flags", ctypes.c_int)]
+
+
+class se2ot_stats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("mass", ctypes.c_double), ("viol", ctypes.c_double),
+                ("ms", ctypes.c_double), ("voxel_iters_per_s", ctypes.c_double),
+                ("conv_ms", ctypes.c_double), ("conv_launches", ctypes.c_longlong),
+                ("kernel_launches", ctypes.c_longlong), ("redo_outputs", ctypes.c_longlong)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class SE2OTError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), message))
+        self.status = status
+
+
+_LIB = None
+
+
+def lib():
+    """Load libse2ot.so (built in-tree by paper_2402_15322_gb300.build)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libse2ot.so not found at %s; build it with "
+                          "`python -m paper_2402_15322_gb300.build`" % LIB_PATH)
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    L.se2ot_kernel_build.argtypes = [ctypes.POINTER(se2ot_kernel_desc), vp, ctypes.POINTER(vp)]
+    L.se2ot_kernel_destroy.argtypes = [vp]
+    L.se2ot_kernel_taps.argtypes = [vp, vp]
+    L.se2ot_apply.argtypes = [vp, vp, vp, i, vp]
+    L.se2ot_apply_log.argtypes = [vp, vp, vp, i, vp]
+    L.se2ot_barycenter.argtypes = [vp, i, vp, vp, ctypes.POINTER(se2ot_solve_opts), vp,
+                                   ctypes.POINTER(se2ot_stats), vp]
+    L.se2ot_interpolate.argtypes = [vp, vp, vp, d, ctypes.POINTER(se2ot_solve_opts), vp,
+                                    ctypes.POINTER(se2ot_stats), vp]
+    L.se2ot_last_error.restype = ctypes.c_char_p
+    L.se2ot_version.restype = ctypes.c_char_p
+    for name in ("se2ot_kernel_build", "se2ot_kernel_destroy", "se2ot_kernel_taps", "se2ot_apply",
+                 "se2ot_apply_log", "se2ot_barycenter", "se2ot_interpolate"):
+        getattr(L, name).restype = ctypes.c_int
+    _LIB = L
+    return L
+
+
+def _check(status):
+    if status != SE2OT_OK:
+        raise SE2OTError(status, se2ot_last_error())
+
+
+def _stream(stream=None):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t, dtype):
+    if t.dtype != dtype:
+        raise TypeError("expected %s, got %s" % (dtype, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def se2ot_last_error():
+    return lib().se2ot_last_error().decode()
+
+
+def se2ot_version():
+    return lib().se2ot_version().decode()
+
+
+class Kernel:
+    """Owner of an se2ot_kernel handle (tap tables and workspace on the current device)."""
+
+    def __init__(self, handle, desc):
+        self.handle = handle
+        self.desc = desc
+
+    @property
+    def shape(self):
+        d = self.desc
+        return (d.ny, d.nx, d.ntheta)
+
+    @property
+    def V(self):
+        d = self.desc
+        return d.nx * d.ny * d.ntheta
+
+    def close(self):
+        if self.handle:
+            lib().se2ot_kernel_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def make_desc(nx, ny, ntheta, radius, w=(1.0, 3.0, 0.5), eps=1e-3, periodic=False):
+    return se2ot_kernel_desc(int(nx), int(ny), int(ntheta), int(radius), float(w[0]), float(w[1]),
+                             float(w[2]), float(eps),
+                             SE2OT_BOUNDARY_PERIODIC if periodic else SE2OT_BOUNDARY_ZERO)
+
+
+def se2ot_kernel_build(desc, stream=None):
+    h = ctypes.c_void_p()
+    _check(lib().se2ot_kernel_build(ctypes.byref(desc), _stream(stream), ctypes.byref(h)))
+    return Kernel(h, desc)
+
+
+def se2ot_kernel_destroy(kernel):
+    kernel.close()
+
+
+def se2ot_kernel_taps(kernel):
+    """Tap table as a float32 CPU tensor [o, i, dy + r, dx + r] of log2 K."""
+    d = kernel.desc
+    D = 2 * d.radius + 1
+    out = torch.empty((d.ntheta, d.ntheta, D, D), dtype=torch.float32)
+    _check(lib().se2ot_kernel_taps(kernel.handle, ctypes.c_void_p(out.data_ptr())))
+    return out
+
+
+def se2ot_apply(kernel, f, out=None, stream=None):
+    """out = K * f for f of shape [batch, ny, nx, ntheta] (float32, CUDA)."""
+    if out is None:
+        out = torch.empty_like(f)
+    batch = f.numel() // kernel.V
+    _check(lib().se2ot_apply(kernel.handle, _ptr(f, torch.float32), _ptr(out, torch.float32), batch,
+                             _stream(stream)))
+    return out
+
+
+def se2ot_apply_log(kernel, lf, out=None, stream=None):
+    """out = log(K * exp(lf)) (float64, CUDA)."""
+    if out is None:
+        out = torch.empty_like(lf)
+    batch = lf.numel() // kernel.V
+    _check(lib().se2ot_apply_log(kernel.handle, _ptr(lf, torch.float64), _ptr(out, torch.float64), batch,
+                                 _stream(stream)))
+    return out
+
+
+def solve_opts(max_iters=100, check_every=0, tol_viol=0.0, precision=SE2OT_FP32, flags=0):
+    return se2ot_solve_opts(int(max_iters), int(check_every), float(tol_viol), int(precision), int(flags))
+
+
+def se2ot_barycenter(kernel, mu, lam, opts=None, out=None, stream=None, raise_on_error=True):
+    """Barycenter of mu [n, ny, nx, ntheta] (float32, CUDA or pinned/pageable CPU) with weights
+    lam (n floats).  Returns (bary, stats dict, status)."""
+    n = mu.shape[0]
+    if out is None:
+        out = torch.empty(mu.shape[1:], dtype=torch.float32, device=mu.device)
+    lam_c = (ctypes.c_double * n)(*[float(x) for x in lam])
+    st = se2ot_stats()
+    status = lib().se2ot_barycenter(kernel.handle, n, _ptr(mu, torch.float32), lam_c,
+                                    ctypes.byref(opts if opts is not None else solve_opts()),
+                                    _ptr(out, torch.float32), ctypes.byref(st), _stream(stream))
+    if raise_on_error:
+        _check(status)
+    return out, st.as_dict(), status
+
+
+def se2ot_interpolate(kernel, mu0, mu1, t, opts=None, out=None, stream=None, raise_on_error=True):
+    """Phi_t(mu0, mu1): the barycenter with weights (1 - t, t)."""
+    if out is None:
+        out = torch.empty_like(mu0)
+    st = se2ot_stats()
+    status = lib().se2ot_interpolate(kernel.handle, _ptr(mu0, torch.float32), _ptr(mu1, torch.float32),
+                                     float(t), ctypes.byref(opts if opts is not None else solve_opts()),
+                                     _ptr(out, torch.float32), ctypes.byref(st), _stream(stream))
+    if raise_on_error:
+        _check(status)
+    return out, st.as_dict(), status
