@@ -129,16 +129,35 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
-def peak_terms_per_s(sm_mhz=None):
-    """ALU ceiling of the log-domain convolution: each kernel term costs one MUFU ex2 and four
-    FP32 adds; with 16 ex2 results per SM per clock the MUFU pipe binds at
-    152 SMs x clock x 16 terms.  Uses the measured peak file's maximum SM clock."""
+MUFU_EX2_PER_SM_CLK = 32.0   # GB300 SFU: 32 ex2 results per SM per clock
+
+
+def peak_terms_per_s():
+    """ALU ceiling of the log-domain convolution.  Each kernel term costs one MUFU ex2 and four
+    FP32 adds; the MUFU pipe (32 ex2 per SM per clock) binds before the FP32 pipe (128 lanes per
+    SM per clock, 4 adds per term -> 32 terms).  Ceiling: 152 SMs x maximum SM clock x 32 terms.
+    The maximum SM clock comes from the measured-peaks file (2070 MHz)."""
     peaks = {}
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         peaks = json.load(open(p))
     mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    return 152 * mhz * 1e6 * 16.0
+    return 152 * mhz * 1e6 * MUFU_EX2_PER_SM_CLK
+
+
+def conv_traffic(kernel_name="conv_kernel<16, false>"):
+    """DRAM bytes per launch of the convolution from the committed ncu summary, if it was taken
+    on the current source of conv.cu (else None)."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "conv_kernel_traffic.json")
+    src = os.path.join(ROOT, "paper_2402_15322_gb300", "csrc", "conv.cu")
+    if not os.path.exists(p):
+        return None
+    rec = json.load(open(p))
+    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    if rec.get("conv_cu_sha256") != digest:
+        return None
+    return rec.get("dram_bytes_per_launch")
 
 
 def run_gpu(args):
@@ -160,7 +179,8 @@ def run_gpu(args):
     mu = mu_h.to(device)
     out = torch.empty((NY, NX, NT), dtype=torch.float32, device=device)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=device)   # > L2 (129 MB)
-    opts = se2ot.solve_opts(ITERS, flags=se2ot.SE2OT_FLAG_TIME_CONV)
+    iters = args.iters
+    opts = se2ot.solve_opts(iters, flags=se2ot.SE2OT_FLAG_TIME_CONV)
     stream = torch.cuda.current_stream()
 
     for _ in range(args.warmup):
@@ -172,6 +192,7 @@ def run_gpu(args):
     conv_launches = 0
     launches = 0
     redo = 0
+    evaluated = 0
     barrier(world, device)
     torch.cuda.synchronize()
     ev0 = torch.cuda.Event(enable_timing=True)
@@ -185,6 +206,7 @@ def run_gpu(args):
             conv_launches += st["conv_launches"]
             launches += st["kernel_launches"]
             redo += st["redo_outputs"]
+            evaluated += st["evaluated_terms"]
         ev1.record(stream)
         torch.cuda.synchronize()
     barrier(world, device)
@@ -194,7 +216,7 @@ def run_gpu(args):
     # end to end through the C ABI with pinned host buffers: copies inside the timed region
     mu_pin = mu_h.pin_memory()
     out_pin = torch.empty((NY, NX, NT), dtype=torch.float32).pin_memory()
-    opts_e2e = se2ot.solve_opts(ITERS)
+    opts_e2e = se2ot.solve_opts(iters)
     e2e_steps = max(1, min(args.steps, 3))
     barrier(world, device)
     torch.cuda.synchronize()
@@ -206,18 +228,19 @@ def run_gpu(args):
 
     result = None
     if rank == 0:
-        value = world * V * ITERS * args.steps / (elapsed_ms * 1e-3)
-        e2e_value = world * V * ITERS * e2e_steps / e2e_s
+        value = world * V * iters * args.steps / (elapsed_ms * 1e-3)
+        e2e_value = world * V * iters * e2e_steps / e2e_s
         avg_conv_s = conv_ms * 1e-3 / max(1, conv_launches)
         peak = peak_terms_per_s()
         achieved_tflops = CONV_FLOP_PER_LAUNCH / avg_conv_s / 1e12
         peak_tflops = 2.0 * peak / 1e12
+        eval_tflops = 2.0 * evaluated / max(1e-12, conv_ms * 1e-3) / 1e12
         result = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "grid": [NX, NY, NT], "radius": R, "measures": N_MEAS,
-                       "iterations": ITERS, "eps": EPS, "w": list(W),
+                       "iterations": iters, "eps": EPS, "w": list(W),
                        "inputs": "seeded coupled synthetic lifted densities",
                        "l2": "flushed before every step (256 MB write)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -226,10 +249,14 @@ def run_gpu(args):
             "gpu_launches": int(launches),
             "roofline": {"bound": "alu", "kernel": "conv_kernel<16> (log-domain group convolution)",
                          "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
-                         "frac": achieved_tflops / peak_tflops, "traffic": None,
+                         "frac": achieved_tflops / peak_tflops, "traffic": conv_traffic(),
                          "avg_launch_ms": avg_conv_s * 1e3, "launches": int(conv_launches),
                          "flop_per_launch": CONV_FLOP_PER_LAUNCH,
-                         "peak_basis": "152 SMs x max SM clock x 16 MUFU ex2/clk x 2 flop per term"},
+                         "peak_basis": "152 SMs x max SM clock x 32 MUFU ex2/clk x 2 flop per kernel term",
+                         "evaluated": {"achieved": eval_tflops, "frac": eval_tflops / peak_tflops,
+                                       "terms_per_launch": evaluated / max(1, conv_launches),
+                                       "note": "kernel terms actually computed; orientation pairs "
+                                               "below 2^-40 of the output are skipped"}},
             "solve": {"mass": mass, "viol": viol, "redo_outputs_timed": int(redo)},
         }
         cs = clocks.summary()
@@ -290,6 +317,8 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--iters", type=int, default=ITERS,
+                    help="Sinkhorn iterations per solve (profiling runs only; the metric uses 500)")
     args = ap.parse_args(argv)
     args.warmup = max(3, args.warmup)   # at least 3 untimed warm-up steps
     if args.impl == "reference":

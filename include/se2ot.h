@@ -106,7 +106,10 @@ typedef struct {
  *                    convolution launches and their number (0 otherwise)
  *   kernel_launches  kernels this call launched
  *   redo_outputs     convolution outputs whose first evaluation fell outside the safe range
- *                    of its shift and were recomputed exactly */
+ *                    of its shift and were recomputed exactly
+ *   evaluated_terms  kernel terms the convolutions evaluated; orientation pairs whose whole
+ *                    contribution lies below 2^-40 of the output are skipped, so this is at
+ *                    most 2 * iters * n * V * ntheta * (2r+1)^2 */
 typedef struct {
     int iters;
     double mass, viol, ms, voxel_iters_per_s;
@@ -114,6 +117,7 @@ typedef struct {
     long long conv_launches;
     long long kernel_launches;
     long long redo_outputs;
+    long long evaluated_terms;
 } se2ot_stats;
 
 /* Build the kernel for a grid: validates desc, evaluates the taps

@@ -3,10 +3,11 @@
 //
 // Each output c(g, o) = log2 sum_{i, dy, dx} 2^(lk[o][i][dy][dx] + in(g - (dx, dy), i)) is
 // evaluated as S + log2 sum 2^(term - S) with a per-output shift S (the output of the same
-// convolution in the previous Sinkhorn iteration, or in(g, o) when there is none).  Any S gives
-// the same value in exact arithmetic; a good S keeps every significant term a normal FP32
-// number.  When the sum lands outside [2^-24, 2^100] the shift was poor: the output is queued and
-// recomputed by redo_kernel with the exact maximum as shift, in FP64.
+// convolution in the previous Sinkhorn iteration, or the largest term from a MAXPASS launch of
+// this kernel when there is none).  Any S gives the same value in exact arithmetic; a good S keeps
+// the exponent argument of every significant term small, so that its FP32 rounding costs little
+// absolute precision.  When the sum lands outside [2^-24, 2^16] the shift was poor: the output is
+// queued and recomputed by redo_kernel with the exact maximum as shift, in FP64.
 //
 // Precision: inputs are FP64 base-2 logarithms.  They are split into FP32 hi + lo parts in
 // shared memory and each term is ((hi - S) + tap) + lo, so that the large common magnitude of
@@ -29,8 +30,8 @@ namespace {
 
 constexpr int TX = 32, TY = 8, XQ = 4;
 constexpr float SKIP_MARGIN = 64.f;   // log2 units below the shift
-constexpr float ACC_LO = -24.f;       // accepted range of log2(sum) around the shift
-constexpr float ACC_HI = 100.f;
+constexpr float ACC_LO = -24.f;       // accepted range of log2(sum) around the shift: beyond
+constexpr float ACC_HI = 16.f;        // +16 the exponent arguments lose FP32 absolute precision
 
 template <int NT>
 struct Cfg {
@@ -74,7 +75,7 @@ __device__ __forceinline__ void epilogue(const ConvArgs &a, long flat, double c)
     }
 }
 
-template <int NT>
+template <int NT, bool MAXPASS>
 __global__ void __launch_bounds__(Cfg<NT>::THREADS) conv_kernel(ConvArgs a)
 {
     constexpr int OQ = Cfg<NT>::OQ;
@@ -101,6 +102,7 @@ __global__ void __launch_bounds__(Cfg<NT>::THREADS) conv_kernel(ConvArgs a)
 
     float S[XQ][OQ], acc[XQ][OQ];
     bool valid[XQ];
+    unsigned evaluated = 0;   // warp-slices not skipped
 #pragma unroll
     for (int j = 0; j < XQ; ++j) {
         const int gx = x0 + xl + j;
@@ -108,13 +110,13 @@ __global__ void __launch_bounds__(Cfg<NT>::THREADS) conv_kernel(ConvArgs a)
 #pragma unroll
         for (int q = 0; q < OQ; ++q) {
             float s = 0.f;
-            if (valid[j]) {
+            if (!MAXPASS && valid[j]) {
                 const long flat = ((long)gy * nx + gx) * NT + o0 + q;
                 s = a.hint ? a.hint[b * V + flat] : (float)(in_b[flat] * a.in_scale);
                 if (!isfinite(s)) s = 0.f;  // a useless shift; the window check sends it to redo
             }
             S[j][q] = s;
-            acc[j][q] = 0.f;
+            acc[j][q] = MAXPASS ? -INFINITY : 0.f;
         }
     }
 
@@ -151,16 +153,20 @@ __global__ void __launch_bounds__(Cfg<NT>::THREADS) conv_kernel(ConvArgs a)
 #pragma unroll
         for (int w = 1; w < NWARP; ++w) hmax = fmaxf(hmax, red[w]);
 
-        // skip the slice when no term can reach 2^-64 of any shift of this warp
+        // skip the slice when no term can reach 2^-64 of any shift (MAXPASS: of the running
+        // maximum) of this warp
         bool need = false;
 #pragma unroll
         for (int q = 0; q < OQ; ++q) {
             const float bound = a.lkmax[(o0 + q) * NT + i] + hmax + 1.0f;
 #pragma unroll
-            for (int j = 0; j < XQ; ++j)
-                if (valid[j] && !(bound < S[j][q] - SKIP_MARGIN)) need = true;
+            for (int j = 0; j < XQ; ++j) {
+                const float ref = MAXPASS ? acc[j][q] : S[j][q];
+                if (valid[j] && !(bound < ref - SKIP_MARGIN)) need = true;
+            }
         }
         if (!__any_sync(0xffffffffu, need)) continue;
+        ++evaluated;
 
         for (int dyi = 0; dyi < D; ++dyi) {
             const int row = (yl + 2 * r - dyi) * HXP + xl + 2 * r;
@@ -194,13 +200,19 @@ __global__ void __launch_bounds__(Cfg<NT>::THREADS) conv_kernel(ConvArgs a)
                 for (int j = 0; j < XQ; ++j)
 #pragma unroll
                     for (int q = 0; q < OQ; ++q) {
-                        float t = (wh[j] - S[j][q]) + tq[q];
-                        t += wl[j];
-                        acc[j][q] += ex2(t);
+                        if constexpr (MAXPASS) {
+                            acc[j][q] = fmaxf(acc[j][q], wh[j] + tq[q]);
+                        } else {
+                            float t = (wh[j] - S[j][q]) + tq[q];
+                            t += wl[j];
+                            acc[j][q] += ex2(t);
+                        }
                     }
             }
         }
     }
+
+    if (lane == 0 && a.eval_count) atomicAdd(a.eval_count, (unsigned long long)evaluated);
 
 #pragma unroll
     for (int j = 0; j < XQ; ++j) {
@@ -209,6 +221,11 @@ __global__ void __launch_bounds__(Cfg<NT>::THREADS) conv_kernel(ConvArgs a)
 #pragma unroll
         for (int q = 0; q < OQ; ++q) {
             const long flat = b * V + ((long)gy * nx + gx) * NT + o0 + q;
+            if constexpr (MAXPASS) {
+                // the largest term (hi parts) becomes the shift of the summing pass
+                a.hint[flat] = acc[j][q];
+                continue;
+            }
             const float lacc = log2f(acc[j][q]);
             if (!(lacc >= ACC_LO && lacc <= ACC_HI)) {
                 const unsigned k = atomicAdd(a.redo_count, 1u);
@@ -270,7 +287,7 @@ __global__ void redo_kernel(ConvArgs a)
     if (blockIdx.x == 0 && threadIdx.x == 0 && a.redo_total) atomicAdd(a.redo_total, (unsigned long long)n);
 }
 
-template <int NT>
+template <int NT, bool MAXPASS>
 cudaError_t launch_conv_nt(const ConvArgs &a, cudaStream_t s)
 {
     const int r = a.r, D = 2 * r + 1;
@@ -278,13 +295,13 @@ cudaError_t launch_conv_nt(const ConvArgs &a, cudaStream_t s)
     const size_t smem = sizeof(float) * ((size_t)2 * HY * halo_pitch(HX) + (size_t)D * D * NT + 32);
     static size_t configured = 0;   // largest dynamic shared memory size granted so far
     if (smem > 48 * 1024 && smem > configured) {
-        cudaError_t e = cudaFuncSetAttribute(conv_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(conv_kernel<NT, MAXPASS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
         configured = smem;
     }
     dim3 grid((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY, a.batch);
-    conv_kernel<NT><<<grid, Cfg<NT>::THREADS, smem, s>>>(a);
+    conv_kernel<NT, MAXPASS><<<grid, Cfg<NT>::THREADS, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -297,24 +314,35 @@ cudaError_t launch_redo_nt(const ConvArgs &a, int max_blocks, cudaStream_t s)
 
 }  // namespace
 
+long long terms_per_warp_slice(int nt, int r)
+{
+    const int oq = nt >= 4 ? 4 : nt;
+    return 32LL * XQ * oq * (2 * r + 1) * (2 * r + 1);
+}
+
 size_t conv_smem_bytes(int nt, int r)
 {
     const int D = 2 * r + 1;
     return sizeof(float) * ((size_t)2 * (TY + 2 * r) * halo_pitch(TX + 2 * r) + (size_t)D * D * nt + 32);
 }
 
-cudaError_t launch_conv(const ConvArgs &a, cudaStream_t s)
+template <bool MAXPASS>
+cudaError_t launch_conv_mode(const ConvArgs &a, cudaStream_t s)
 {
     switch (a.nt) {
-    case 1: return launch_conv_nt<1>(a, s);
-    case 2: return launch_conv_nt<2>(a, s);
-    case 4: return launch_conv_nt<4>(a, s);
-    case 8: return launch_conv_nt<8>(a, s);
-    case 16: return launch_conv_nt<16>(a, s);
-    case 32: return launch_conv_nt<32>(a, s);
+    case 1: return launch_conv_nt<1, MAXPASS>(a, s);
+    case 2: return launch_conv_nt<2, MAXPASS>(a, s);
+    case 4: return launch_conv_nt<4, MAXPASS>(a, s);
+    case 8: return launch_conv_nt<8, MAXPASS>(a, s);
+    case 16: return launch_conv_nt<16, MAXPASS>(a, s);
+    case 32: return launch_conv_nt<32, MAXPASS>(a, s);
     default: return cudaErrorInvalidValue;
     }
 }
+
+cudaError_t launch_conv(const ConvArgs &a, cudaStream_t s) { return launch_conv_mode<false>(a, s); }
+
+cudaError_t launch_conv_max(const ConvArgs &a, cudaStream_t s) { return launch_conv_mode<true>(a, s); }
 
 cudaError_t launch_redo(const ConvArgs &a, int max_blocks, cudaStream_t s)
 {

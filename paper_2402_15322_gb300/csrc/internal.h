@@ -32,6 +32,7 @@ struct ConvArgs {
     int *redo_list;        // outputs to recompute exactly (flat index b*V + g*nt + o)
     unsigned *redo_count;  // entries in redo_list
     unsigned long long *redo_total;  // running total for statistics
+    unsigned long long *eval_count;  // warp-slices evaluated (not skipped), for statistics
     int nx, ny, nt, r, periodic, batch, epi;
 };
 
@@ -44,6 +45,10 @@ struct Taps {
 // Launchers (conv.cu / taps.cu).
 cudaError_t build_taps(const se2ot_kernel_desc &d, Taps &t, cudaStream_t s);
 cudaError_t launch_conv(const ConvArgs &a, cudaStream_t s);
+// Same tiling, writing the largest term of every output to a.hint (the shift of a later launch).
+cudaError_t launch_conv_max(const ConvArgs &a, cudaStream_t s);
+// Kernel terms behind one evaluated warp-slice (lanes x outputs per lane x taps).
+long long terms_per_warp_slice(int nt, int r);
 cudaError_t launch_redo(const ConvArgs &a, int max_blocks, cudaStream_t s);
 size_t conv_smem_bytes(int nt, int r);   // dynamic shared memory of one conv CTA
 

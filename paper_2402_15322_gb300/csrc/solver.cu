@@ -191,7 +191,9 @@ struct se2ot_kernel_s {
     int *redo = nullptr;
     size_t c_redo = 0;
     unsigned *counters = nullptr;           // [0] redo count
-    unsigned long long *redo_total = nullptr;
+    unsigned long long *redo_total = nullptr;   // [0] redo outputs, [1] evaluated warp-slices
+    float *hint_ws = nullptr;
+    size_t c_hint_ws = 0;
     double *partial = nullptr, *scal = nullptr;
     std::vector<cudaEvent_t> ev;
 };
@@ -245,6 +247,7 @@ ConvArgs conv_args(se2ot_kernel k, int batch, int epi)
     a.redo_list = k->redo;
     a.redo_count = k->counters;
     a.redo_total = k->redo_total;
+    a.eval_count = k->redo_total + 1;
     a.nx = k->d.nx;
     a.ny = k->d.ny;
     a.nt = k->d.ntheta;
@@ -295,11 +298,11 @@ se2ot_status se2ot_kernel_build(const se2ot_kernel_desc *desc, void *stream, se2
     cudaError_t e = cudaMalloc((void **)&k->taps.taps, ntap * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc((void **)&k->taps.lkmax, (size_t)desc->ntheta * desc->ntheta * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc((void **)&k->counters, 4 * sizeof(unsigned));
-    if (e == cudaSuccess) e = cudaMalloc((void **)&k->redo_total, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&k->redo_total, 2 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMalloc((void **)&k->partial, 2 * RB * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc((void **)&k->scal, 4 * sizeof(double));
     if (e == cudaSuccess) e = cudaMemsetAsync(k->counters, 0, 4 * sizeof(unsigned), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(k->redo_total, 0, sizeof(unsigned long long), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(k->redo_total, 0, 2 * sizeof(unsigned long long), s);
     if (e == cudaSuccess) e = build_taps(*desc, k->taps, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
@@ -314,7 +317,7 @@ se2ot_status se2ot_kernel_destroy(se2ot_kernel k)
 {
     if (!k) return SE2OT_OK;
     cudaDeviceSynchronize();
-    void *ptrs[] = {k->taps.taps, k->taps.lkmax, k->lmu, k->lv, k->lw, k->ld, k->L, k->lf, k->h1, k->h2,
+    void *ptrs[] = {k->taps.taps, k->taps.lkmax, k->lmu, k->lv, k->lw, k->ld, k->L, k->lf, k->h1, k->h2, k->hint_ws,
                     k->mu_stage, k->bary_stage, k->redo, k->counters, k->redo_total, k->partial, k->scal};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -349,9 +352,12 @@ se2ot_status se2ot_apply(se2ot_kernel k, const float *f, float *out, int batch, 
     CK(grow(k->redo, k->c_redo, nV), "cudaMalloc(redo)");
     lin_to_log2_kernel<<<grid_for((long)nV), 256, 0, s>>>(f, k->lf, (long)nV);
     CK(cudaGetLastError(), "lin_to_log2 launch");
+    CK(grow(k->hint_ws, k->c_hint_ws, nV), "cudaMalloc(hint)");
     ConvArgs a = conv_args(k, batch, EPI_LIN_OUT);
     a.in = k->lf;
+    a.hint = k->hint_ws;
     a.out32 = out;
+    CK(launch_conv_max(a, s), "conv max-pass launch");
     return run_conv(k, a, s, nullptr);
 }
 
@@ -362,11 +368,14 @@ se2ot_status se2ot_apply_log(se2ot_kernel k, const double *lf, double *lout, int
     if ((double)batch * k->V >= 2147483647.0) return fail(SE2OT_EINVAL, "batch*V too large");
     cudaStream_t s = (cudaStream_t)stream;
     CK(grow(k->redo, k->c_redo, (size_t)batch * k->V), "cudaMalloc(redo)");
+    CK(grow(k->hint_ws, k->c_hint_ws, (size_t)batch * k->V), "cudaMalloc(hint)");
     ConvArgs a = conv_args(k, batch, EPI_LOG_OUT);
     a.in = lf;
     a.in_scale = LOG2E;
+    a.hint = k->hint_ws;
     a.out64 = lout;
     a.out_scale = LN2;
+    CK(launch_conv_max(a, s), "conv max-pass launch");
     return run_conv(k, a, s, nullptr);
 }
 
@@ -431,7 +440,7 @@ se2ot_status se2ot_barycenter(se2ot_kernel k, int n, const float *mu, const doub
             k->ev.push_back(e);
         }
     }
-    CK(cudaMemsetAsync(k->redo_total, 0, sizeof(unsigned long long), s), "cudaMemsetAsync");
+    CK(cudaMemsetAsync(k->redo_total, 0, 2 * sizeof(unsigned long long), s), "cudaMemsetAsync");
 
     ConvArgs aw = conv_args(k, n, EPI_W);
     aw.in = k->lv;
@@ -479,10 +488,10 @@ se2ot_status se2ot_barycenter(se2ot_kernel k, int n, const float *mu, const doub
         CK(cudaMemcpyAsync(bary, bary_dev, (size_t)V * sizeof(float), cudaMemcpyDeviceToHost, s),
            "cudaMemcpyAsync(bary)");
     double h[2];
-    unsigned long long redo_total = 0;
+    unsigned long long counts[2] = {0, 0};
     CK(cudaMemcpyAsync(h, k->scal, sizeof h, cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync(stats)");
-    CK(cudaMemcpyAsync(&redo_total, k->redo_total, sizeof redo_total, cudaMemcpyDeviceToHost, s),
-       "cudaMemcpyAsync(redo)");
+    CK(cudaMemcpyAsync(counts, k->redo_total, sizeof counts, cudaMemcpyDeviceToHost, s),
+       "cudaMemcpyAsync(counters)");
     CK(cudaStreamSynchronize(s), "cudaStreamSynchronize");
     mass = h[0];
     viol = h[1];
@@ -495,7 +504,8 @@ se2ot_status se2ot_barycenter(se2ot_kernel k, int n, const float *mu, const doub
         stats->ms = ms;
         stats->voxel_iters_per_s = ms > 0 ? (double)V * it / (ms * 1e-3) : 0.0;
         stats->kernel_launches = launches;
-        stats->redo_outputs = (long long)redo_total;
+        stats->redo_outputs = (long long)counts[0];
+        stats->evaluated_terms = (long long)counts[1] * terms_per_warp_slice(k->d.ntheta, k->d.radius);
         if (timing) {
             double tot = 0.0;
             for (int j = 0; j < it; ++j)

@@ -44,7 +44,8 @@ class se2ot_stats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("mass", ctypes.c_double), ("viol", ctypes.c_double),
                 ("ms", ctypes.c_double), ("voxel_iters_per_s", ctypes.c_double),
                 ("conv_ms", ctypes.c_double), ("conv_launches", ctypes.c_longlong),
-                ("kernel_launches", ctypes.c_longlong), ("redo_outputs", ctypes.c_longlong)]
+                ("kernel_launches", ctypes.c_longlong), ("redo_outputs", ctypes.c_longlong),
+                ("evaluated_terms", ctypes.c_longlong)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
