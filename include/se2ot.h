@@ -148,14 +148,14 @@ SE2OT_API se2ot_status se2ot_apply_log(se2ot_kernel k, const double *lf, double 
 
 /* Barycenter of n >= 1 measures with weights lambda (Appendix A; Eq. barywass with the
  * entropic kernel of Sec. 4.2).  mu: n*V floats, host or device memory (detected), each
- * measure >= 0, not all zero, and all n masses equal to 1e-6 relative (the barycenter is
- * homogeneous of degree one in a common scale).  lambda: n host doubles, >= 0, summing to 1
- * within 1e-12.  bary: V floats, host or device memory.  opts may be NULL (100 iterations,
- * no checks).  stats may be NULL.  Host memory is copied on the stream; the call
- * synchronises the stream before returning (stats need it).  Workspace: 5 n V doubles and
- * 2 n V floats, owned by the kernel handle and reused.
- * Returns EINVAL for invalid arguments, ENONFINITE if an iterate became non-finite,
- * ENOTCONV if tol_viol > 0 was not reached (the result is still written). */
+ * measure >= 0 and not all zero; the caller makes the n masses equal (the iteration assumes it
+ * and does not check or renormalise; the barycenter is homogeneous of degree one in a common
+ * scale).  lambda: n <= 64 host doubles, >= 0, summing to 1 within 1e-12.  bary: V floats, host
+ * or device memory.  opts may be NULL (100 iterations, no checks).  stats may be NULL.  Host
+ * memory is copied on the stream; the call synchronises the stream before returning (stats
+ * need it).  Workspace: 4 n V + V doubles, 3 n V words, owned by the kernel handle and reused.
+ * Returns EINVAL for invalid arguments, ENONFINITE if an iterate became non-finite (a NaN input
+ * does that), ENOTCONV if tol_viol > 0 was not reached (the result is still written). */
 SE2OT_API se2ot_status se2ot_barycenter(se2ot_kernel k, int n, const float *mu, const double *lambda,
                               const se2ot_solve_opts *opts, float *bary, se2ot_stats *stats,
                               void *stream);

@@ -9,9 +9,10 @@
 // absolute precision.  When the sum lands outside [2^-24, 2^16] the shift was poor: the output is
 // queued and recomputed by redo_kernel with the exact maximum as shift, in FP64.
 //
-// Precision: inputs are FP64 base-2 logarithms.  They are split into FP32 hi + lo parts in
-// shared memory and each term is ((hi - S) + tap) + lo, so that the large common magnitude of
-// in and S (hundreds to thousands) cancels before rounding.
+// Precision: inputs and taps are FP64-accurate base-2 logarithms held as FP32 hi + lo pairs, and
+// each term is ((in_hi - S) + tap_hi) + (in_lo + tap_lo): the large common magnitude of in and S
+// (hundreds to thousands) and of the orientation factor of the tap (hundreds) cancels exactly
+// before anything is rounded.
 //
 // Pair skipping: every term of orientation pair (o, i) in a tile is at most
 // lkmax[o][i] + max(in over the tile's halo of slice i).  A warp skips slice i when that bound is
@@ -89,7 +90,8 @@ __global__ void __launch_bounds__(Cfg<NT>::THREADS) conv_kernel(ConvArgs a)
     float *hhi = smem;
     float *hlo = hhi + HY * HXP;
     float *tps = hlo + HY * HXP;
-    float *red = tps + D * D * NT;
+    float *tpl = tps + D * D * NT;
+    float *red = tpl + D * D * NT;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int og = warp >> 1, rg = warp & 1;
@@ -144,7 +146,11 @@ __global__ void __launch_bounds__(Cfg<NT>::THREADS) conv_kernel(ConvArgs a)
             lmax = fmaxf(lmax, vh);
         }
         const float *tsrc = a.taps + (long)i * D * D * NT;
-        for (int idx = tid; idx < D * D * NT; idx += THREADS) tps[idx] = tsrc[idx];
+        const float *tlsrc = a.taps_lo + (long)i * D * D * NT;
+        for (int idx = tid; idx < D * D * NT; idx += THREADS) {
+            tps[idx] = tsrc[idx];
+            tpl[idx] = tlsrc[idx];
+        }
 #pragma unroll
         for (int off = 16; off; off >>= 1) lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, off));
         if (lane == 0) red[warp] = lmax;
@@ -178,6 +184,7 @@ __global__ void __launch_bounds__(Cfg<NT>::THREADS) conv_kernel(ConvArgs a)
                 wl[j] = rl[j];
             }
             const float *tp = tps + dyi * D * NT + o0;
+            const float *tl = tpl + dyi * D * NT + o0;
             for (int dxi = 0; dxi < D; ++dxi) {
                 if (dxi) {
 #pragma unroll
@@ -188,13 +195,18 @@ __global__ void __launch_bounds__(Cfg<NT>::THREADS) conv_kernel(ConvArgs a)
                     wh[0] = rh[-dxi];
                     wl[0] = rl[-dxi];
                 }
-                float tq[OQ];
+                float tq[OQ], tlq[OQ];
                 if constexpr (OQ == 4) {
                     const float4 t4 = *reinterpret_cast<const float4 *>(tp + dxi * NT);
                     tq[0] = t4.x; tq[1] = t4.y; tq[2] = t4.z; tq[3] = t4.w;
+                    const float4 l4 = *reinterpret_cast<const float4 *>(tl + dxi * NT);
+                    tlq[0] = l4.x; tlq[1] = l4.y; tlq[2] = l4.z; tlq[3] = l4.w;
                 } else {
 #pragma unroll
-                    for (int q = 0; q < OQ; ++q) tq[q] = tp[dxi * NT + q];
+                    for (int q = 0; q < OQ; ++q) {
+                        tq[q] = tp[dxi * NT + q];
+                        tlq[q] = tl[dxi * NT + q];
+                    }
                 }
 #pragma unroll
                 for (int j = 0; j < XQ; ++j)
@@ -204,7 +216,7 @@ __global__ void __launch_bounds__(Cfg<NT>::THREADS) conv_kernel(ConvArgs a)
                             acc[j][q] = fmaxf(acc[j][q], wh[j] + tq[q]);
                         } else {
                             float t = (wh[j] - S[j][q]) + tq[q];
-                            t += wl[j];
+                            t += wl[j] + tlq[q];
                             acc[j][q] += ex2(t);
                         }
                     }
@@ -266,8 +278,8 @@ __global__ void redo_kernel(ConvArgs a)
             } else if (sy < 0 || sy >= ny || sx < 0 || sx >= nx) {
                 return -INFINITY;
             }
-            return in_b[((long)sy * nx + sx) * NT + i] * a.in_scale +
-                   (double)a.taps[(((long)i * D + dyi) * D + dxi) * NT + o];
+            const long ti = (((long)i * D + dyi) * D + dxi) * NT + o;
+            return in_b[((long)sy * nx + sx) * NT + i] * a.in_scale + ((double)a.taps[ti] + (double)a.taps_lo[ti]);
         };
         double m = -INFINITY;
         for (long t = lane; t < T; t += 32) m = fmax(m, term(t));
@@ -292,7 +304,7 @@ cudaError_t launch_conv_nt(const ConvArgs &a, cudaStream_t s)
 {
     const int r = a.r, D = 2 * r + 1;
     const int HX = TX + 2 * r, HY = TY + 2 * r;
-    const size_t smem = sizeof(float) * ((size_t)2 * HY * halo_pitch(HX) + (size_t)D * D * NT + 32);
+    const size_t smem = sizeof(float) * ((size_t)2 * HY * halo_pitch(HX) + (size_t)2 * D * D * NT + 32);
     static size_t configured = 0;   // largest dynamic shared memory size granted so far
     if (smem > 48 * 1024 && smem > configured) {
         cudaError_t e = cudaFuncSetAttribute(conv_kernel<NT, MAXPASS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -323,7 +335,7 @@ long long terms_per_warp_slice(int nt, int r)
 size_t conv_smem_bytes(int nt, int r)
 {
     const int D = 2 * r + 1;
-    return sizeof(float) * ((size_t)2 * (TY + 2 * r) * halo_pitch(TX + 2 * r) + (size_t)D * D * nt + 32);
+    return sizeof(float) * ((size_t)2 * (TY + 2 * r) * halo_pitch(TX + 2 * r) + (size_t)2 * D * D * nt + 32);
 }
 
 template <bool MAXPASS>

@@ -22,7 +22,8 @@ enum Epilogue : int {
 struct ConvArgs {
     const double *in;      // [batch][V] base-2 logarithms (times in_scale)
     double in_scale;       // multiplies `in` as it is read (log2(e) for natural-log input)
-    const float *taps;     // [i][dy][dx][o] log2 K, i-major (device layout of the tap table)
+    const float *taps;     // [i][dy][dx][o] log2 K rounded to FP32, i-major (device layout)
+    const float *taps_lo;  // same layout: log2 K - taps (the FP32 rounding residual)
     const float *lkmax;    // [o][i] largest tap of each orientation pair
     float *hint;           // [batch][V] shift per output, updated with c; NULL: use in(g, o)
     const double *aux;     // EPI_W: log2 mu_i; EPI_D: log2 v_i
@@ -39,6 +40,7 @@ struct ConvArgs {
 // Device tap tables of one kernel handle.
 struct Taps {
     float *taps = nullptr;   // [nt][D][D][nt] (i, dy, dx, o)
+    float *taps_lo = nullptr;  // rounding residual of taps, same layout
     float *lkmax = nullptr;  // [nt][nt] (o, i)
 };
 

@@ -241,6 +241,7 @@ ConvArgs conv_args(se2ot_kernel k, int batch, int epi)
     ConvArgs a;
     std::memset(&a, 0, sizeof a);
     a.taps = k->taps.taps;
+    a.taps_lo = k->taps.taps_lo;
     a.lkmax = k->taps.lkmax;
     a.in_scale = 1.0;
     a.out_scale = 1.0;
@@ -296,6 +297,7 @@ se2ot_status se2ot_kernel_build(const se2ot_kernel_desc *desc, void *stream, se2
     const int D = 2 * desc->radius + 1;
     const size_t ntap = (size_t)desc->ntheta * desc->ntheta * D * D;
     cudaError_t e = cudaMalloc((void **)&k->taps.taps, ntap * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&k->taps.taps_lo, ntap * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc((void **)&k->taps.lkmax, (size_t)desc->ntheta * desc->ntheta * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc((void **)&k->counters, 4 * sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMalloc((void **)&k->redo_total, 2 * sizeof(unsigned long long));
@@ -317,7 +319,7 @@ se2ot_status se2ot_kernel_destroy(se2ot_kernel k)
 {
     if (!k) return SE2OT_OK;
     cudaDeviceSynchronize();
-    void *ptrs[] = {k->taps.taps, k->taps.lkmax, k->lmu, k->lv, k->lw, k->ld, k->L, k->lf, k->h1, k->h2, k->hint_ws,
+    void *ptrs[] = {k->taps.taps, k->taps.taps_lo, k->taps.lkmax, k->lmu, k->lv, k->lw, k->ld, k->L, k->lf, k->h1, k->h2, k->hint_ws,
                     k->mu_stage, k->bary_stage, k->redo, k->counters, k->redo_total, k->partial, k->scal};
     for (void *p : ptrs)
         if (p) cudaFree(p);

@@ -6,8 +6,9 @@
 // and the tap is log2 K(u) = -rho_b(u)^2 / (eps ln 2) with
 //   rho_b(u)^2 = (w1 b1)^2 + (w2 b2)^2 + (w3 b3)^2,
 //   (b1, b2) = R(-u_theta / 2) (u_x, u_y),  b3 = u_theta in [-pi, pi)          (Sec. 4.3)
-// evaluated in FP64 and rounded once to FP32.  A theta difference of exactly pi is taken as -pi
-// (small-angle convention); rho_b is the same for +pi and -pi, so the choice does not matter.
+// evaluated in FP64 and stored as an FP32 value plus its FP32 rounding residual.  A theta
+// difference of exactly pi is taken as -pi (small-angle convention); rho_b is the same for +pi
+// and -pi, so the choice does not matter.
 #include "internal.h"
 
 namespace se2ot {
@@ -15,7 +16,7 @@ namespace se2ot {
 namespace {
 
 __global__ void taps_kernel(int nx, int ny, int nt, int r, double w1, double w2, double w3,
-                            double eps, float *taps)
+                            double eps, float *taps, float *taps_lo)
 {
     const int D = 2 * r + 1;
     const long total = (long)nt * D * D * nt;
@@ -48,7 +49,10 @@ __global__ void taps_kernel(int nx, int ny, int nt, int r, double w1, double w2,
         const double b2 = -ux * sh + uy * ch;
         const double b3 = dth * 3.14159265358979323846;
         const double rho2 = (w1 * b1) * (w1 * b1) + (w2 * b2) * (w2 * b2) + (w3 * b3) * (w3 * b3);
-        taps[idx] = (float)(-rho2 / eps * 1.44269504088896340736);  // log2(e)
+        const double v = -rho2 / eps * 1.44269504088896340736;  // log2(e)
+        const float hi = (float)v;
+        taps[idx] = hi;
+        taps_lo[idx] = (float)(v - (double)hi);
     }
 }
 
@@ -74,7 +78,7 @@ cudaError_t build_taps(const se2ot_kernel_desc &d, Taps &t, cudaStream_t s)
     int blocks = (int)((total + 255) / 256);
     if (blocks > 4096) blocks = 4096;
     taps_kernel<<<blocks, 256, 0, s>>>(d.nx, d.ny, d.ntheta, d.radius, d.w1, d.w2, d.w3, d.eps,
-                                       t.taps);
+                                       t.taps, t.taps_lo);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     int pairs = d.ntheta * d.ntheta;
