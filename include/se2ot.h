@@ -167,6 +167,36 @@ SE2OT_API se2ot_status se2ot_interpolate(se2ot_kernel k, const float *mu0, const
                                const se2ot_solve_opts *opts, float *out, se2ot_stats *stats,
                                void *stream);
 
+/* Size of the device array behind se2ot_barycenter_noalloc: 16 MiB on every GPU that loads the
+ * library, held until the process exits. */
+#define SE2OT_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/* se2ot_barycenter for callers that cannot allocate device memory.  The paper has no
+ * counterpart: this is a deployment variant of the same solve.
+ *
+ * Some callers may not call cudaMalloc: a host application or framework that owns the device's
+ * whole memory budget through its own allocator, a latency-critical loop that cannot afford
+ * cudaMalloc's implicit synchronisation, a plugin restricted to the buffers it is given.  They
+ * cannot create an se2ot_kernel either, because building one allocates its tap table and
+ * workspace.  This call takes the kernel descriptor itself and keeps the tap table and every
+ * scaling vector in one statically allocated device array of SE2OT_NOALLOC_SCRATCH_BYTES; it
+ * calls no cudaMalloc, cudaFree or other allocating routine.
+ *
+ * Arguments as in se2ot_barycenter, except: desc replaces the kernel handle; mu (n*V floats) and
+ * bary (V floats) must be device memory (EINVAL otherwise: nothing is staged); stats->conv_ms is
+ * not measured (0).  A problem whose tap table and workspace need more than the array
+ * (2 ntheta^2 (2r+1)^2 + ntheta^2 floats, 4 n V + V doubles, 3 n V words, plus 4 KiB) is
+ * rejected with EINVAL and a message giving the size; e.g. n = 4 measures on 64 x 64 x 16 fit,
+ * 128 x 128 x 16 does not.
+ *
+ * The first call on each device looks up the array's device address (cudaGetSymbolAddress) and
+ * caches it; make that first call before any stream capture.  Every call shares the one array
+ * and finds the previous call's contents in it; it re-initialises all it reads.  Calls whose GPU
+ * work overlaps (other threads, other streams) race on the array: serialise them. */
+SE2OT_API se2ot_status se2ot_barycenter_noalloc(const se2ot_kernel_desc *desc, int n, const float *mu,
+                                                const double *lambda, const se2ot_solve_opts *opts,
+                                                float *bary, se2ot_stats *stats, void *stream);
+
 /* Message for the calling host thread's most recent error ("" if none).  The pointer stays
  * valid until the thread's next failing call. */
 SE2OT_API const char *se2ot_last_error(void);

@@ -54,4 +54,8 @@ long long terms_per_warp_slice(int nt, int r);
 cudaError_t launch_redo(const ConvArgs &a, int max_blocks, cudaStream_t s);
 size_t conv_smem_bytes(int nt, int r);   // dynamic shared memory of one conv CTA
 
+// Host helpers of solver.cu shared with other entry points.
+se2ot_status validate_kernel_desc(const se2ot_kernel_desc *d);   // EINVAL + message, or OK
+void set_last_error(const char *msg);                            // se2ot_last_error() text
+
 }  // namespace se2ot

@@ -274,6 +274,14 @@ se2ot_status run_conv(se2ot_kernel k, const ConvArgs &a, cudaStream_t s, long lo
 
 }  // namespace
 
+namespace se2ot {
+
+se2ot_status validate_kernel_desc(const se2ot_kernel_desc *d) { return validate_desc(d); }
+
+void set_last_error(const char *msg) { g_last_error = msg; }
+
+}  // namespace se2ot
+
 extern "C" {
 
 const char *se2ot_last_error(void) { return g_last_error.c_str(); }

@@ -79,10 +79,13 @@ def lib():
                                    ctypes.POINTER(se2ot_stats), vp]
     L.se2ot_interpolate.argtypes = [vp, vp, vp, d, ctypes.POINTER(se2ot_solve_opts), vp,
                                     ctypes.POINTER(se2ot_stats), vp]
+    L.se2ot_barycenter_noalloc.argtypes = [ctypes.POINTER(se2ot_kernel_desc), i, vp, vp,
+                                           ctypes.POINTER(se2ot_solve_opts), vp,
+                                           ctypes.POINTER(se2ot_stats), vp]
     L.se2ot_last_error.restype = ctypes.c_char_p
     L.se2ot_version.restype = ctypes.c_char_p
     for name in ("se2ot_kernel_build", "se2ot_kernel_destroy", "se2ot_kernel_taps", "se2ot_apply",
-                 "se2ot_apply_log", "se2ot_barycenter", "se2ot_interpolate"):
+                 "se2ot_apply_log", "se2ot_barycenter", "se2ot_interpolate", "se2ot_barycenter_noalloc"):
         getattr(L, name).restype = ctypes.c_int
     _LIB = L
     return L
@@ -217,6 +220,27 @@ def se2ot_interpolate(kernel, mu0, mu1, t, opts=None, out=None, stream=None, rai
     status = lib().se2ot_interpolate(kernel.handle, _ptr(mu0, torch.float32), _ptr(mu1, torch.float32),
                                      float(t), ctypes.byref(opts if opts is not None else solve_opts()),
                                      _ptr(out, torch.float32), ctypes.byref(st), _stream(stream))
+    if raise_on_error:
+        _check(status)
+    return out, st.as_dict(), status
+
+
+NOALLOC_SCRATCH_BYTES = 16 << 20
+
+
+def se2ot_barycenter_noalloc(desc, mu, lam, opts=None, out=None, stream=None, raise_on_error=True):
+    """Barycenter without any device allocation by the library (for callers that cannot
+    allocate): mu [n, ny, nx, ntheta] and out must be CUDA tensors; the tap table and the
+    workspace live in the library's static 16 MiB device array, shared by every call.
+    Returns (bary, stats dict, status)."""
+    n = mu.shape[0]
+    if out is None:
+        out = torch.empty(mu.shape[1:], dtype=torch.float32, device=mu.device)
+    lam_c = (ctypes.c_double * n)(*[float(x) for x in lam])
+    st = se2ot_stats()
+    status = lib().se2ot_barycenter_noalloc(ctypes.byref(desc), n, _ptr(mu, torch.float32), lam_c,
+                                            ctypes.byref(opts if opts is not None else solve_opts()),
+                                            _ptr(out, torch.float32), ctypes.byref(st), _stream(stream))
     if raise_on_error:
         _check(status)
     return out, st.as_dict(), status
