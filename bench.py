@@ -145,17 +145,17 @@ def peak_terms_per_s():
     return 152 * mhz * 1e6 * MUFU_EX2_PER_SM_CLK
 
 
-def conv_traffic(kernel_name="conv_kernel<16, false>"):
+def conv_traffic():
     """DRAM bytes per launch of the convolution from the committed ncu summary, if it was taken
     on the current source of conv.cu (else None)."""
     import hashlib
     p = os.path.join(ROOT, "profiles", "conv_kernel_traffic.json")
-    src = os.path.join(ROOT, "paper_2402_15322_gb300", "csrc", "conv.cu")
+    src = os.path.join(ROOT, "paper_2402_15322_gb300", "csrc", "conv_tile.cuh")
     if not os.path.exists(p):
         return None
     rec = json.load(open(p))
-    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    if rec.get("conv_cu_sha256") != digest:
+    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()   # counters only valid for this source
+    if rec.get("conv_tile_cuh_sha256") != digest:
         return None
     return rec.get("dram_bytes_per_launch")
 
@@ -247,7 +247,7 @@ def run_gpu(args):
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(N_MEAS * V * 4),
                     "d2h_bytes_per_step": int(V * 4)},
             "gpu_launches": int(launches),
-            "roofline": {"bound": "alu", "kernel": "conv_kernel<16> (log-domain group convolution)",
+            "roofline": {"bound": "alu", "kernel": "conv_tile_kernel<10, false> (+ tile-max pre-pass): log-domain group convolution",
                          "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
                          "frac": achieved_tflops / peak_tflops, "traffic": conv_traffic(),
                          "avg_launch_ms": avg_conv_s * 1e3, "launches": int(conv_launches),

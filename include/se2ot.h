@@ -72,8 +72,8 @@ typedef enum {
     SE2OT_BOUNDARY_PERIODIC = 1  /* spatial indices wrap (theta always wraps)               */
 } se2ot_boundary;
 
-/* Grid, metric and kernel.  Valid ranges: nx, ny >= 2*radius + 1; radius >= 0;
- * 1 <= ntheta <= 32 and ntheta in {1, 2, 4, 8, 16, 32}; w1, w2, w3 > 0; eps > 0. */
+/* Grid, metric and kernel.  Valid ranges: nx, ny >= 2*radius + 1; 0 <= radius <= 16;
+ * 1 <= ntheta <= 64; w1, w2, w3 > 0; eps > 0. */
 typedef struct {
     int nx, ny, ntheta, radius;
     double w1, w2, w3, eps;
@@ -107,9 +107,10 @@ typedef struct {
  *   kernel_launches  kernels this call launched
  *   redo_outputs     convolution outputs whose first evaluation fell outside the safe range
  *                    of its shift and were recomputed exactly
- *   evaluated_terms  kernel terms the convolutions evaluated; orientation pairs whose whole
- *                    contribution lies below 2^-40 of the output are skipped, so this is at
- *                    most 2 * iters * n * V * ntheta * (2r+1)^2 */
+ *   evaluated_terms  kernel terms the convolutions evaluated; orientation pairs and kernel rows
+ *                    whose whole contribution lies below 2^-40 of the output are skipped, so
+ *                    this is at most 2 * iters * n * V * ntheta * (2r+1)^2 (counted per 32x32
+ *                    tile, ragged tiles in full) */
 typedef struct {
     int iters;
     double mass, viol, ms, voxel_iters_per_s;
@@ -122,7 +123,8 @@ typedef struct {
 
 /* Build the kernel for a grid: validates desc, evaluates the taps
  * log2 K = -rho_b(h^-1 g)^2 / (eps ln 2) for every orientation pair and offset on the device
- * in FP64 (Sec. 4.3 Eq. rho_b, Sec. 4.2 kernel definition) and stores them in FP32.
+ * in FP64 (Sec. 4.3 Eq. rho_b, Sec. 4.2 kernel definition), kept as the exact FP64 orientation
+ * factor plus the spatial part as FP32 value + FP32 rounding residual.
  * Returns EINVAL for an invalid desc, ENOMEM/ECUDA on device failure.  The handle must be
  * released with se2ot_kernel_destroy.  Synchronises `stream` before returning. */
 SE2OT_API se2ot_status se2ot_kernel_build(const se2ot_kernel_desc *desc, void *stream, se2ot_kernel *out);

@@ -1,0 +1,20 @@
+// conv_r_a.cu -- instantiations of the tiled log-domain convolution for radii 0..5
+// (split across files so that they compile in parallel).
+#include "conv_tile.cuh"
+
+namespace se2ot {
+
+bool launch_tile_a(int r, bool maxpass, const ConvArgs &a, cudaStream_t s, cudaError_t *err)
+{
+    switch (r) {
+    case 0: *err = maxpass ? tile::launch_tile<0, true>(a, s) : tile::launch_tile<0, false>(a, s); return true;
+    case 1: *err = maxpass ? tile::launch_tile<1, true>(a, s) : tile::launch_tile<1, false>(a, s); return true;
+    case 2: *err = maxpass ? tile::launch_tile<2, true>(a, s) : tile::launch_tile<2, false>(a, s); return true;
+    case 3: *err = maxpass ? tile::launch_tile<3, true>(a, s) : tile::launch_tile<3, false>(a, s); return true;
+    case 4: *err = maxpass ? tile::launch_tile<4, true>(a, s) : tile::launch_tile<4, false>(a, s); return true;
+    case 5: *err = maxpass ? tile::launch_tile<5, true>(a, s) : tile::launch_tile<5, false>(a, s); return true;
+    default: return false;
+    }
+}
+
+}  // namespace se2ot

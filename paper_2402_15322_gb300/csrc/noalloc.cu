@@ -93,10 +93,20 @@ struct Lam {
     double v[64];
 };
 
-__global__ void na_init_kernel(const float *mu, double *lmu, double *lv, float *h1, float *h2, long n)
+// slice-major index e = ((b*nt + t)*ny + y)*nx + x  ->  caller index ((b*ny + y)*nx + x)*nt + t
+__device__ __forceinline__ long na_user_index(long e, int nx, int ny, int nt)
+{
+    const long plane = (long)nx * ny;
+    const long bt = e / plane, p = e - bt * plane;
+    const long b = bt / nt, t = bt - b * nt;
+    return (b * plane + p) * nt + t;
+}
+
+__global__ void na_init_kernel(const float *mu, double *lmu, double *lv, float *h1, float *h2, long n, int nx,
+                               int ny, int nt)
 {
     for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
-        const double l = log2((double)mu[e]);
+        const double l = log2((double)mu[na_user_index(e, nx, ny, nt)]);
         lmu[e] = l;
         lv[e] = 0.0;
         h1[e] = 0.f;
@@ -115,10 +125,10 @@ __global__ void na_update_kernel(double *lv, const double *ld, double *L, Lam la
     }
 }
 
-__global__ void na_finalize_kernel(const double *L, float *bary, long V)
+__global__ void na_finalize_kernel(const double *L, float *bary, long V, int nx, int ny, int nt)
 {
     for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < V; g += (long)gridDim.x * blockDim.x)
-        bary[g] = (float)exp2(L[g]);
+        bary[na_user_index(g, nx, ny, nt)] = (float)exp2(L[g]);
 }
 
 constexpr int NRB = 256, NRT = 256;
@@ -218,13 +228,17 @@ extern "C" se2ot_status se2ot_barycenter_noalloc(const se2ot_kernel_desc *desc, 
     const int nt = desc->ntheta, D = 2 * desc->radius + 1;
     const long V = (long)desc->nx * desc->ny * nt;
     const size_t nV = (size_t)n * V;
-    const size_t ntap = (size_t)nt * nt * D * D;
+    const size_t npair = (size_t)nt * nt;
+    const size_t ntmax = (size_t)n * nt * conv_tiles(desc->nx, desc->ny);
+    if ((double)n * nt > 65535.0) return nfail(SE2OT_EINVAL, "n*ntheta too large");
 
     // Lay out the scratch array; first a dry run to size it.
     Carver dry{nullptr};
-    dry.take<float>(ntap);
-    dry.take<float>(ntap);
-    dry.take<float>((size_t)nt * nt);
+    dry.take<double>(npair);
+    dry.take<float>(npair * D * D);
+    dry.take<float>(npair * D * D);
+    dry.take<float>(npair * D);
+    dry.take<float>(ntmax);
     for (int k = 0; k < 4; ++k) dry.take<double>(nV);
     dry.take<double>((size_t)V);
     dry.take<float>(nV);
@@ -243,9 +257,11 @@ extern "C" se2ot_status se2ot_barycenter_noalloc(const se2ot_kernel_desc *desc, 
     if (st != SE2OT_OK) return st;
     Carver c{base};
     Taps taps;
-    taps.taps = c.take<float>(ntap);
-    taps.taps_lo = c.take<float>(ntap);
-    taps.lkmax = c.take<float>((size_t)nt * nt);
+    taps.ltheta = c.take<double>(npair);
+    taps.ls = c.take<float>(npair * D * D);
+    taps.ls_lo = c.take<float>(npair * D * D);
+    taps.lsrow = c.take<float>(npair * D);
+    float *tmax = c.take<float>(ntmax);
     double *lmu = c.take<double>(nV), *lv = c.take<double>(nV), *lw = c.take<double>(nV), *ld = c.take<double>(nV);
     double *L = c.take<double>((size_t)V);
     float *h1 = c.take<float>(nV), *h2 = c.take<float>(nV);
@@ -263,15 +279,18 @@ extern "C" se2ot_status se2ot_barycenter_noalloc(const se2ot_kernel_desc *desc, 
     // everything read below is (re)initialised here: the array keeps the previous call's values
     NCK(cudaMemsetAsync(totals, 0, 2 * sizeof(unsigned long long), s), "cudaMemsetAsync");
     NCK(build_taps(*desc, taps, s), "tap build");
-    na_init_kernel<<<na_grid((long)nV), 256, 0, s>>>(mu, lmu, lv, h1, h2, (long)nV);
+    na_init_kernel<<<na_grid((long)nV), 256, 0, s>>>(mu, lmu, lv, h1, h2, (long)nV, desc->nx, desc->ny, nt);
     NCK(cudaGetLastError(), "init launch");
     long long launches = 3;
 
     ConvArgs aw;
     std::memset(&aw, 0, sizeof aw);
-    aw.taps = taps.taps;
-    aw.taps_lo = taps.taps_lo;
-    aw.lkmax = taps.lkmax;
+    aw.ltheta = taps.ltheta;
+    aw.ls = taps.ls;
+    aw.ls_lo = taps.ls_lo;
+    aw.lsrow = taps.lsrow;
+    aw.tmax = tmax;
+    aw.tmax_w = tmax;
     aw.in_scale = 1.0;
     aw.out_scale = 1.0;
     aw.redo_list = redo;
@@ -303,7 +322,7 @@ extern "C" se2ot_status se2ot_barycenter_noalloc(const se2ot_kernel_desc *desc, 
             NCK(cudaMemsetAsync(count, 0, sizeof(unsigned), s), "cudaMemsetAsync");
             NCK(launch_conv(*a, s), "conv launch");
             NCK(launch_redo(*a, 2 * sms, s), "redo launch");
-            launches += 2;
+            launches += 3;
         }
         na_update_kernel<<<na_grid(V), 256, 0, s>>>(lv, ld, L, lam, n, V);
         NCK(cudaGetLastError(), "update launch");
@@ -322,7 +341,7 @@ extern "C" se2ot_status se2ot_barycenter_noalloc(const se2ot_kernel_desc *desc, 
             }
         }
     }
-    na_finalize_kernel<<<na_grid(V), 256, 0, s>>>(L, bary, V);
+    na_finalize_kernel<<<na_grid(V), 256, 0, s>>>(L, bary, V, desc->nx, desc->ny, nt);
     na_stats_partial<<<NRB, NRT, 0, s>>>(L, ld, lam, n, V, partial);
     na_stats_final<<<1, NRT, 0, s>>>(partial, scal);
     NCK(cudaGetLastError(), "finalize launch");
@@ -342,7 +361,7 @@ extern "C" se2ot_status se2ot_barycenter_noalloc(const se2ot_kernel_desc *desc, 
         stats->voxel_iters_per_s = ms > 0 ? (double)V * it / (ms * 1e-3) : 0.0;
         stats->kernel_launches = launches;
         stats->redo_outputs = (long long)counts[0];
-        stats->evaluated_terms = (long long)counts[1] * terms_per_warp_slice(nt, desc->radius);
+        stats->evaluated_terms = (long long)counts[1];
     }
     if (!std::isfinite(h[0]) || !std::isfinite(h[1]))
         return nfail(SE2OT_ENONFINITE, "non-finite iterate (mass=%g, viol=%g)", h[0], h[1]);

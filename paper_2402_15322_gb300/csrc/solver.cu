@@ -7,7 +7,8 @@
 //   conv EPI_D   ld_i = lv_i + log2(K * 2^lw_i)           d_i = v_i (K w_i)
 //   redo
 //   update       L = sum_i lambda_i ld_i ; lv_i += L - ld_i  mu = prod d_i^lambda_i ; v_i *= mu/d_i
-// Every scaling vector is a base-2 logarithm in FP64; the barycenter is 2^L.
+// Every scaling vector is a base-2 logarithm in FP64, stored slice-major ([i][theta][y][x]); the
+// caller's arrays are [i][y][x][theta] and are converted on the way in and out.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -56,18 +57,36 @@ constexpr double LOG2E = 1.44269504088896340736;
 constexpr double LN2 = 0.69314718055994530942;
 
 // ------------------------------------------------------------------ elementwise kernels
-__global__ void lin_to_log2_kernel(const float *f, double *out, long n)
+// Slice-major index e = ((b*nt + t)*ny + y)*nx + x  <->  caller index ((b*ny + y)*nx + x)*nt + t.
+__device__ __forceinline__ long user_index(long e, int nx, int ny, int nt)
+{
+    const long plane = (long)nx * ny;
+    const long bt = e / plane, p = e - bt * plane;
+    const long b = bt / nt, t = bt - b * nt;
+    return (b * plane + p) * nt + t;
+}
+
+// lf = log2 f (apply): caller layout float -> slice-major FP64
+__global__ void lin_to_log2_kernel(const float *f, double *out, long n, int nx, int ny, int nt)
 {
     for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x)
-        out[e] = log2((double)f[e]);
+        out[e] = log2((double)f[user_index(e, nx, ny, nt)]);
+}
+
+// apply_log: caller layout FP64 -> slice-major FP64 (natural logs; the kernel scales them)
+__global__ void to_slices_kernel(const double *f, double *out, long n, int nx, int ny, int nt)
+{
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x)
+        out[e] = f[user_index(e, nx, ny, nt)];
 }
 
 // lmu = log2 mu; lv = 0 (v = 1); hint of the first w-convolution 0 (its input is all zeros);
 // hint of the first d-convolution log2 mu (K w ~ w ~ mu when v = 1).
-__global__ void init_kernel(const float *mu, double *lmu, double *lv, float *h1, float *h2, long n)
+__global__ void init_kernel(const float *mu, double *lmu, double *lv, float *h1, float *h2, long n, int nx,
+                            int ny, int nt)
 {
     for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
-        const double l = log2((double)mu[e]);
+        const double l = log2((double)mu[user_index(e, nx, ny, nt)]);
         lmu[e] = l;
         lv[e] = 0.0;
         h1[e] = 0.f;
@@ -92,10 +111,10 @@ __global__ void update_kernel(double *lv, const double *ld, double *L, Lambdas l
     }
 }
 
-__global__ void finalize_kernel(const double *L, float *bary, long V)
+__global__ void finalize_kernel(const double *L, float *bary, long V, int nx, int ny, int nt)
 {
     for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < V; g += (long)gridDim.x * blockDim.x)
-        bary[g] = (float)exp2(L[g]);
+        bary[user_index(g, nx, ny, nt)] = (float)exp2(L[g]);
 }
 
 // Deterministic FP64 reductions: a fixed grid of RB blocks, each summing a fixed strided subset
@@ -195,6 +214,8 @@ struct se2ot_kernel_s {
     float *hint_ws = nullptr;
     size_t c_hint_ws = 0;
     double *partial = nullptr, *scal = nullptr;
+    float *tmax = nullptr;
+    size_t c_tmax = 0;
     std::vector<cudaEvent_t> ev;
 };
 
@@ -204,9 +225,9 @@ se2ot_status validate_desc(const se2ot_kernel_desc *d)
 {
     if (!d) return fail(SE2OT_EINVAL, "desc is NULL");
     const int nt = d->ntheta;
-    if (!(nt == 1 || nt == 2 || nt == 4 || nt == 8 || nt == 16 || nt == 32))
-        return fail(SE2OT_EINVAL, "ntheta=%d not in {1,2,4,8,16,32}", nt);
-    if (d->radius < 0) return fail(SE2OT_EINVAL, "radius=%d < 0", d->radius);
+    if (nt < 1 || nt > 64) return fail(SE2OT_EINVAL, "ntheta=%d not in [1, 64]", nt);
+    if (d->radius < 0 || d->radius > MAX_RADIUS)
+        return fail(SE2OT_EINVAL, "radius=%d not in [0, %d]", d->radius, MAX_RADIUS);
     if (d->nx < 2 * d->radius + 1 || d->ny < 2 * d->radius + 1)
         return fail(SE2OT_EINVAL, "grid %dx%d smaller than the kernel window 2r+1=%d", d->nx, d->ny,
                     2 * d->radius + 1);
@@ -217,8 +238,6 @@ se2ot_status validate_desc(const se2ot_kernel_desc *d)
     if (d->boundary != SE2OT_BOUNDARY_ZERO && d->boundary != SE2OT_BOUNDARY_PERIODIC)
         return fail(SE2OT_EINVAL, "boundary=%d unknown", d->boundary);
     if ((double)d->nx * d->ny * nt > 1.0e9) return fail(SE2OT_EINVAL, "grid too large");
-    if (conv_smem_bytes(nt, d->radius) > 227 * 1024)
-        return fail(SE2OT_EINVAL, "radius=%d with ntheta=%d exceeds the shared-memory tile", d->radius, nt);
     return SE2OT_OK;
 }
 
@@ -233,6 +252,7 @@ se2ot_status ensure_solver_ws(se2ot_kernel k, int n)
     CK(grow(k->h1, k->c_h1, nV), "cudaMalloc(hint)");
     CK(grow(k->h2, k->c_h2, nV), "cudaMalloc(hint)");
     CK(grow(k->redo, k->c_redo, nV), "cudaMalloc(redo)");
+    CK(grow(k->tmax, k->c_tmax, (size_t)n * k->d.ntheta * conv_tiles(k->d.nx, k->d.ny)), "cudaMalloc(tmax)");
     return SE2OT_OK;
 }
 
@@ -240,9 +260,12 @@ ConvArgs conv_args(se2ot_kernel k, int batch, int epi)
 {
     ConvArgs a;
     std::memset(&a, 0, sizeof a);
-    a.taps = k->taps.taps;
-    a.taps_lo = k->taps.taps_lo;
-    a.lkmax = k->taps.lkmax;
+    a.ltheta = k->taps.ltheta;
+    a.ls = k->taps.ls;
+    a.ls_lo = k->taps.ls_lo;
+    a.lsrow = k->taps.lsrow;
+    a.tmax = k->tmax;
+    a.tmax_w = k->tmax;
     a.in_scale = 1.0;
     a.out_scale = 1.0;
     a.redo_list = k->redo;
@@ -268,7 +291,7 @@ se2ot_status run_conv(se2ot_kernel k, const ConvArgs &a, cudaStream_t s, long lo
     CK(launch_conv(a, s), "conv launch");
     if (t1) CK(cudaEventRecord(t1, s), "cudaEventRecord");
     CK(launch_redo(a, 2 * k->sms, s), "redo launch");
-    if (launches) *launches += 2;
+    if (launches) *launches += 3;   // tile-max pre-pass, convolution, exact recompute
     return SE2OT_OK;
 }
 
@@ -303,10 +326,11 @@ se2ot_status se2ot_kernel_build(const se2ot_kernel_desc *desc, void *stream, se2
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&k->sms, cudaDevAttrMultiProcessorCount, dev);
     const int D = 2 * desc->radius + 1;
-    const size_t ntap = (size_t)desc->ntheta * desc->ntheta * D * D;
-    cudaError_t e = cudaMalloc((void **)&k->taps.taps, ntap * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc((void **)&k->taps.taps_lo, ntap * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc((void **)&k->taps.lkmax, (size_t)desc->ntheta * desc->ntheta * sizeof(float));
+    const size_t npair = (size_t)desc->ntheta * desc->ntheta;
+    cudaError_t e = cudaMalloc((void **)&k->taps.ltheta, npair * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&k->taps.ls, npair * D * D * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&k->taps.ls_lo, npair * D * D * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&k->taps.lsrow, npair * D * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc((void **)&k->counters, 4 * sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMalloc((void **)&k->redo_total, 2 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMalloc((void **)&k->partial, 2 * RB * sizeof(double));
@@ -327,7 +351,7 @@ se2ot_status se2ot_kernel_destroy(se2ot_kernel k)
 {
     if (!k) return SE2OT_OK;
     cudaDeviceSynchronize();
-    void *ptrs[] = {k->taps.taps, k->taps.taps_lo, k->taps.lkmax, k->lmu, k->lv, k->lw, k->ld, k->L, k->lf, k->h1, k->h2, k->hint_ws,
+    void *ptrs[] = {k->taps.ltheta, k->taps.ls, k->taps.ls_lo, k->taps.lsrow, k->tmax, k->lmu, k->lv, k->lw, k->ld, k->L, k->lf, k->h1, k->h2, k->hint_ws,
                     k->mu_stage, k->bary_stage, k->redo, k->counters, k->redo_total, k->partial, k->scal};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -340,14 +364,17 @@ se2ot_status se2ot_kernel_taps(se2ot_kernel k, float *taps_host)
 {
     if (!k || !taps_host) return fail(SE2OT_EINVAL, "NULL argument");
     const int nt = k->d.ntheta, D = 2 * k->d.radius + 1;
-    std::vector<float> dev((size_t)nt * nt * D * D);
+    const size_t npair = (size_t)nt * nt;
+    std::vector<double> lt(npair);
+    std::vector<float> hi(npair * D * D), lo(npair * D * D);
     CK(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
-    CK(cudaMemcpy(dev.data(), k->taps.taps, dev.size() * sizeof(float), cudaMemcpyDeviceToHost), "cudaMemcpy(taps)");
-    // device layout [i][dy][dx][o] -> documented layout [o][i][dy][dx]
-    for (int o = 0; o < nt; ++o)
-        for (int i = 0; i < nt; ++i)
-            for (int t = 0; t < D * D; ++t)
-                taps_host[((size_t)o * nt + i) * D * D + t] = dev[((size_t)i * D * D + t) * nt + o];
+    CK(cudaMemcpy(lt.data(), k->taps.ltheta, lt.size() * sizeof(double), cudaMemcpyDeviceToHost), "cudaMemcpy");
+    CK(cudaMemcpy(hi.data(), k->taps.ls, hi.size() * sizeof(float), cudaMemcpyDeviceToHost), "cudaMemcpy");
+    CK(cudaMemcpy(lo.data(), k->taps.ls_lo, lo.size() * sizeof(float), cudaMemcpyDeviceToHost), "cudaMemcpy");
+    // device layout is already [o][i][dy][dx]; the tap is the orientation factor plus the spatial part
+    for (size_t p = 0; p < npair; ++p)
+        for (int t = 0; t < D * D; ++t)
+            taps_host[p * D * D + t] = (float)(lt[p] + ((double)hi[p * D * D + t] + (double)lo[p * D * D + t]));
     return SE2OT_OK;
 }
 
@@ -355,14 +382,16 @@ se2ot_status se2ot_apply(se2ot_kernel k, const float *f, float *out, int batch, 
 {
     if (!k || !f || !out) return fail(SE2OT_EINVAL, "NULL argument");
     if (batch < 1) return fail(SE2OT_EINVAL, "batch=%d < 1", batch);
-    if ((double)batch * k->V >= 2147483647.0) return fail(SE2OT_EINVAL, "batch*V too large");
+    if ((double)batch * k->V >= 2147483647.0 || (double)batch * k->d.ntheta > 65535.0)
+        return fail(SE2OT_EINVAL, "batch too large");
     cudaStream_t s = (cudaStream_t)stream;
     const size_t nV = (size_t)batch * k->V;
     CK(grow(k->lf, k->c_lf, nV), "cudaMalloc(lf)");
     CK(grow(k->redo, k->c_redo, nV), "cudaMalloc(redo)");
-    lin_to_log2_kernel<<<grid_for((long)nV), 256, 0, s>>>(f, k->lf, (long)nV);
-    CK(cudaGetLastError(), "lin_to_log2 launch");
     CK(grow(k->hint_ws, k->c_hint_ws, nV), "cudaMalloc(hint)");
+    CK(grow(k->tmax, k->c_tmax, (size_t)batch * k->d.ntheta * conv_tiles(k->d.nx, k->d.ny)), "cudaMalloc(tmax)");
+    lin_to_log2_kernel<<<grid_for((long)nV), 256, 0, s>>>(f, k->lf, (long)nV, k->d.nx, k->d.ny, k->d.ntheta);
+    CK(cudaGetLastError(), "lin_to_log2 launch");
     ConvArgs a = conv_args(k, batch, EPI_LIN_OUT);
     a.in = k->lf;
     a.hint = k->hint_ws;
@@ -375,12 +404,18 @@ se2ot_status se2ot_apply_log(se2ot_kernel k, const double *lf, double *lout, int
 {
     if (!k || !lf || !lout) return fail(SE2OT_EINVAL, "NULL argument");
     if (batch < 1) return fail(SE2OT_EINVAL, "batch=%d < 1", batch);
-    if ((double)batch * k->V >= 2147483647.0) return fail(SE2OT_EINVAL, "batch*V too large");
+    if ((double)batch * k->V >= 2147483647.0 || (double)batch * k->d.ntheta > 65535.0)
+        return fail(SE2OT_EINVAL, "batch too large");
     cudaStream_t s = (cudaStream_t)stream;
-    CK(grow(k->redo, k->c_redo, (size_t)batch * k->V), "cudaMalloc(redo)");
-    CK(grow(k->hint_ws, k->c_hint_ws, (size_t)batch * k->V), "cudaMalloc(hint)");
+    const size_t nV = (size_t)batch * k->V;
+    CK(grow(k->lf, k->c_lf, nV), "cudaMalloc(lf)");
+    CK(grow(k->redo, k->c_redo, nV), "cudaMalloc(redo)");
+    CK(grow(k->hint_ws, k->c_hint_ws, nV), "cudaMalloc(hint)");
+    CK(grow(k->tmax, k->c_tmax, (size_t)batch * k->d.ntheta * conv_tiles(k->d.nx, k->d.ny)), "cudaMalloc(tmax)");
+    to_slices_kernel<<<grid_for((long)nV), 256, 0, s>>>(lf, k->lf, (long)nV, k->d.nx, k->d.ny, k->d.ntheta);
+    CK(cudaGetLastError(), "to_slices launch");
     ConvArgs a = conv_args(k, batch, EPI_LOG_OUT);
-    a.in = lf;
+    a.in = k->lf;
     a.in_scale = LOG2E;
     a.hint = k->hint_ws;
     a.out64 = lout;
@@ -395,7 +430,8 @@ se2ot_status se2ot_barycenter(se2ot_kernel k, int n, const float *mu, const doub
     const auto wall0 = std::chrono::steady_clock::now();
     if (!k || !mu || !lambda || !bary) return fail(SE2OT_EINVAL, "NULL argument");
     if (n < 1 || n > 64) return fail(SE2OT_EINVAL, "n=%d not in [1, 64]", n);
-    if ((double)n * k->V >= 2147483647.0) return fail(SE2OT_EINVAL, "n*V too large");
+    if ((double)n * k->V >= 2147483647.0 || (double)n * k->d.ntheta > 65535.0)
+        return fail(SE2OT_EINVAL, "n*V too large");
     se2ot_solve_opts o = {100, 0, 0.0, SE2OT_FP32, 0};
     if (opts) o = *opts;
     if (o.max_iters < 1) return fail(SE2OT_EINVAL, "max_iters=%d < 1", o.max_iters);
@@ -436,7 +472,8 @@ se2ot_status se2ot_barycenter(se2ot_kernel k, int n, const float *mu, const doub
     // validate the inputs on the device: masses (FP64) and the sign of every entry are checked by
     // the reductions below once log2 mu exists
     long long launches = 0;
-    init_kernel<<<grid_for((long)nV), 256, 0, s>>>(mu_dev, k->lmu, k->lv, k->h1, k->h2, (long)nV);
+    init_kernel<<<grid_for((long)nV), 256, 0, s>>>(mu_dev, k->lmu, k->lv, k->h1, k->h2, (long)nV, k->d.nx,
+                                                   k->d.ny, k->d.ntheta);
     CK(cudaGetLastError(), "init launch");
     ++launches;
 
@@ -489,7 +526,7 @@ se2ot_status se2ot_barycenter(se2ot_kernel k, int n, const float *mu, const doub
             }
         }
     }
-    finalize_kernel<<<grid_for(V), 256, 0, s>>>(k->L, bary_dev, V);
+    finalize_kernel<<<grid_for(V), 256, 0, s>>>(k->L, bary_dev, V, k->d.nx, k->d.ny, k->d.ntheta);
     stats_partial_kernel<<<RB, RT, 0, s>>>(k->L, k->ld, lam, n, V, k->partial);
     stats_final_kernel<<<1, RT, 0, s>>>(k->partial, k->scal);
     CK(cudaGetLastError(), "finalize launch");
@@ -515,7 +552,7 @@ se2ot_status se2ot_barycenter(se2ot_kernel k, int n, const float *mu, const doub
         stats->voxel_iters_per_s = ms > 0 ? (double)V * it / (ms * 1e-3) : 0.0;
         stats->kernel_launches = launches;
         stats->redo_outputs = (long long)counts[0];
-        stats->evaluated_terms = (long long)counts[1] * terms_per_warp_slice(k->d.ntheta, k->d.radius);
+        stats->evaluated_terms = (long long)counts[1];
         if (timing) {
             double tot = 0.0;
             for (int j = 0; j < it; ++j)

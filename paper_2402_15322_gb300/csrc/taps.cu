@@ -6,67 +6,73 @@
 // and the tap is log2 K(u) = -rho_b(u)^2 / (eps ln 2) with
 //   rho_b(u)^2 = (w1 b1)^2 + (w2 b2)^2 + (w3 b3)^2,
 //   (b1, b2) = R(-u_theta / 2) (u_x, u_y),  b3 = u_theta in [-pi, pi)          (Sec. 4.3)
-// evaluated in FP64 and stored as an FP32 value plus its FP32 rounding residual.  A theta
-// difference of exactly pi is taken as -pi (small-angle convention); rho_b is the same for +pi
-// and -pi, so the choice does not matter.
+// evaluated in FP64.  Because b3 depends only on the orientation pair, the tap splits exactly into
+//   ltheta[o][i] = -(w3 b3)^2 / (eps ln 2)                      (FP64)
+//   ls[o][i][dy][dx] = -((w1 b1)^2 + (w2 b2)^2) / (eps ln 2)    (FP32 + FP32 rounding residual)
+// with ls <= 0 and ls = 0 at the zero offset; lsrow[o][i][dy] is the largest ls of each row.
+// A theta difference of exactly pi is taken as -pi (small-angle convention); rho_b is the same
+// for +pi and -pi, so the choice does not matter.
 #include "internal.h"
 
 namespace se2ot {
 
 namespace {
 
-__global__ void taps_kernel(int nx, int ny, int nt, int r, double w1, double w2, double w3,
-                            double eps, float *taps, float *taps_lo)
+constexpr double LOG2E = 1.44269504088896340736;
+
+// orientation difference theta_o - theta_i in units of pi, wrapped to [-1, 1)
+__device__ double dtheta_pi(int o, int i, int nt)
+{
+    int k = ((o - i) % nt + nt) % nt;
+    if (2 * k >= nt) k -= nt;
+    return 2.0 * k / nt;
+}
+
+__global__ void spatial_taps_kernel(int nx, int ny, int nt, int r, double w1, double w2, double eps,
+                                    float *ls, float *ls_lo)
 {
     const int D = 2 * r + 1;
-    const long total = (long)nt * D * D * nt;
+    const long total = (long)nt * nt * D * D;
     for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total;
          idx += (long)gridDim.x * blockDim.x) {
-        int o = (int)(idx % nt);
-        long rest = idx / nt;
-        int dxi = (int)(rest % D);
+        const int dxi = (int)(idx % D);
+        long rest = idx / D;
+        const int dyi = (int)(rest % D);
         rest /= D;
-        int dyi = (int)(rest % D);
-        int i = (int)(rest / D);
-        int dx = dxi - r, dy = dyi - r;
-
-        // orientation difference in whole steps, wrapped to [-nt/2, nt/2)
-        int k = ((o - i) % nt + nt) % nt;
-        if (2 * k >= nt) k -= nt;
-        const double dth = 2.0 * k / nt;          // in units of pi
-        const double thi = 2.0 * i / nt;          // in units of pi
-
+        const int i = (int)(rest % nt);
+        const int o = (int)(rest / nt);
+        const double X = (double)(dxi - r) / nx, Y = (double)(dyi - r) / ny;
         double si, ci;
-        sincospi(thi, &si, &ci);
-        const double X = (double)dx / nx, Y = (double)dy / ny;
-        // spatial part of h^-1 g: rotate the offset by -theta_i
+        sincospi(2.0 * i / nt, &si, &ci);
+        // spatial part of h^-1 g: the offset rotated by -theta_i
         const double ux = X * ci + Y * si;
         const double uy = -X * si + Y * ci;
         // half-angle coordinates: rotate by -u_theta / 2
         double sh, ch;
-        sincospi(0.5 * dth, &sh, &ch);
+        sincospi(0.5 * dtheta_pi(o, i, nt), &sh, &ch);
         const double b1 = ux * ch + uy * sh;
         const double b2 = -ux * sh + uy * ch;
-        const double b3 = dth * 3.14159265358979323846;
-        const double rho2 = (w1 * b1) * (w1 * b1) + (w2 * b2) * (w2 * b2) + (w3 * b3) * (w3 * b3);
-        const double v = -rho2 / eps * 1.44269504088896340736;  // log2(e)
+        const double v = -((w1 * b1) * (w1 * b1) + (w2 * b2) * (w2 * b2)) / eps * LOG2E;
         const float hi = (float)v;
-        taps[idx] = hi;
-        taps_lo[idx] = (float)(v - (double)hi);
+        ls[idx] = hi;
+        ls_lo[idx] = (float)(v - (double)hi);
     }
 }
 
-// lkmax[o][i] = largest tap over the (2r+1)^2 offsets of the pair: an upper bound on every term
-// the pair contributes, used to skip pairs whose whole contribution is below FP32 resolution.
-__global__ void lkmax_kernel(int nt, int r, const float *taps, float *lkmax)
+__global__ void theta_taps_kernel(int nt, int r, double w3, double eps, const float *ls, double *ltheta,
+                                  float *lsrow)
 {
     const int D = 2 * r + 1;
-    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= nt * nt) return;
-    int o = p / nt, i = p % nt;
-    float m = -INFINITY;
-    for (int t = 0; t < D * D; ++t) m = fmaxf(m, taps[((long)i * D * D + t) * nt + o]);
-    lkmax[o * nt + i] = m;
+    const int o = p / nt, i = p - o * nt;
+    const double b3 = dtheta_pi(o, i, nt) * 3.14159265358979323846;
+    ltheta[p] = -(w3 * b3) * (w3 * b3) / eps * LOG2E;
+    for (int dyi = 0; dyi < D; ++dyi) {
+        float m = -INFINITY;
+        for (int dxi = 0; dxi < D; ++dxi) m = fmaxf(m, ls[((long)p * D + dyi) * D + dxi]);
+        lsrow[(long)p * D + dyi] = m;
+    }
 }
 
 }  // namespace
@@ -74,15 +80,16 @@ __global__ void lkmax_kernel(int nt, int r, const float *taps, float *lkmax)
 cudaError_t build_taps(const se2ot_kernel_desc &d, Taps &t, cudaStream_t s)
 {
     const int D = 2 * d.radius + 1;
-    const long total = (long)d.ntheta * D * D * d.ntheta;
+    const long total = (long)d.ntheta * d.ntheta * D * D;
     int blocks = (int)((total + 255) / 256);
     if (blocks > 4096) blocks = 4096;
-    taps_kernel<<<blocks, 256, 0, s>>>(d.nx, d.ny, d.ntheta, d.radius, d.w1, d.w2, d.w3, d.eps,
-                                       t.taps, t.taps_lo);
+    spatial_taps_kernel<<<blocks, 256, 0, s>>>(d.nx, d.ny, d.ntheta, d.radius, d.w1, d.w2, d.eps, t.ls,
+                                               t.ls_lo);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    int pairs = d.ntheta * d.ntheta;
-    lkmax_kernel<<<(pairs + 127) / 128, 128, 0, s>>>(d.ntheta, d.radius, t.taps, t.lkmax);
+    const int pairs = d.ntheta * d.ntheta;
+    theta_taps_kernel<<<(pairs + 127) / 128, 128, 0, s>>>(d.ntheta, d.radius, d.w3, d.eps, t.ls, t.ltheta,
+                                                        t.lsrow);
     return cudaGetLastError();
 }
 

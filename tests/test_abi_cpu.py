@@ -46,11 +46,11 @@ def test_version_and_empty_error(lib):
 
 @pytest.mark.parametrize("bad", [
     dict(nx=4, ny=16, ntheta=8, radius=3),      # grid smaller than the window
-    dict(nx=16, ny=16, ntheta=6, radius=3),     # unsupported ntheta
+    dict(nx=16, ny=16, ntheta=65, radius=3),    # unsupported ntheta
     dict(nx=16, ny=16, ntheta=8, radius=-1),
     dict(nx=16, ny=16, ntheta=8, radius=3, eps=0.0),
     dict(nx=16, ny=16, ntheta=8, radius=3, w=(1.0, -3.0, 0.5)),
-    dict(nx=256, ny=256, ntheta=32, radius=40),  # tile does not fit in shared memory
+    dict(nx=256, ny=256, ntheta=32, radius=17),  # radius beyond the instantiated kernels
 ])
 def test_invalid_descriptor_is_rejected_on_the_host(lib, bad):
     args = dict(w=(1.0, 3.0, 0.5), eps=1e-3)
