@@ -20,8 +20,9 @@
  * Memory layout of every field: f[((b*Ny + y)*Nx + x)*Ntheta + k], orientation innermost,
  * densely packed, b the batch / measure index.  V = Nx*Ny*Ntheta.
  *
- * Numerics.  The scaling vectors are kept as base-2 logarithms in FP64 device memory; every
- * convolution is evaluated as a log-sum-exp with a per-output shift, its terms in FP32.  The
+ * Numerics.  The scaling vectors are kept as base-2 logarithms in double-float device memory
+ * (pairs of FP32 numbers, ~48 significant bits); every convolution is evaluated as a log-sum-exp
+ * with a per-output shift, its terms in FP32.  The
  * paper's linear-domain iteration is the same algorithm; at the regularisations this library
  * targets (eps ~ 1e-4 on 128^2 grids) v_i and w_i span thousands of nats, far outside the
  * FP32 (and FP64) exponent range, so the linear form cannot be evaluated directly.
@@ -155,7 +156,8 @@ SE2OT_API se2ot_status se2ot_apply_log(se2ot_kernel k, const double *lf, double 
  * scale).  lambda: n <= 64 host doubles, >= 0, summing to 1 within 1e-12.  bary: V floats, host
  * or device memory.  opts may be NULL (100 iterations, no checks).  stats may be NULL.  Host
  * memory is copied on the stream; the call synchronises the stream before returning (stats
- * need it).  Workspace: 4 n V + V doubles, 3 n V words, owned by the kernel handle and reused.
+ * need it).  Workspace: 4 n V + V double-floats, 3 n V words, owned by the kernel handle and
+ * reused.
  * Returns EINVAL for invalid arguments, ENONFINITE if an iterate became non-finite (a NaN input
  * does that), ENOTCONV if tol_viol > 0 was not reached (the result is still written). */
 SE2OT_API se2ot_status se2ot_barycenter(se2ot_kernel k, int n, const float *mu, const double *lambda,
@@ -187,7 +189,8 @@ SE2OT_API se2ot_status se2ot_interpolate(se2ot_kernel k, const float *mu0, const
  * Arguments as in se2ot_barycenter, except: desc replaces the kernel handle; mu (n*V floats) and
  * bary (V floats) must be device memory (EINVAL otherwise: nothing is staged); stats->conv_ms is
  * not measured (0).  A problem whose tap table and workspace need more than the array
- * (2 ntheta^2 (2r+1)^2 + ntheta^2 floats, 4 n V + V doubles, 3 n V words, plus 4 KiB) is
+ * (ntheta^2 (2 (2r+1)^2 + (2r+1) + 2) floats of taps, 4 n V + V double-floats and 3 n V words of
+ * workspace, n ntheta ceil(nx/32) ceil(ny/32) floats of tile maxima, plus 4 KiB) is
  * rejected with EINVAL and a message giving the size; e.g. n = 4 measures on 64 x 64 x 16 fit,
  * 128 x 128 x 16 does not.
  *

@@ -14,15 +14,19 @@ bool launch_tile_c(int r, bool maxpass, const ConvArgs &a, cudaStream_t s, cudaE
 
 namespace {
 
-// tmax[b][i][tile] = max over the tile's halo ((TY + 2r) x (TX + 2r) voxels of slice i) of the
-// input (FP32-rounded, times in_scale); -inf where the halo holds no term.
+// tmax[b][i][tile]: largest input (hi part) of slice i over
+//   zero boundary: the tile itself (32 x 32, clipped to the grid); the convolution takes the max
+//                  over the 3 x 3 neighbouring tiles, which cover the tile's halo since r < 32;
+//   periodic:      the tile's whole halo ((TY + 2r) x (TX + 2r), wrapped), read directly.
+// -inf where the region holds no term; +inf if it holds a NaN (so that nothing is skipped).
 __global__ void __launch_bounds__(256) tile_max_kernel(ConvArgs a)
 {
-    const int nx = a.nx, ny = a.ny, r = a.r;
+    const int nx = a.nx, ny = a.ny;
+    const int r = a.periodic ? a.r : 0;
     const int HX = tile::TX + 2 * r, HY = tile::TY + 2 * r;
     const int x0 = blockIdx.x * tile::TX - r, y0 = blockIdx.y * tile::TY - r;
     const long plane = (long)nx * ny;
-    const double *src = a.in + (long)blockIdx.z * plane;
+    const float2 *src = a.in + (long)blockIdx.z * plane;
     float m = -INFINITY;
     bool nan_seen = false;
     for (int idx = threadIdx.x; idx < HX * HY; idx += blockDim.x) {
@@ -31,14 +35,14 @@ __global__ void __launch_bounds__(256) tile_max_kernel(ConvArgs a)
         if (a.periodic) {
             sy = tile::wrapi(sy, ny);
             sx = tile::wrapi(sx, nx);
-        } else if (sy < 0 || sy >= ny || sx < 0 || sx >= nx) {
+        } else if (sy >= ny || sx >= nx) {
             continue;
         }
-        const float v = (float)(src[(long)sy * nx + sx] * a.in_scale);
+        const float v = src[(long)sy * nx + sx].x;
         if (v != v) nan_seen = true;
         m = fmaxf(m, v);
     }
-    if (__syncthreads_or(nan_seen)) m = INFINITY;   // a NaN input must not make its pair look negligible
+    if (__syncthreads_or(nan_seen)) m = INFINITY;
     __shared__ float red[8];
 #pragma unroll
     for (int off = 16; off; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
@@ -65,7 +69,7 @@ __global__ void redo_kernel(ConvArgs a)
         const long bo = flat / plane, p = flat - bo * plane;
         const int b = (int)(bo / nt), o = (int)(bo - (long)b * nt);
         const int y = (int)(p / nx), x = (int)(p - (long)y * nx);
-        const double *in_b = a.in + (long)b * nt * plane;
+        const float2 *in_b = a.in + (long)b * nt * plane;
         auto term = [&](long t) -> double {
             const int i = (int)(t / (D * D));
             const int rem = (int)(t - (long)i * D * D);
@@ -78,7 +82,7 @@ __global__ void redo_kernel(ConvArgs a)
                 return -INFINITY;
             }
             const long ti = ((long)o * nt + i) * D * D + rem;
-            return in_b[(long)i * plane + (long)sy * nx + sx] * a.in_scale + a.ltheta[o * nt + i] +
+            return df_to_double(in_b[(long)i * plane + (long)sy * nx + sx]) + df_to_double(a.ltheta[o * nt + i]) +
                    ((double)a.ls[ti] + (double)a.ls_lo[ti]);
         };
         double m = -INFINITY;
@@ -94,7 +98,10 @@ __global__ void redo_kernel(ConvArgs a)
         if (m == -INFINITY) c = -INFINITY;   // empty window: zero density
         else if (!isfinite(m)) c = NAN;      // +inf or NaN input
         else c = m + log2(s);
-        if (lane == 0) tile::write_out(a, flat, b, o, y, x, c);
+        if (lane == 0) {
+            const float2 cd = df_from_double(c);   // c as an exact-enough hi + lo pair
+            tile::write_out(a, flat, b, o, y, x, cd.x, cd.y);
+        }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0 && a.redo_total) atomicAdd(a.redo_total, (unsigned long long)n);
 }

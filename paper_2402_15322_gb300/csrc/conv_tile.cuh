@@ -3,7 +3,7 @@
 // c(g, o) = log2 sum_{i, dy, dx} 2^( in(g - (dx, dy), i) + lt(o, i) + ls(o, i, dy, dx) )
 //
 // with the tap split exactly into its orientation factor lt(o, i) = -w3^2 dtheta^2 / (eps ln 2)
-// (FP64) and its spatial part ls = -(w1^2 b1^2 + w2^2 b2^2) / (eps ln 2) (FP32), Sec. 4.3.
+// (double-float) and its spatial part ls = -(w1^2 b1^2 + w2^2 b2^2) / (eps ln 2) (FP32), Sec. 4.3.
 //
 // One CTA computes one output orientation o of a 32 x 32 spatial tile of one field; each of its
 // 128 threads owns 8 consecutive x positions of one row.  For every input orientation i that can
@@ -14,23 +14,28 @@
 // Shift and precision: output j of a thread is evaluated as
 //   S_j + log2 sum 2^t,  t = ((in_hi - S'_j,hi) + ls) + (in_lo - S'_j,lo),   S'_j = S_j - lt(o, i)
 // where S_j is the previous output of the same convolution (or the largest term, from a MAXPASS
-// launch) and S'_j is formed in FP64 and split into FP32 hi + lo once per slice.  The big common
-// magnitudes (the scaling vectors are hundreds to thousands of log2 units, the orientation
-// factor hundreds) cancel exactly before anything is rounded.  Outputs whose log2 sum leaves
-// [-24, 16] are queued for the exact FP64 recompute of conv.cu.
+// launch), the input is a double-float (hi + lo) and S'_j is formed exactly (TwoSum) as hi + lo
+// once per slice.  The big common magnitudes (the scaling vectors are hundreds to thousands of
+// log2 units, the orientation factor hundreds) cancel exactly before anything is rounded.  No
+// FP64 instruction runs per staged element or per output (GB300's FP64 rate is a small fraction
+// of FP32's).  Outputs whose log2 sum leaves [-24, 16] are queued for the exact FP64 recompute of
+// conv.cu.
 //
 // Skipping (exact at FP32 resolution): a pair (o, i) is skipped when lt(o, i) + max(in over the
 // tile's halo of slice i) (from the tile-max pre-pass; the spatial taps are <= 0) is 2^-64 below
-// the smallest shift of the CTA, and a row dy when the same bound with the row's largest spatial
-// tap and the largest input in the rows it reads is.  Skipped terms total < 2^-40 of the output.
+// the smallest shift of the CTA; a row dy when the same bound with the row's largest spatial tap
+// and the largest input in the rows it reads is; and within a row, the window positions that
+// only meet taps below the row's threshold.  Skipped terms total < 2^-40 of the output.
 #pragma once
 
+#include "dfloat.cuh"
 #include "internal.h"
 
 namespace se2ot {
 namespace tile {
 
 constexpr int TX = 32, TY = 32, XQ = 8, THREADS = 128;
+constexpr int MAX_NT = 64;   // largest ntheta (validated by the library)
 constexpr float SKIP_MARGIN = 64.f;
 constexpr float ACC_LO = -24.f, ACC_HI = 16.f;
 
@@ -53,7 +58,7 @@ __host__ __device__ constexpr int tap_pitch(int d) { return (d + 3) & ~3; }
 __host__ __device__ constexpr size_t smem_floats(int r)
 {
     return (size_t)2 * (TY + 2 * r) * halo_pitch(TX + 2 * r) + (size_t)(2 * r + 1) * tap_pitch(2 * r + 1) +
-           (size_t)(TY + 2 * r) + (size_t)(2 * r + 1) + 64;
+           (size_t)(TY + 2 * r) + (size_t)(2 * r + 2) + 8 + 3 * MAX_NT + 8;
 }
 
 __device__ __forceinline__ int wrapi(int v, int n)
@@ -62,25 +67,31 @@ __device__ __forceinline__ int wrapi(int v, int n)
     return v < 0 ? v + n : v;
 }
 
-__device__ __forceinline__ void write_out(const ConvArgs &a, long flat, int b, int o, int y, int x, double c)
+// Epilogue of one output, c = log2 (K * 2^in)(g, o) given exactly as s + l (two floats).  flat
+// indexes the slice-major arrays; the apply epilogues write the caller's [b][y][x][o] in FP64
+// arithmetic (not on the Sinkhorn loop); the Sinkhorn epilogues stay in FP32 double-floats.
+__device__ __forceinline__ void write_out(const ConvArgs &a, long flat, int b, int o, int y, int x, float s, float l)
 {
-    // flat indexes the slice-major arrays; the apply epilogues write the caller's [b][y][x][o]
     switch (a.epi) {
-    case EPI_LOG_OUT: a.out64[(((long)b * a.ny + y) * a.nx + x) * a.nt + o] = c * a.out_scale; break;
-    case EPI_LIN_OUT: a.out32[(((long)b * a.ny + y) * a.nx + x) * a.nt + o] = (float)exp2(c); break;
+    case EPI_LOG_OUT:
+        a.out64[(((long)b * a.ny + y) * a.nx + x) * a.nt + o] = ((double)s + (double)l) * a.out_scale;
+        break;
+    case EPI_LIN_OUT:
+        a.out32[(((long)b * a.ny + y) * a.nx + x) * a.nt + o] = (float)exp2((double)s + (double)l);
+        break;
     case EPI_W:
-        a.out64[flat] = a.aux[flat] - c;
-        a.hint[flat] = (float)c;
+        a.out2[flat] = df_add(a.aux[flat], df_neg(df_two_sum(s, l)));   // w_i = mu_i / K v_i
+        a.hint[flat] = s + l;
         break;
     default:
-        a.out64[flat] = a.aux[flat] + c;
-        a.hint[flat] = (float)c;
+        a.out2[flat] = df_add(a.aux[flat], df_two_sum(s, l));           // d_i = v_i K w_i
+        a.hint[flat] = s + l;
         break;
     }
 }
 
 template <int R, bool MAXPASS>
-__global__ void __launch_bounds__(THREADS) conv_tile_kernel(const ConvArgs a)
+__global__ void __launch_bounds__(THREADS, 5) conv_tile_kernel(const ConvArgs a)
 {
     constexpr int D = 2 * R + 1;
     constexpr int HX = TX + 2 * R, HY = TY + 2 * R, HXP = halo_pitch(HX), TP = tap_pitch(D);
@@ -91,8 +102,10 @@ __global__ void __launch_bounds__(THREADS) conv_tile_kernel(const ConvArgs a)
     float *hlo = hhi + HY * HXP;
     float *ts = hlo + HY * HXP;            // [D][TP] spatial taps of the pair (hi)
     float *rowmax = ts + D * TP;           // [HY]
-    float *bandmax = rowmax + HY;          // [D]
-    float *red = bandmax + D;              // [THREADS / 32]
+    int *rowk = (int *)(rowmax + HY);      // [D] packed (first window index << 16 | last)
+    float *red = (float *)(rowk + ((D + 1) & ~1));   // [THREADS / 32] (even offset: float2 below)
+    float2 *lts = (float2 *)(red + 8);     // [nt] orientation factors lt(o, i)
+    int *need = (int *)(lts + MAX_NT);     // [nt] slice i contributes
 
     const int nx = a.nx, ny = a.ny, nt = a.nt;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -100,7 +113,7 @@ __global__ void __launch_bounds__(THREADS) conv_tile_kernel(const ConvArgs a)
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int b = blockIdx.z / nt, o = blockIdx.z - b * nt;
     const long plane = (long)nx * ny;
-    const double *in_b = a.in + (long)b * nt * plane;
+    const float2 *in_b = a.in + (long)b * nt * plane;
     const int gy = y0 + yl;
     const long obase = ((long)b * nt + o) * plane + (long)gy * nx + x0 + xl;
 
@@ -123,22 +136,42 @@ __global__ void __launch_bounds__(THREADS) conv_tile_kernel(const ConvArgs a)
 #pragma unroll
         for (int off = 16; off; off >>= 1) smin = fminf(smin, __shfl_xor_sync(0xffffffffu, smin, off));
         if (lane == 0) red[warp] = smin;
-        __syncthreads();
-        smin = fminf(fminf(red[0], red[1]), fminf(red[2], red[3]));
     }
+    __syncthreads();
+    if (!MAXPASS) smin = fminf(fminf(red[0], red[1]), fminf(red[2], red[3]));
 
-    const int tile = blockIdx.y * gridDim.x + blockIdx.x;
+    // which input slices can contribute: one thread per slice, from the tile-max pre-pass
     const long ntiles = (long)gridDim.x * gridDim.y;
-    unsigned rows_eval = 0;
-
-    for (int i = 0; i < nt; ++i) {
-        const double lt = a.ltheta[o * nt + i];
+    for (int i = tid; i < nt; i += THREADS) {
+        const float2 lt = a.ltheta[o * nt + i];
+        lts[i] = lt;
+        int nd = 1;
         if (!MAXPASS) {
-            const float tm = a.tmax[((long)b * nt + i) * ntiles + tile];
-            if ((float)lt + tm + 1.0f < smin - SKIP_MARGIN) continue;   // uniform over the CTA
+            // largest input over the tile's halo of slice i
+            const float *tmi = a.tmax + ((long)b * nt + i) * ntiles;
+            float tm;
+            if (a.periodic) {
+                tm = tmi[blockIdx.y * gridDim.x + blockIdx.x];
+            } else {
+                tm = -INFINITY;
+                for (int ty = (int)blockIdx.y - 1; ty <= (int)blockIdx.y + 1; ++ty)
+                    for (int tx = (int)blockIdx.x - 1; tx <= (int)blockIdx.x + 1; ++tx)
+                        if (ty >= 0 && ty < (int)gridDim.y && tx >= 0 && tx < (int)gridDim.x)
+                            tm = fmaxf(tm, tmi[ty * gridDim.x + tx]);
+            }
+            nd = !(lt.x + tm + 1.0f < smin - SKIP_MARGIN);
         }
+        need[i] = nd;
+    }
+    __syncthreads();
+
+    unsigned rows_eval = 0;
+    for (int i = 0; i < nt; ++i) {
+        if (!need[i]) continue;   // uniform over the CTA
+        const float2 lt = lts[i];
         __syncthreads();   // the previous slice is no longer read
-        const double *src = in_b + (long)i * plane;
+        const float2 *src = in_b + (long)i * plane;
+#pragma unroll 8
         for (int idx = tid; idx < HY * HX; idx += THREADS) {
             const int hy = idx / HX, hx = idx - hy * HX;
             int sy = y0 - R + hy, sx = x0 - R + hx;
@@ -149,14 +182,10 @@ __global__ void __launch_bounds__(THREADS) conv_tile_kernel(const ConvArgs a)
             } else {
                 inside = sy >= 0 && sy < ny && sx >= 0 && sx < nx;
             }
-            float vh = -INFINITY, vl = 0.f;
-            if (inside) {
-                const double v = src[(long)sy * nx + sx] * a.in_scale;
-                vh = (float)v;
-                if (isfinite(vh)) vl = (float)(v - (double)vh);
-            }
-            hhi[hy * HXP + hx] = vh;
-            hlo[hy * HXP + hx] = vl;
+            float2 v = make_float2(-INFINITY, 0.f);
+            if (inside) v = src[(long)sy * nx + sx];
+            hhi[hy * HXP + hx] = v.x;
+            hlo[hy * HXP + hx] = v.y;
         }
         const float *tsrc = a.ls + ((long)o * nt + i) * D * D;
         for (int idx = tid; idx < D * TP; idx += THREADS) {
@@ -165,35 +194,58 @@ __global__ void __launch_bounds__(THREADS) conv_tile_kernel(const ConvArgs a)
         }
         __syncthreads();
         if (!MAXPASS) {
-            for (int hy = tid; hy < HY; hy += THREADS) {
+            // row maxima of the staged halo: one warp per row, lanes across the row
+            for (int hy = warp; hy < HY; hy += THREADS / 32) {
                 float m = -INFINITY;
-                for (int hx = 0; hx < HX; ++hx) m = fmaxf(m, hhi[hy * HXP + hx]);
-                rowmax[hy] = m;
+#pragma unroll
+                for (int c = 0; c < (HX + 31) / 32; ++c)
+                    if (lane + 32 * c < HX) m = fmaxf(m, hhi[hy * HXP + lane + 32 * c]);
+#pragma unroll
+                for (int off = 16; off; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+                if (lane == 0) rowmax[hy] = m;
             }
             __syncthreads();
-            for (int d = tid; d < D; d += THREADS) {
-                // output rows y0..y0+TY-1 read halo rows (2R - d) .. (2R - d + TY - 1)
-                float m = -INFINITY;
-                for (int k = 0; k < TY; ++k) m = fmaxf(m, rowmax[2 * R - d + k]);
-                bandmax[d] = m;
+            // per kernel row d: the largest input the tile's outputs meet in it (output rows
+            // y0..y0+TY-1 read halo rows 2R-d .. 2R-d+TY-1), and the window positions whose taps
+            // can reach the skip threshold.  The spatial taps of a row are a concave quadratic in
+            // dx, so the taps >= thr form one interval [lo, hi]; a thread's window positions that
+            // meet them are k in [2R - hi, 2R - lo + XQ - 1].
+            for (int d = warp; d < D; d += THREADS / 32) {
+                float m = rowmax[2 * R - d + lane];   // TY == 32 rows, one per lane
+#pragma unroll
+                for (int off = 16; off; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+                const float thr = smin - SKIP_MARGIN - 1.0f - m - lt.x;
+                const unsigned m0 = __ballot_sync(0xffffffffu, lane < D && ts[d * TP + lane] >= thr);
+                const unsigned m1 = __ballot_sync(0xffffffffu, lane + 32 < D && ts[d * TP + lane + 32] >= thr);
+                int lo, hi;
+                if (m0) lo = __ffs(m0) - 1;
+                else lo = m1 ? 32 + __ffs(m1) - 1 : D;
+                if (m1) hi = 32 + 31 - __clz(m1);
+                else hi = m0 ? 31 - __clz(m0) : -1;
+                if (lane == 0) rowk[d] = hi < lo ? -1 : ((2 * R - hi) << 16) | (2 * R - lo + XQ - 1);
             }
             __syncthreads();
         }
 
-        // per-slice shift with the orientation factor folded in, split into FP32 hi + lo
+        // per-slice shift with the orientation factor folded in: S'_j = S_j - lt as hi + lo
         float Shi[XQ], Slo[XQ], mi[XQ];
 #pragma unroll
         for (int j = 0; j < XQ; ++j) {
-            const double sd = (double)S[j] - lt;
-            Shi[j] = (float)sd;
-            Slo[j] = (float)(sd - (double)Shi[j]);
+            float e;
+            two_sum(S[j], -lt.x, Shi[j], e);
+            Slo[j] = e - lt.y;
             mi[j] = -INFINITY;
         }
-        const float *lsrow = a.lsrow + ((long)o * nt + i) * D;
-
+    
         for (int dyi = 0; dyi < D; ++dyi) {
-            if (!MAXPASS && bandmax[dyi] + (float)lt + lsrow[dyi] + 1.0f < smin - SKIP_MARGIN) continue;
-            ++rows_eval;
+            int klo = 0, khi = WIN - 1;
+            if (!MAXPASS) {
+                const int rk = rowk[dyi];
+                if (rk < 0) continue;   // no tap of the row can reach the threshold
+                klo = rk >> 16;
+                khi = rk & 0xffff;
+            }
+            rows_eval += (unsigned)(min(WIN4 - 1, khi >> 2) - (klo >> 2) + 1);
             const float *rh = hhi + (yl + 2 * R - dyi) * HXP + xl;
             const float *rl = hlo + (yl + 2 * R - dyi) * HXP + xl;
             float th[D];
@@ -207,6 +259,7 @@ __global__ void __launch_bounds__(THREADS) conv_tile_kernel(const ConvArgs a)
             }
 #pragma unroll
             for (int k4 = 0; k4 < WIN4; ++k4) {
+                if (4 * k4 + 3 < klo || 4 * k4 > khi) continue;   // uniform over the CTA
                 const float4 h4 = *reinterpret_cast<const float4 *>(rh + 4 * k4);
                 const float4 l4 = *reinterpret_cast<const float4 *>(rl + 4 * k4);
                 const float wh4[4] = {h4.x, h4.y, h4.z, h4.w};
@@ -231,12 +284,14 @@ __global__ void __launch_bounds__(THREADS) conv_tile_kernel(const ConvArgs a)
         }
         if (MAXPASS) {
 #pragma unroll
-            for (int j = 0; j < XQ; ++j) acc[j] = fmaxf(acc[j], mi[j] + (float)lt);
+            for (int j = 0; j < XQ; ++j) acc[j] = fmaxf(acc[j], mi[j] + lt.x);
         }
     }
 
+    // terms evaluated: per block of 4 window positions, on average 4 * XQ * D / WIN terms for each
+    // of the tile's TX * TY / XQ thread rows
     if (tid == 0 && a.eval_count)
-        atomicAdd(a.eval_count, (unsigned long long)rows_eval * (TX * TY * D));
+        atomicAdd(a.eval_count, (unsigned long long)((double)rows_eval * 4 * TX * TY * D / WIN));
 
 #pragma unroll
     for (int j = 0; j < XQ; ++j) {
@@ -252,7 +307,7 @@ __global__ void __launch_bounds__(THREADS) conv_tile_kernel(const ConvArgs a)
             a.redo_list[k] = (int)flat;
             continue;
         }
-        write_out(a, flat, b, o, gy, x0 + xl + j, (double)S[j] + (double)lacc);
+        write_out(a, flat, b, o, gy, x0 + xl + j, S[j], lacc);
     }
 }
 

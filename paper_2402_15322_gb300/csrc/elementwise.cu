@@ -1,0 +1,154 @@
+// elementwise.cu -- the pointwise steps of the Appendix A loop and the layout conversions at the
+// library boundary.  Scaling vectors are base-2 logarithms held as double-floats (dfloat.cuh) in
+// slice-major order [i][theta][y][x]; the caller's arrays are [i][y][x][theta].
+//
+//   init      lmu_i = log2 mu_i, lv_i = 0 (v_i = 1), first shifts          (Appendix A, init)
+//   update    L = sum_i lambda_i ld_i, lv_i += L - ld_i                     (mu = prod d_i^lambda_i;
+//                                                                           v_i = v_i mu / d_i)
+//   finalize  bary = 2^L                                                    (return mu)
+//   stats     FP64 mass and marginal violation, fixed-order reduction      (stopping quantities)
+#include "dfloat.cuh"
+#include "internal.h"
+
+namespace se2ot {
+
+namespace {
+
+// slice-major index e = ((b*nt + t)*ny + y)*nx + x  ->  caller index ((b*ny + y)*nx + x)*nt + t
+__device__ __forceinline__ long user_index(long e, int nx, int ny, int nt)
+{
+    const long plane = (long)nx * ny;
+    const long bt = e / plane, p = e - bt * plane;
+    const long b = bt / nt, t = bt - b * nt;
+    return (b * plane + p) * nt + t;
+}
+
+int grid_for(long n)
+{
+    long b = (n + 255) / 256;
+    if (b < 1) b = 1;
+    if (b > 8 * 152) b = 8 * 152;
+    return (int)b;
+}
+
+// hint of the first w-convolution: 0 (its input lv is all zeros, so the output is log2 of a sum
+// of kernel values, within a few units of 0); of the first d-convolution: log2 mu (K w ~ w ~ mu
+// when v = 1).
+__global__ void init_kernel(const float *mu, float2 *lmu, float2 *lv, float *h1, float *h2, long n, int nx,
+                            int ny, int nt)
+{
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
+        const double l = log2((double)mu[user_index(e, nx, ny, nt)]);
+        const float2 ld = df_from_double(l);
+        lmu[e] = ld;
+        lv[e] = make_float2(0.f, 0.f);
+        h1[e] = 0.f;
+        h2[e] = isfinite(ld.x) ? ld.x : 0.f;
+    }
+}
+
+__global__ void update_kernel(float2 *lv, const float2 *ld, float2 *L, Lambdas lam, int n, long V)
+{
+    for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < V; g += (long)gridDim.x * blockDim.x) {
+        float2 acc = make_float2(0.f, 0.f);
+        for (int i = 0; i < n; ++i)
+            if (lam.v[i].x != 0.f) acc = df_add(acc, df_mul(ld[(long)i * V + g], lam.v[i]));
+        L[g] = acc;
+        for (int i = 0; i < n; ++i) {
+            const long e = (long)i * V + g;
+            lv[e] = df_add(lv[e], df_add(acc, df_neg(ld[e])));
+        }
+    }
+}
+
+__global__ void finalize_kernel(const float2 *L, float *bary, long V, int nx, int ny, int nt)
+{
+    for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < V; g += (long)gridDim.x * blockDim.x)
+        bary[user_index(g, nx, ny, nt)] = (float)exp2(df_to_double(L[g]));
+}
+
+constexpr int RT = 256;
+
+__device__ double block_sum(double v, double *sh)
+{
+    const int tid = threadIdx.x;
+    sh[tid] = v;
+    __syncthreads();
+    for (int s = RT / 2; s > 0; s >>= 1) {
+        if (tid < s) sh[tid] += sh[tid + s];
+        __syncthreads();
+    }
+    const double out = sh[0];
+    __syncthreads();
+    return out;
+}
+
+// partial[blk] = sum mu ; partial[STATS_BLOCKS + blk] = sum_i lambda_i sum |d_i - mu|
+__global__ void __launch_bounds__(RT) stats_partial_kernel(const float2 *L, const float2 *ld, Lambdas lam, int n,
+                                                           long V, double *partial)
+{
+    __shared__ double sh[RT];
+    double m = 0.0, vio = 0.0;
+    for (long g = blockIdx.x * (long)RT + threadIdx.x; g < V; g += (long)STATS_BLOCKS * RT) {
+        const double mu = exp2(df_to_double(L[g]));
+        m += mu;
+        for (int i = 0; i < n; ++i)
+            vio += df_to_double(lam.v[i]) * fabs(exp2(df_to_double(ld[(long)i * V + g])) - mu);
+    }
+    m = block_sum(m, sh);
+    vio = block_sum(vio, sh);
+    if (threadIdx.x == 0) {
+        partial[blockIdx.x] = m;
+        partial[STATS_BLOCKS + blockIdx.x] = vio;
+    }
+}
+
+__global__ void __launch_bounds__(RT) stats_final_kernel(const double *partial, double *out)
+{
+    __shared__ double sh[RT];
+    double m = 0.0, v = 0.0;
+    for (int k = threadIdx.x; k < STATS_BLOCKS; k += RT) {
+        m += partial[k];
+        v += partial[STATS_BLOCKS + k];
+    }
+    m = block_sum(m, sh);
+    v = block_sum(v, sh);
+    if (threadIdx.x == 0) {
+        out[0] = m;
+        out[1] = v / m;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_init(const float *mu, float2 *lmu, float2 *lv, float *h1, float *h2, int n, int nx, int ny,
+                        int nt, cudaStream_t s)
+{
+    const long nV = (long)n * nx * ny * nt;
+    init_kernel<<<grid_for(nV), 256, 0, s>>>(mu, lmu, lv, h1, h2, nV, nx, ny, nt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_update(float2 *lv, const float2 *ld, float2 *L, const Lambdas &lam, int n, long V,
+                          cudaStream_t s)
+{
+    update_kernel<<<grid_for(V), 256, 0, s>>>(lv, ld, L, lam, n, V);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const float2 *L, float *bary, int nx, int ny, int nt, cudaStream_t s)
+{
+    const long V = (long)nx * ny * nt;
+    finalize_kernel<<<grid_for(V), 256, 0, s>>>(L, bary, V, nx, ny, nt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stats(const float2 *L, const float2 *ld, const Lambdas &lam, int n, long V, double *partial,
+                         double *scal, cudaStream_t s)
+{
+    stats_partial_kernel<<<STATS_BLOCKS, RT, 0, s>>>(L, ld, lam, n, V, partial);
+    stats_final_kernel<<<1, RT, 0, s>>>(partial, scal);
+    return cudaGetLastError();
+}
+
+}  // namespace se2ot

@@ -21,19 +21,20 @@ enum Epilogue : int {
 };
 
 // One launch of the log-domain convolution c = log2 sum_h 2^(lk(h^-1 g) + in(h)).  Every array
-// except the apply outputs is slice-major: x[b][i][y][x].
+// except the apply outputs is slice-major: x[b][i][y][x].  Base-2 logarithms of the scaling
+// vectors are double-floats (float2: hi + lo, see dfloat.cuh).
 struct ConvArgs {
-    const double *in;        // [batch][nt][ny][nx] base-2 logarithms (times in_scale)
-    double in_scale;         // multiplies `in` as it is read (log2(e) for natural-log input)
-    const double *ltheta;    // [o][i] orientation factor of the tap, -w3^2 dtheta^2 / (eps ln 2)
+    const float2 *in;        // [batch][nt][ny][nx] base-2 logarithms
+    const float2 *ltheta;    // [o][i] orientation factor of the tap, -w3^2 dtheta^2 / (eps ln 2)
     const float *ls;         // [o][i][dy][dx] spatial part of the tap (FP32)
     const float *ls_lo;      // same layout: FP64 value - ls (rounding residual)
     const float *lsrow;      // [o][i][dy] largest spatial tap of each row
     const float *tmax;       // [batch][nt][tiles] largest input over each tile's halo
     float *tmax_w;           // the same buffer, written by the pre-pass
     float *hint;             // [batch][nt][ny][nx] shift per output (read; written with c)
-    const double *aux;       // EPI_W: log2 mu_i; EPI_D: log2 v_i
-    double *out64;           // EPI_LOG_OUT / EPI_W / EPI_D destination
+    const float2 *aux;       // EPI_W: log2 mu_i; EPI_D: log2 v_i
+    float2 *out2;            // EPI_W / EPI_D destination (log2 w_i, log2 d_i)
+    double *out64;           // EPI_LOG_OUT destination
     float *out32;            // EPI_LIN_OUT destination
     double out_scale;        // EPI_LOG_OUT: ln 2 for natural-log output
     int *redo_list;          // outputs to recompute exactly (slice-major flat index)
@@ -45,7 +46,7 @@ struct ConvArgs {
 
 // Device tap tables of one kernel handle.
 struct Taps {
-    double *ltheta = nullptr;  // [nt][nt]
+    float2 *ltheta = nullptr;  // [nt][nt] double-float
     float *ls = nullptr;       // [nt][nt][D][D]
     float *ls_lo = nullptr;    // [nt][nt][D][D]
     float *lsrow = nullptr;    // [nt][nt][D]
@@ -64,5 +65,22 @@ size_t conv_smem_bytes(int r);           // dynamic shared memory of one convolu
 // Host helpers of solver.cu shared with other entry points.
 se2ot_status validate_kernel_desc(const se2ot_kernel_desc *d);   // EINVAL + message, or OK
 void set_last_error(const char *msg);                            // se2ot_last_error() text
+
+// Elementwise kernels of the barycenter loop (solver.cu), shared by every entry point.
+struct Lambdas {
+    float2 v[64];   // weights as double-floats
+};
+// lmu = log2 mu (caller layout -> slice-major), lv = 0, hint1 = 0, hint2 = lmu
+cudaError_t launch_init(const float *mu, float2 *lmu, float2 *lv, float *h1, float *h2, int n, int nx, int ny,
+                        int nt, cudaStream_t s);
+// L = sum_i lambda_i ld_i ; lv_i += L - ld_i
+cudaError_t launch_update(float2 *lv, const float2 *ld, float2 *L, const Lambdas &lam, int n, long V,
+                          cudaStream_t s);
+// bary (caller layout) = 2^L
+cudaError_t launch_finalize(const float2 *L, float *bary, int nx, int ny, int nt, cudaStream_t s);
+// scal[0] = sum 2^L, scal[1] = sum_i lambda_i |2^ld_i - 2^L| / scal[0]  (FP64, fixed order)
+constexpr int STATS_BLOCKS = 256;
+cudaError_t launch_stats(const float2 *L, const float2 *ld, const Lambdas &lam, int n, long V, double *partial,
+                         double *scal, cudaStream_t s);
 
 }  // namespace se2ot

@@ -89,103 +89,6 @@ struct Carver {
     }
 };
 
-struct Lam {
-    double v[64];
-};
-
-// slice-major index e = ((b*nt + t)*ny + y)*nx + x  ->  caller index ((b*ny + y)*nx + x)*nt + t
-__device__ __forceinline__ long na_user_index(long e, int nx, int ny, int nt)
-{
-    const long plane = (long)nx * ny;
-    const long bt = e / plane, p = e - bt * plane;
-    const long b = bt / nt, t = bt - b * nt;
-    return (b * plane + p) * nt + t;
-}
-
-__global__ void na_init_kernel(const float *mu, double *lmu, double *lv, float *h1, float *h2, long n, int nx,
-                               int ny, int nt)
-{
-    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
-        const double l = log2((double)mu[na_user_index(e, nx, ny, nt)]);
-        lmu[e] = l;
-        lv[e] = 0.0;
-        h1[e] = 0.f;
-        h2[e] = isfinite(l) ? (float)l : 0.f;
-    }
-}
-
-__global__ void na_update_kernel(double *lv, const double *ld, double *L, Lam lam, int n, long V)
-{
-    for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < V; g += (long)gridDim.x * blockDim.x) {
-        double acc = 0.0;
-        for (int i = 0; i < n; ++i)
-            if (lam.v[i] != 0.0) acc += lam.v[i] * ld[(long)i * V + g];
-        L[g] = acc;
-        for (int i = 0; i < n; ++i) lv[(long)i * V + g] += acc - ld[(long)i * V + g];
-    }
-}
-
-__global__ void na_finalize_kernel(const double *L, float *bary, long V, int nx, int ny, int nt)
-{
-    for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < V; g += (long)gridDim.x * blockDim.x)
-        bary[na_user_index(g, nx, ny, nt)] = (float)exp2(L[g]);
-}
-
-constexpr int NRB = 256, NRT = 256;
-
-__device__ double na_block_sum(double v, double *sh)
-{
-    const int tid = threadIdx.x;
-    sh[tid] = v;
-    __syncthreads();
-    for (int s = NRT / 2; s > 0; s >>= 1) {
-        if (tid < s) sh[tid] += sh[tid + s];
-        __syncthreads();
-    }
-    const double out = sh[0];
-    __syncthreads();
-    return out;
-}
-
-__global__ void __launch_bounds__(NRT) na_stats_partial(const double *L, const double *ld, Lam lam, int n,
-                                                        long V, double *partial)
-{
-    __shared__ double sh[NRT];
-    double m = 0.0, vio = 0.0;
-    for (long g = blockIdx.x * (long)NRT + threadIdx.x; g < V; g += (long)NRB * NRT) {
-        const double mu = exp2(L[g]);
-        m += mu;
-        for (int i = 0; i < n; ++i) vio += lam.v[i] * fabs(exp2(ld[(long)i * V + g]) - mu);
-    }
-    m = na_block_sum(m, sh);
-    vio = na_block_sum(vio, sh);
-    if (threadIdx.x == 0) {
-        partial[blockIdx.x] = m;
-        partial[NRB + blockIdx.x] = vio;
-    }
-}
-
-__global__ void __launch_bounds__(NRT) na_stats_final(const double *partial, double *out)
-{
-    __shared__ double sh[NRT];
-    double m = threadIdx.x < NRB ? partial[threadIdx.x] : 0.0;
-    double v = threadIdx.x < NRB ? partial[NRB + threadIdx.x] : 0.0;
-    m = na_block_sum(m, sh);
-    v = na_block_sum(v, sh);
-    if (threadIdx.x == 0) {
-        out[0] = m;
-        out[1] = v / m;
-    }
-}
-
-int na_grid(long n)
-{
-    long b = (n + 255) / 256;
-    if (b < 1) b = 1;
-    if (b > 8 * 152) b = 8 * 152;
-    return (int)b;
-}
-
 bool on_device(const void *p)
 {
     cudaPointerAttributes at;
@@ -212,13 +115,14 @@ extern "C" se2ot_status se2ot_barycenter_noalloc(const se2ot_kernel_desc *desc, 
     if (o.max_iters < 1) return nfail(SE2OT_EINVAL, "max_iters=%d < 1", o.max_iters);
     if (o.precision != SE2OT_FP32) return nfail(SE2OT_EINVAL, "precision=%d unsupported", o.precision);
     if (o.tol_viol < 0 || !std::isfinite(o.tol_viol)) return nfail(SE2OT_EINVAL, "tol_viol invalid");
-    Lam lam;
+    Lambdas lam;
     double lsum = 0.0;
-    for (int i = 0; i < 64; ++i) lam.v[i] = 0.0;
+    for (int i = 0; i < 64; ++i) lam.v[i] = make_float2(0.f, 0.f);
     for (int i = 0; i < n; ++i) {
         if (!(lambda[i] >= 0.0) || !std::isfinite(lambda[i]))
             return nfail(SE2OT_EINVAL, "lambda[%d]=%g not >= 0", i, lambda[i]);
-        lam.v[i] = lambda[i];
+        const float hi = (float)lambda[i];
+        lam.v[i] = make_float2(hi, (float)(lambda[i] - (double)hi));
         lsum += lambda[i];
     }
     if (std::fabs(lsum - 1.0) > 1e-12) return nfail(SE2OT_EINVAL, "lambda sums to %.17g, not 1", lsum);
@@ -234,19 +138,19 @@ extern "C" se2ot_status se2ot_barycenter_noalloc(const se2ot_kernel_desc *desc, 
 
     // Lay out the scratch array; first a dry run to size it.
     Carver dry{nullptr};
-    dry.take<double>(npair);
+    dry.take<float2>(npair);
     dry.take<float>(npair * D * D);
     dry.take<float>(npair * D * D);
     dry.take<float>(npair * D);
     dry.take<float>(ntmax);
-    for (int k = 0; k < 4; ++k) dry.take<double>(nV);
-    dry.take<double>((size_t)V);
+    for (int k = 0; k < 4; ++k) dry.take<float2>(nV);
+    dry.take<float2>((size_t)V);
     dry.take<float>(nV);
     dry.take<float>(nV);
     dry.take<int>(nV);
     dry.take<unsigned>(4);
     dry.take<unsigned long long>(2);
-    dry.take<double>(2 * NRB);
+    dry.take<double>(2 * STATS_BLOCKS);
     dry.take<double>(4);
     if (dry.off > SCRATCH_BYTES)
         return nfail(SE2OT_EINVAL, "problem needs %zu bytes of scratch, more than the %zu-byte static array",
@@ -257,18 +161,18 @@ extern "C" se2ot_status se2ot_barycenter_noalloc(const se2ot_kernel_desc *desc, 
     if (st != SE2OT_OK) return st;
     Carver c{base};
     Taps taps;
-    taps.ltheta = c.take<double>(npair);
+    taps.ltheta = c.take<float2>(npair);
     taps.ls = c.take<float>(npair * D * D);
     taps.ls_lo = c.take<float>(npair * D * D);
     taps.lsrow = c.take<float>(npair * D);
     float *tmax = c.take<float>(ntmax);
-    double *lmu = c.take<double>(nV), *lv = c.take<double>(nV), *lw = c.take<double>(nV), *ld = c.take<double>(nV);
-    double *L = c.take<double>((size_t)V);
+    float2 *lmu = c.take<float2>(nV), *lv = c.take<float2>(nV), *lw = c.take<float2>(nV), *ld = c.take<float2>(nV);
+    float2 *L = c.take<float2>((size_t)V);
     float *h1 = c.take<float>(nV), *h2 = c.take<float>(nV);
     int *redo = c.take<int>(nV);
     unsigned *count = c.take<unsigned>(4);
     unsigned long long *totals = c.take<unsigned long long>(2);
-    double *partial = c.take<double>(2 * NRB);
+    double *partial = c.take<double>(2 * STATS_BLOCKS);
     double *scal = c.take<double>(4);
 
     cudaStream_t s = (cudaStream_t)stream;
@@ -279,8 +183,7 @@ extern "C" se2ot_status se2ot_barycenter_noalloc(const se2ot_kernel_desc *desc, 
     // everything read below is (re)initialised here: the array keeps the previous call's values
     NCK(cudaMemsetAsync(totals, 0, 2 * sizeof(unsigned long long), s), "cudaMemsetAsync");
     NCK(build_taps(*desc, taps, s), "tap build");
-    na_init_kernel<<<na_grid((long)nV), 256, 0, s>>>(mu, lmu, lv, h1, h2, (long)nV, desc->nx, desc->ny, nt);
-    NCK(cudaGetLastError(), "init launch");
+    NCK(launch_init(mu, lmu, lv, h1, h2, n, desc->nx, desc->ny, nt, s), "init launch");
     long long launches = 3;
 
     ConvArgs aw;
@@ -291,7 +194,6 @@ extern "C" se2ot_status se2ot_barycenter_noalloc(const se2ot_kernel_desc *desc, 
     aw.lsrow = taps.lsrow;
     aw.tmax = tmax;
     aw.tmax_w = tmax;
-    aw.in_scale = 1.0;
     aw.out_scale = 1.0;
     aw.redo_list = redo;
     aw.redo_count = count;
@@ -308,12 +210,12 @@ extern "C" se2ot_status se2ot_barycenter_noalloc(const se2ot_kernel_desc *desc, 
     aw.in = lv;
     aw.hint = h1;
     aw.aux = lmu;
-    aw.out64 = lw;
+    aw.out2 = lw;
     ad.epi = EPI_D;
     ad.in = lw;
     ad.hint = h2;
     ad.aux = lv;
-    ad.out64 = ld;
+    ad.out2 = ld;
 
     int it = 0;
     bool converged = false;
@@ -324,13 +226,11 @@ extern "C" se2ot_status se2ot_barycenter_noalloc(const se2ot_kernel_desc *desc, 
             NCK(launch_redo(*a, 2 * sms, s), "redo launch");
             launches += 3;
         }
-        na_update_kernel<<<na_grid(V), 256, 0, s>>>(lv, ld, L, lam, n, V);
-        NCK(cudaGetLastError(), "update launch");
+        NCK(launch_update(lv, ld, L, lam, n, V, s), "update launch");
         ++launches;
         ++it;
         if (o.tol_viol > 0 && o.check_every > 0 && it % o.check_every == 0 && it < o.max_iters) {
-            na_stats_partial<<<NRB, NRT, 0, s>>>(L, ld, lam, n, V, partial);
-            na_stats_final<<<1, NRT, 0, s>>>(partial, scal);
+            NCK(launch_stats(L, ld, lam, n, V, partial, scal, s), "stats launch");
             launches += 2;
             double h[2];
             NCK(cudaMemcpyAsync(h, scal, sizeof h, cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync(stats)");
@@ -341,10 +241,8 @@ extern "C" se2ot_status se2ot_barycenter_noalloc(const se2ot_kernel_desc *desc, 
             }
         }
     }
-    na_finalize_kernel<<<na_grid(V), 256, 0, s>>>(L, bary, V, desc->nx, desc->ny, nt);
-    na_stats_partial<<<NRB, NRT, 0, s>>>(L, ld, lam, n, V, partial);
-    na_stats_final<<<1, NRT, 0, s>>>(partial, scal);
-    NCK(cudaGetLastError(), "finalize launch");
+    NCK(launch_finalize(L, bary, desc->nx, desc->ny, nt, s), "finalize launch");
+    NCK(launch_stats(L, ld, lam, n, V, partial, scal, s), "stats launch");
     launches += 3;
     double h[2];
     unsigned long long counts[2] = {0, 0};

@@ -21,6 +21,7 @@
 #include <string>
 #include <vector>
 
+#include "dfloat.cuh"
 #include "internal.h"
 
 using namespace se2ot;
@@ -56,8 +57,8 @@ se2ot_status cuda_fail(cudaError_t e, const char *what)
 constexpr double LOG2E = 1.44269504088896340736;
 constexpr double LN2 = 0.69314718055994530942;
 
-// ------------------------------------------------------------------ elementwise kernels
-// Slice-major index e = ((b*nt + t)*ny + y)*nx + x  <->  caller index ((b*ny + y)*nx + x)*nt + t.
+// ------------------------------------------------------------------ boundary conversions (apply)
+// slice-major index e = ((b*nt + t)*ny + y)*nx + x  ->  caller index ((b*ny + y)*nx + x)*nt + t
 __device__ __forceinline__ long user_index(long e, int nx, int ny, int nt)
 {
     const long plane = (long)nx * ny;
@@ -66,105 +67,18 @@ __device__ __forceinline__ long user_index(long e, int nx, int ny, int nt)
     return (b * plane + p) * nt + t;
 }
 
-// lf = log2 f (apply): caller layout float -> slice-major FP64
-__global__ void lin_to_log2_kernel(const float *f, double *out, long n, int nx, int ny, int nt)
+// apply: lf = log2 f, caller layout float -> slice-major double-float
+__global__ void lin_to_log2_kernel(const float *f, float2 *out, long n, int nx, int ny, int nt)
 {
     for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x)
-        out[e] = log2((double)f[user_index(e, nx, ny, nt)]);
+        out[e] = df_from_double(log2((double)f[user_index(e, nx, ny, nt)]));
 }
 
-// apply_log: caller layout FP64 -> slice-major FP64 (natural logs; the kernel scales them)
-__global__ void to_slices_kernel(const double *f, double *out, long n, int nx, int ny, int nt)
+// apply_log: natural logs in the caller layout -> base-2 logs, slice-major double-float
+__global__ void log_to_log2_kernel(const double *f, float2 *out, long n, int nx, int ny, int nt)
 {
     for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x)
-        out[e] = f[user_index(e, nx, ny, nt)];
-}
-
-// lmu = log2 mu; lv = 0 (v = 1); hint of the first w-convolution 0 (its input is all zeros);
-// hint of the first d-convolution log2 mu (K w ~ w ~ mu when v = 1).
-__global__ void init_kernel(const float *mu, double *lmu, double *lv, float *h1, float *h2, long n, int nx,
-                            int ny, int nt)
-{
-    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
-        const double l = log2((double)mu[user_index(e, nx, ny, nt)]);
-        lmu[e] = l;
-        lv[e] = 0.0;
-        h1[e] = 0.f;
-        h2[e] = isfinite(l) ? (float)l : 0.f;
-    }
-}
-
-struct Lambdas {
-    double v[64];
-};
-
-// Geometric mean and v-update, one thread per voxel:
-// L = sum_i lambda_i ld_i (terms with lambda_i = 0 skipped), lv_i += L - ld_i.
-__global__ void update_kernel(double *lv, const double *ld, double *L, Lambdas lam, int n, long V)
-{
-    for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < V; g += (long)gridDim.x * blockDim.x) {
-        double acc = 0.0;
-        for (int i = 0; i < n; ++i)
-            if (lam.v[i] != 0.0) acc += lam.v[i] * ld[(long)i * V + g];
-        L[g] = acc;
-        for (int i = 0; i < n; ++i) lv[(long)i * V + g] += acc - ld[(long)i * V + g];
-    }
-}
-
-__global__ void finalize_kernel(const double *L, float *bary, long V, int nx, int ny, int nt)
-{
-    for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < V; g += (long)gridDim.x * blockDim.x)
-        bary[user_index(g, nx, ny, nt)] = (float)exp2(L[g]);
-}
-
-// Deterministic FP64 reductions: a fixed grid of RB blocks, each summing a fixed strided subset
-// in a fixed order and reducing in a fixed tree; a single block then sums the partials in order.
-constexpr int RB = 256, RT = 256;
-
-__device__ double block_sum(double v, double *sh)
-{
-    const int tid = threadIdx.x;
-    sh[tid] = v;
-    __syncthreads();
-    for (int s = RT / 2; s > 0; s >>= 1) {
-        if (tid < s) sh[tid] += sh[tid + s];
-        __syncthreads();
-    }
-    const double out = sh[0];
-    __syncthreads();
-    return out;
-}
-
-// partial[blk] = sum mu ; partial[RB + blk] = sum_i lambda_i sum |d_i - mu|
-__global__ void __launch_bounds__(RT) stats_partial_kernel(const double *L, const double *ld, Lambdas lam,
-                                                           int n, long V, double *partial)
-{
-    __shared__ double sh[RT];
-    double m = 0.0, vio = 0.0;
-    for (long g = blockIdx.x * (long)RT + threadIdx.x; g < V; g += (long)RB * RT) {
-        const double mu = exp2(L[g]);
-        m += mu;
-        for (int i = 0; i < n; ++i) vio += lam.v[i] * fabs(exp2(ld[(long)i * V + g]) - mu);
-    }
-    m = block_sum(m, sh);
-    vio = block_sum(vio, sh);
-    if (threadIdx.x == 0) {
-        partial[blockIdx.x] = m;
-        partial[RB + blockIdx.x] = vio;
-    }
-}
-
-__global__ void __launch_bounds__(RT) stats_final_kernel(const double *partial, double *out)
-{
-    __shared__ double sh[RT];
-    double m = threadIdx.x < RB ? partial[threadIdx.x] : 0.0;
-    double v = threadIdx.x < RB ? partial[RB + threadIdx.x] : 0.0;
-    m = block_sum(m, sh);
-    v = block_sum(v, sh);
-    if (threadIdx.x == 0) {
-        out[0] = m;
-        out[1] = v / m;
-    }
+        out[e] = df_from_double(f[user_index(e, nx, ny, nt)] * LOG2E);
 }
 
 int grid_for(long n, int threads = 256)
@@ -202,8 +116,8 @@ struct se2ot_kernel_s {
     Taps taps;
     long V = 0;
     int sms = 152;
-    // workspace (grown on demand)
-    double *lmu = nullptr, *lv = nullptr, *lw = nullptr, *ld = nullptr, *L = nullptr, *lf = nullptr;
+    // workspace (grown on demand); scaling vectors as double-float base-2 logarithms
+    float2 *lmu = nullptr, *lv = nullptr, *lw = nullptr, *ld = nullptr, *L = nullptr, *lf = nullptr;
     size_t c_lmu = 0, c_lv = 0, c_lw = 0, c_ld = 0, c_L = 0, c_lf = 0;
     float *h1 = nullptr, *h2 = nullptr, *mu_stage = nullptr, *bary_stage = nullptr;
     size_t c_h1 = 0, c_h2 = 0, c_mus = 0, c_bs = 0;
@@ -266,7 +180,6 @@ ConvArgs conv_args(se2ot_kernel k, int batch, int epi)
     a.lsrow = k->taps.lsrow;
     a.tmax = k->tmax;
     a.tmax_w = k->tmax;
-    a.in_scale = 1.0;
     a.out_scale = 1.0;
     a.redo_list = k->redo;
     a.redo_count = k->counters;
@@ -327,13 +240,13 @@ se2ot_status se2ot_kernel_build(const se2ot_kernel_desc *desc, void *stream, se2
     cudaDeviceGetAttribute(&k->sms, cudaDevAttrMultiProcessorCount, dev);
     const int D = 2 * desc->radius + 1;
     const size_t npair = (size_t)desc->ntheta * desc->ntheta;
-    cudaError_t e = cudaMalloc((void **)&k->taps.ltheta, npair * sizeof(double));
+    cudaError_t e = cudaMalloc((void **)&k->taps.ltheta, npair * sizeof(float2));
     if (e == cudaSuccess) e = cudaMalloc((void **)&k->taps.ls, npair * D * D * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc((void **)&k->taps.ls_lo, npair * D * D * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc((void **)&k->taps.lsrow, npair * D * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc((void **)&k->counters, 4 * sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMalloc((void **)&k->redo_total, 2 * sizeof(unsigned long long));
-    if (e == cudaSuccess) e = cudaMalloc((void **)&k->partial, 2 * RB * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&k->partial, 2 * STATS_BLOCKS * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc((void **)&k->scal, 4 * sizeof(double));
     if (e == cudaSuccess) e = cudaMemsetAsync(k->counters, 0, 4 * sizeof(unsigned), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(k->redo_total, 0, 2 * sizeof(unsigned long long), s);
@@ -365,16 +278,17 @@ se2ot_status se2ot_kernel_taps(se2ot_kernel k, float *taps_host)
     if (!k || !taps_host) return fail(SE2OT_EINVAL, "NULL argument");
     const int nt = k->d.ntheta, D = 2 * k->d.radius + 1;
     const size_t npair = (size_t)nt * nt;
-    std::vector<double> lt(npair);
+    std::vector<float2> lt(npair);
     std::vector<float> hi(npair * D * D), lo(npair * D * D);
     CK(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
-    CK(cudaMemcpy(lt.data(), k->taps.ltheta, lt.size() * sizeof(double), cudaMemcpyDeviceToHost), "cudaMemcpy");
+    CK(cudaMemcpy(lt.data(), k->taps.ltheta, lt.size() * sizeof(float2), cudaMemcpyDeviceToHost), "cudaMemcpy");
     CK(cudaMemcpy(hi.data(), k->taps.ls, hi.size() * sizeof(float), cudaMemcpyDeviceToHost), "cudaMemcpy");
     CK(cudaMemcpy(lo.data(), k->taps.ls_lo, lo.size() * sizeof(float), cudaMemcpyDeviceToHost), "cudaMemcpy");
     // device layout is already [o][i][dy][dx]; the tap is the orientation factor plus the spatial part
     for (size_t p = 0; p < npair; ++p)
         for (int t = 0; t < D * D; ++t)
-            taps_host[p * D * D + t] = (float)(lt[p] + ((double)hi[p * D * D + t] + (double)lo[p * D * D + t]));
+            taps_host[p * D * D + t] = (float)(((double)lt[p].x + (double)lt[p].y) +
+                                               ((double)hi[p * D * D + t] + (double)lo[p * D * D + t]));
     return SE2OT_OK;
 }
 
@@ -412,11 +326,10 @@ se2ot_status se2ot_apply_log(se2ot_kernel k, const double *lf, double *lout, int
     CK(grow(k->redo, k->c_redo, nV), "cudaMalloc(redo)");
     CK(grow(k->hint_ws, k->c_hint_ws, nV), "cudaMalloc(hint)");
     CK(grow(k->tmax, k->c_tmax, (size_t)batch * k->d.ntheta * conv_tiles(k->d.nx, k->d.ny)), "cudaMalloc(tmax)");
-    to_slices_kernel<<<grid_for((long)nV), 256, 0, s>>>(lf, k->lf, (long)nV, k->d.nx, k->d.ny, k->d.ntheta);
-    CK(cudaGetLastError(), "to_slices launch");
+    log_to_log2_kernel<<<grid_for((long)nV), 256, 0, s>>>(lf, k->lf, (long)nV, k->d.nx, k->d.ny, k->d.ntheta);
+    CK(cudaGetLastError(), "log_to_log2 launch");
     ConvArgs a = conv_args(k, batch, EPI_LOG_OUT);
     a.in = k->lf;
-    a.in_scale = LOG2E;
     a.hint = k->hint_ws;
     a.out64 = lout;
     a.out_scale = LN2;
@@ -439,11 +352,12 @@ se2ot_status se2ot_barycenter(se2ot_kernel k, int n, const float *mu, const doub
     if (o.tol_viol < 0 || !std::isfinite(o.tol_viol)) return fail(SE2OT_EINVAL, "tol_viol invalid");
     Lambdas lam;
     double lsum = 0.0;
-    for (int i = 0; i < 64; ++i) lam.v[i] = 0.0;
+    for (int i = 0; i < 64; ++i) lam.v[i] = make_float2(0.f, 0.f);
     for (int i = 0; i < n; ++i) {
         if (!(lambda[i] >= 0.0) || !std::isfinite(lambda[i]))
             return fail(SE2OT_EINVAL, "lambda[%d]=%g not >= 0", i, lambda[i]);
-        lam.v[i] = lambda[i];
+        const float hi = (float)lambda[i];
+        lam.v[i] = make_float2(hi, (float)(lambda[i] - (double)hi));
         lsum += lambda[i];
     }
     if (std::fabs(lsum - 1.0) > 1e-12) return fail(SE2OT_EINVAL, "lambda sums to %.17g, not 1", lsum);
@@ -472,9 +386,7 @@ se2ot_status se2ot_barycenter(se2ot_kernel k, int n, const float *mu, const doub
     // validate the inputs on the device: masses (FP64) and the sign of every entry are checked by
     // the reductions below once log2 mu exists
     long long launches = 0;
-    init_kernel<<<grid_for((long)nV), 256, 0, s>>>(mu_dev, k->lmu, k->lv, k->h1, k->h2, (long)nV, k->d.nx,
-                                                   k->d.ny, k->d.ntheta);
-    CK(cudaGetLastError(), "init launch");
+    CK(launch_init(mu_dev, k->lmu, k->lv, k->h1, k->h2, n, k->d.nx, k->d.ny, k->d.ntheta, s), "init launch");
     ++launches;
 
     const bool timing = (o.flags & SE2OT_FLAG_TIME_CONV) != 0;
@@ -493,12 +405,12 @@ se2ot_status se2ot_barycenter(se2ot_kernel k, int n, const float *mu, const doub
     aw.in = k->lv;
     aw.hint = k->h1;
     aw.aux = k->lmu;
-    aw.out64 = k->lw;
+    aw.out2 = k->lw;
     ConvArgs ad = conv_args(k, n, EPI_D);
     ad.in = k->lw;
     ad.hint = k->h2;
     ad.aux = k->lv;
-    ad.out64 = k->ld;
+    ad.out2 = k->ld;
 
     int it = 0;
     double viol = NAN, mass = NAN;
@@ -509,13 +421,11 @@ se2ot_status se2ot_barycenter(se2ot_kernel k, int n, const float *mu, const doub
         if (st != SE2OT_OK) return st;
         st = run_conv(k, ad, s, &launches, e ? e[2] : nullptr, e ? e[3] : nullptr);
         if (st != SE2OT_OK) return st;
-        update_kernel<<<grid_for(V), 256, 0, s>>>(k->lv, k->ld, k->L, lam, n, V);
-        CK(cudaGetLastError(), "update launch");
+        CK(launch_update(k->lv, k->ld, k->L, lam, n, V, s), "update launch");
         ++launches;
         ++it;
         if (o.tol_viol > 0 && o.check_every > 0 && (it % o.check_every == 0) && it < max_it) {
-            stats_partial_kernel<<<RB, RT, 0, s>>>(k->L, k->ld, lam, n, V, k->partial);
-            stats_final_kernel<<<1, RT, 0, s>>>(k->partial, k->scal);
+            CK(launch_stats(k->L, k->ld, lam, n, V, k->partial, k->scal, s), "stats launch");
             launches += 2;
             double h[2];
             CK(cudaMemcpyAsync(h, k->scal, sizeof h, cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync(stats)");
@@ -526,10 +436,8 @@ se2ot_status se2ot_barycenter(se2ot_kernel k, int n, const float *mu, const doub
             }
         }
     }
-    finalize_kernel<<<grid_for(V), 256, 0, s>>>(k->L, bary_dev, V, k->d.nx, k->d.ny, k->d.ntheta);
-    stats_partial_kernel<<<RB, RT, 0, s>>>(k->L, k->ld, lam, n, V, k->partial);
-    stats_final_kernel<<<1, RT, 0, s>>>(k->partial, k->scal);
-    CK(cudaGetLastError(), "finalize launch");
+    CK(launch_finalize(k->L, bary_dev, k->d.nx, k->d.ny, k->d.ntheta, s), "finalize launch");
+    CK(launch_stats(k->L, k->ld, lam, n, V, k->partial, k->scal, s), "stats launch");
     launches += 3;
     if (bary_host)
         CK(cudaMemcpyAsync(bary, bary_dev, (size_t)V * sizeof(float), cudaMemcpyDeviceToHost, s),

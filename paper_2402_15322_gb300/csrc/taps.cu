@@ -7,11 +7,12 @@
 //   rho_b(u)^2 = (w1 b1)^2 + (w2 b2)^2 + (w3 b3)^2,
 //   (b1, b2) = R(-u_theta / 2) (u_x, u_y),  b3 = u_theta in [-pi, pi)          (Sec. 4.3)
 // evaluated in FP64.  Because b3 depends only on the orientation pair, the tap splits exactly into
-//   ltheta[o][i] = -(w3 b3)^2 / (eps ln 2)                      (FP64)
+//   ltheta[o][i] = -(w3 b3)^2 / (eps ln 2)                      (FP64, stored as double-float)
 //   ls[o][i][dy][dx] = -((w1 b1)^2 + (w2 b2)^2) / (eps ln 2)    (FP32 + FP32 rounding residual)
 // with ls <= 0 and ls = 0 at the zero offset; lsrow[o][i][dy] is the largest ls of each row.
 // A theta difference of exactly pi is taken as -pi (small-angle convention); rho_b is the same
 // for +pi and -pi, so the choice does not matter.
+#include "dfloat.cuh"
 #include "internal.h"
 
 namespace se2ot {
@@ -59,7 +60,7 @@ __global__ void spatial_taps_kernel(int nx, int ny, int nt, int r, double w1, do
     }
 }
 
-__global__ void theta_taps_kernel(int nt, int r, double w3, double eps, const float *ls, double *ltheta,
+__global__ void theta_taps_kernel(int nt, int r, double w3, double eps, const float *ls, float2 *ltheta,
                                   float *lsrow)
 {
     const int D = 2 * r + 1;
@@ -67,7 +68,7 @@ __global__ void theta_taps_kernel(int nt, int r, double w3, double eps, const fl
     if (p >= nt * nt) return;
     const int o = p / nt, i = p - o * nt;
     const double b3 = dtheta_pi(o, i, nt) * 3.14159265358979323846;
-    ltheta[p] = -(w3 * b3) * (w3 * b3) / eps * LOG2E;
+    ltheta[p] = df_from_double(-(w3 * b3) * (w3 * b3) / eps * LOG2E);
     for (int dyi = 0; dyi < D; ++dyi) {
         float m = -INFINITY;
         for (int dxi = 0; dxi < D; ++dxi) m = fmaxf(m, ls[((long)p * D + dyi) * D + dxi]);
