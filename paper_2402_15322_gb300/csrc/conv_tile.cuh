@@ -5,8 +5,8 @@
 // with the tap split exactly into its orientation factor lt(o, i) = -w3^2 dtheta^2 / (eps ln 2)
 // (double-float) and its spatial part ls = -(w1^2 b1^2 + w2^2 b2^2) / (eps ln 2) (FP32), Sec. 4.3.
 //
-// One CTA computes one output orientation o of a 32 x 32 spatial tile of one field; each of its
-// 128 threads owns 8 consecutive x positions of one row.  For every input orientation i that can
+// One CTA computes one output orientation o of a TY x TX spatial tile of one field; each thread
+// owns XQ consecutive x positions of one row.  For every input orientation i that can
 // contribute (see skipping), the CTA stages slice i of the input halo ((32 + 2R)^2, FP64 split
 // into FP32 hi + lo) and the (2R+1)^2 spatial taps of the pair in shared memory, then each thread
 // walks the rows of the window; the (2R+1)-tap row is fully unrolled (R is a template parameter).
@@ -21,11 +21,12 @@
 // of FP32's).  Outputs whose log2 sum leaves [-24, 16] are queued for the exact FP64 recompute of
 // conv.cu.
 //
-// Skipping (exact at FP32 resolution): a pair (o, i) is skipped when lt(o, i) + max(in over the
-// tile's halo of slice i) (from the tile-max pre-pass; the spatial taps are <= 0) is 2^-64 below
-// the smallest shift of the CTA; a row dy when the same bound with the row's largest spatial tap
-// and the largest input in the rows it reads is; and within a row, the window positions that
-// only meet taps below the row's threshold.  Skipped terms total < 2^-40 of the output.
+// Skipping (exact at FP32 resolution): a pair (o, i) is skipped by the CTA when lt(o, i) +
+// max(in over the tile's halo of slice i) (from the tile-max pre-pass; the spatial taps are <= 0)
+// is 2^-64 below the smallest shift of the CTA; a kernel row dy is skipped by a warp when the same
+// bound with the row's largest spatial tap and the largest input in the halo rows the warp reads
+// is 2^-64 below the warp's smallest shift; within a row, blocks of 4 window positions that
+// only meet taps below that threshold are skipped too.  Skipped terms total < 2^-40 of the output.
 #pragma once
 
 #include "dfloat.cuh"
@@ -34,7 +35,9 @@
 namespace se2ot {
 namespace tile {
 
-constexpr int TX = 32, TY = 32, XQ = 8, THREADS = 128;
+constexpr int TX = 32, TY = 16, XQ = 4, THREADS = 128;
+constexpr int WARP_ROWS = 4;               // output rows of one warp
+constexpr int ROW_LANES = TX / XQ;         // lanes per output row
 constexpr int MAX_NT = 64;   // largest ntheta (validated by the library)
 constexpr float SKIP_MARGIN = 64.f;
 constexpr float ACC_LO = -24.f, ACC_HI = 16.f;
@@ -49,7 +52,7 @@ __device__ __forceinline__ float ex2(float x)
 __host__ __device__ constexpr int halo_pitch(int hx)
 {
     // >= hx, multiple of 4 (16-byte rows for float4 loads) and 4 mod 32: the 8 lanes of a
-    // quarter-warp (4 x-groups of 8 floats, 2 rows) hit 32 distinct banks
+    // quarter-warp (x-groups of XQ floats over 32 / XQ rows) hit 32 distinct banks
     return ((hx + 27) / 32) * 32 + 4;
 }
 
@@ -58,7 +61,7 @@ __host__ __device__ constexpr int tap_pitch(int d) { return (d + 3) & ~3; }
 __host__ __device__ constexpr size_t smem_floats(int r)
 {
     return (size_t)2 * (TY + 2 * r) * halo_pitch(TX + 2 * r) + (size_t)(2 * r + 1) * tap_pitch(2 * r + 1) +
-           (size_t)(TY + 2 * r) + (size_t)(2 * r + 2) + 8 + 3 * MAX_NT + 8;
+           (size_t)(TY + 2 * r) + 8 + 3 * MAX_NT + 8;
 }
 
 __device__ __forceinline__ int wrapi(int v, int n)
@@ -91,7 +94,7 @@ __device__ __forceinline__ void write_out(const ConvArgs &a, long flat, int b, i
 }
 
 template <int R, bool MAXPASS>
-__global__ void __launch_bounds__(THREADS, 5) conv_tile_kernel(const ConvArgs a)
+__global__ void __launch_bounds__(THREADS, 6) conv_tile_kernel(const ConvArgs a)
 {
     constexpr int D = 2 * R + 1;
     constexpr int HX = TX + 2 * R, HY = TY + 2 * R, HXP = halo_pitch(HX), TP = tap_pitch(D);
@@ -102,14 +105,13 @@ __global__ void __launch_bounds__(THREADS, 5) conv_tile_kernel(const ConvArgs a)
     float *hlo = hhi + HY * HXP;
     float *ts = hlo + HY * HXP;            // [D][TP] spatial taps of the pair (hi)
     float *rowmax = ts + D * TP;           // [HY]
-    int *rowk = (int *)(rowmax + HY);      // [D] packed (first window index << 16 | last)
-    float *red = (float *)(rowk + ((D + 1) & ~1));   // [THREADS / 32] (even offset: float2 below)
+    float *red = rowmax + HY;              // [THREADS / 32]
     float2 *lts = (float2 *)(red + 8);     // [nt] orientation factors lt(o, i)
     int *need = (int *)(lts + MAX_NT);     // [nt] slice i contributes
 
     const int nx = a.nx, ny = a.ny, nt = a.nt;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int xl = (lane & 3) * XQ, yl = warp * 8 + (lane >> 2);
+    const int xl = (lane % ROW_LANES) * XQ, yl = warp * WARP_ROWS + lane / ROW_LANES;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int b = blockIdx.z / nt, o = blockIdx.z - b * nt;
     const long plane = (long)nx * ny;
@@ -132,13 +134,19 @@ __global__ void __launch_bounds__(THREADS, 5) conv_tile_kernel(const ConvArgs a)
         S[j] = s;
         acc[j] = MAXPASS ? -INFINITY : 0.f;
     }
+    float wmin = smin;   // smallest shift of the warp's outputs (row/column skipping)
     if (!MAXPASS) {
 #pragma unroll
-        for (int off = 16; off; off >>= 1) smin = fminf(smin, __shfl_xor_sync(0xffffffffu, smin, off));
-        if (lane == 0) red[warp] = smin;
+        for (int off = 16; off; off >>= 1) wmin = fminf(wmin, __shfl_xor_sync(0xffffffffu, wmin, off));
+        if (lane == 0) red[warp] = wmin;
     }
     __syncthreads();
-    if (!MAXPASS) smin = fminf(fminf(red[0], red[1]), fminf(red[2], red[3]));
+    // smallest shift of the CTA (slice skipping)
+    if (!MAXPASS) {
+        smin = red[0];
+#pragma unroll
+        for (int w = 1; w < THREADS / 32; ++w) smin = fminf(smin, red[w]);
+    }
 
     // which input slices can contribute: one thread per slice, from the tile-max pre-pass
     const long ntiles = (long)gridDim.x * gridDim.y;
@@ -205,26 +213,6 @@ __global__ void __launch_bounds__(THREADS, 5) conv_tile_kernel(const ConvArgs a)
                 if (lane == 0) rowmax[hy] = m;
             }
             __syncthreads();
-            // per kernel row d: the largest input the tile's outputs meet in it (output rows
-            // y0..y0+TY-1 read halo rows 2R-d .. 2R-d+TY-1), and the window positions whose taps
-            // can reach the skip threshold.  The spatial taps of a row are a concave quadratic in
-            // dx, so the taps >= thr form one interval [lo, hi]; a thread's window positions that
-            // meet them are k in [2R - hi, 2R - lo + XQ - 1].
-            for (int d = warp; d < D; d += THREADS / 32) {
-                float m = rowmax[2 * R - d + lane];   // TY == 32 rows, one per lane
-#pragma unroll
-                for (int off = 16; off; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
-                const float thr = smin - SKIP_MARGIN - 1.0f - m - lt.x;
-                const unsigned m0 = __ballot_sync(0xffffffffu, lane < D && ts[d * TP + lane] >= thr);
-                const unsigned m1 = __ballot_sync(0xffffffffu, lane + 32 < D && ts[d * TP + lane + 32] >= thr);
-                int lo, hi;
-                if (m0) lo = __ffs(m0) - 1;
-                else lo = m1 ? 32 + __ffs(m1) - 1 : D;
-                if (m1) hi = 32 + 31 - __clz(m1);
-                else hi = m0 ? 31 - __clz(m0) : -1;
-                if (lane == 0) rowk[d] = hi < lo ? -1 : ((2 * R - hi) << 16) | (2 * R - lo + XQ - 1);
-            }
-            __syncthreads();
         }
 
         // per-slice shift with the orientation factor folded in: S'_j = S_j - lt as hi + lo
@@ -240,10 +228,23 @@ __global__ void __launch_bounds__(THREADS, 5) conv_tile_kernel(const ConvArgs a)
         for (int dyi = 0; dyi < D; ++dyi) {
             int klo = 0, khi = WIN - 1;
             if (!MAXPASS) {
-                const int rk = rowk[dyi];
-                if (rk < 0) continue;   // no tap of the row can reach the threshold
-                klo = rk >> 16;
-                khi = rk & 0xffff;
+                // kernel row dyi for this warp: its WARP_ROWS output rows read halo rows
+                // wy + 2R - dyi .. wy + 2R - dyi + WARP_ROWS - 1 (wy = WARP_ROWS * warp).  Largest
+                // input there:
+                float m = lane < WARP_ROWS ? rowmax[WARP_ROWS * warp + 2 * R - dyi + lane] : -INFINITY;
+#pragma unroll
+                for (int off = 16; off; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+                // taps that can matter: ls >= thr.  The spatial taps of a row are a concave
+                // quadratic in dx, so they form one interval [lo, hi] of dx indices; a thread's
+                // window positions that meet them are k in [2R - hi, 2R - lo + XQ - 1].
+                const float thr = wmin - SKIP_MARGIN - 1.0f - m - lt.x;
+                const unsigned m0 = __ballot_sync(0xffffffffu, lane < D && ts[dyi * TP + lane] >= thr);
+                const unsigned m1 = D > 32 ? __ballot_sync(0xffffffffu, lane + 32 < D && ts[dyi * TP + lane + 32] >= thr) : 0u;
+                if (!(m0 | m1)) continue;   // no tap of the row can reach the threshold (uniform over the warp)
+                const int lo = m0 ? __ffs(m0) - 1 : 32 + __ffs(m1) - 1;
+                const int hi = m1 ? 63 - __clz(m1) : 31 - __clz(m0);
+                klo = 2 * R - hi;
+                khi = 2 * R - lo + XQ - 1;
             }
             rows_eval += (unsigned)(min(WIN4 - 1, khi >> 2) - (klo >> 2) + 1);
             const float *rh = hhi + (yl + 2 * R - dyi) * HXP + xl;
@@ -289,9 +290,9 @@ __global__ void __launch_bounds__(THREADS, 5) conv_tile_kernel(const ConvArgs a)
     }
 
     // terms evaluated: per block of 4 window positions, on average 4 * XQ * D / WIN terms for each
-    // of the tile's TX * TY / XQ thread rows
-    if (tid == 0 && a.eval_count)
-        atomicAdd(a.eval_count, (unsigned long long)((double)rows_eval * 4 * TX * TY * D / WIN));
+    // of the warp's 32 threads
+    if (lane == 0 && a.eval_count)
+        atomicAdd(a.eval_count, (unsigned long long)((double)rows_eval * 4 * 32 * XQ * D / WIN));
 
 #pragma unroll
     for (int j = 0; j < XQ; ++j) {
