@@ -14,6 +14,7 @@ bool launch_tile_c(int r, bool maxpass, const ConvArgs &a, cudaStream_t s, cudaE
 
 namespace {
 
+// Tile-max pre-pass, for inputs whose tile maxima no producer wrote (apply calls; periodic grids).
 // tmax[b][i][tile]: largest input (hi part) of slice i over
 //   zero boundary: the tile itself (32 x 32, clipped to the grid); the convolution takes the max
 //                  over the 3 x 3 neighbouring tiles, which cover the tile's halo since r < 32;
@@ -123,10 +124,12 @@ size_t conv_smem_bytes(int r) { return sizeof(float) * tile::smem_floats(r); }
 
 cudaError_t launch_conv(const ConvArgs &a, cudaStream_t s)
 {
-    dim3 g((a.nx + tile::TX - 1) / tile::TX, (a.ny + tile::TY - 1) / tile::TY, a.batch * a.nt);
-    tile_max_kernel<<<g, 256, 0, s>>>(a);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    if (!a.tmax_ready || a.periodic) {
+        dim3 g((a.nx + tile::TX - 1) / tile::TX, (a.ny + tile::TY - 1) / tile::TY, a.batch * a.nt);
+        tile_max_kernel<<<g, 256, 0, s>>>(a);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     return dispatch(a, false, s);
 }
 

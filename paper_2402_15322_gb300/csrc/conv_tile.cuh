@@ -35,7 +35,7 @@
 namespace se2ot {
 namespace tile {
 
-constexpr int TX = 32, TY = 16, XQ = 4, THREADS = 128;
+constexpr int TX = TILE_X, TY = TILE_Y, XQ = 4, THREADS = 128;
 constexpr int WARP_ROWS = 4;               // output rows of one warp
 constexpr int ROW_LANES = TX / XQ;         // lanes per output row
 constexpr int MAX_NT = 64;   // largest ntheta (validated by the library)
@@ -294,6 +294,7 @@ __global__ void __launch_bounds__(THREADS, 6) conv_tile_kernel(const ConvArgs a)
     if (lane == 0 && a.eval_count)
         atomicAdd(a.eval_count, (unsigned long long)((double)rows_eval * 4 * 32 * XQ * D / WIN));
 
+    float omax = -INFINITY;   // largest output written (hi part), for the next convolution's skipping
 #pragma unroll
     for (int j = 0; j < XQ; ++j) {
         if (!valid[j]) continue;
@@ -306,9 +307,22 @@ __global__ void __launch_bounds__(THREADS, 6) conv_tile_kernel(const ConvArgs a)
         if (!(lacc >= ACC_LO && lacc <= ACC_HI)) {
             const unsigned k = atomicAdd(a.redo_count, 1u);
             a.redo_list[k] = (int)flat;
+            omax = INFINITY;          // value unknown until the exact recompute: no skipping on it
             continue;
         }
         write_out(a, flat, b, o, gy, x0 + xl + j, S[j], lacc);
+        if (a.tmax_out) omax = fmaxf(omax, a.out2[flat].x);
+    }
+    if (!MAXPASS && a.tmax_out) {   // uniform over the CTA
+#pragma unroll
+        for (int off = 16; off; off >>= 1) omax = fmaxf(omax, __shfl_xor_sync(0xffffffffu, omax, off));
+        __syncthreads();
+        if (lane == 0) red[warp] = omax;
+        __syncthreads();
+        if (tid == 0) {
+            for (int w = 1; w < THREADS / 32; ++w) omax = fmaxf(omax, red[w]);
+            a.tmax_out[((long)b * nt + o) * ntiles + blockIdx.y * gridDim.x + blockIdx.x] = omax;
+        }
     }
 }
 

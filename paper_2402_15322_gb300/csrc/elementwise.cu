@@ -47,16 +47,53 @@ __global__ void init_kernel(const float *mu, float2 *lmu, float2 *lv, float *h1,
     }
 }
 
-__global__ void update_kernel(float2 *lv, const float2 *ld, float2 *L, Lambdas lam, int n, long V)
+// One CTA per (spatial tile of the convolution, orientation slice): 256 threads over the tile's
+// voxels.  Besides the update it writes the inner-tile maximum of every new lv_i (hi part), which
+// the next w-convolution uses to skip orientation pairs.
+__global__ void __launch_bounds__(256) update_kernel(float2 *lv, const float2 *ld, float2 *L, Lambdas lam, int n,
+                                                     int nx, int ny, int nt, float *tmax_v)
 {
-    for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < V; g += (long)gridDim.x * blockDim.x) {
+    constexpr int TX = TILE_X, TY = TILE_Y;   // the convolution's tile
+    static_assert(TX * TY == 512, "two voxels per thread");
+    const long plane = (long)nx * ny, V = plane * nt;
+    const int t = blockIdx.z;
+    const long ntiles = (long)gridDim.x * gridDim.y;
+    __shared__ float red[8];
+    long gi[2];
+    bool ok[2];
+    float2 Lg[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int e = threadIdx.x + 256 * k;            // TX * TY = 512 voxels, 2 per thread
+        const int y = blockIdx.y * TY + e / TX, x = blockIdx.x * TX + e % TX;
+        ok[k] = y < ny && x < nx;
+        gi[k] = (long)t * plane + (long)y * nx + x;
         float2 acc = make_float2(0.f, 0.f);
-        for (int i = 0; i < n; ++i)
-            if (lam.v[i].x != 0.f) acc = df_add(acc, df_mul(ld[(long)i * V + g], lam.v[i]));
-        L[g] = acc;
-        for (int i = 0; i < n; ++i) {
-            const long e = (long)i * V + g;
-            lv[e] = df_add(lv[e], df_add(acc, df_neg(ld[e])));
+        if (ok[k])
+            for (int i = 0; i < n; ++i)
+                if (lam.v[i].x != 0.f) acc = df_add(acc, df_mul(ld[(long)i * V + gi[k]], lam.v[i]));
+        Lg[k] = acc;
+        if (ok[k]) L[gi[k]] = acc;
+    }
+    for (int i = 0; i < n; ++i) {
+        float m = -INFINITY;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            if (!ok[k]) continue;
+            const long e = (long)i * V + gi[k];
+            const float2 nv = df_add(lv[e], df_add(Lg[k], df_neg(ld[e])));
+            lv[e] = nv;
+            m = fmaxf(m, nv.x);
+        }
+        if (!tmax_v) continue;   // uniform
+#pragma unroll
+        for (int off = 16; off; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int w = 1; w < 8; ++w) m = fmaxf(m, red[w]);
+            tmax_v[((long)i * nt + t) * ntiles + blockIdx.y * gridDim.x + blockIdx.x] = m;
         }
     }
 }
@@ -129,10 +166,11 @@ cudaError_t launch_init(const float *mu, float2 *lmu, float2 *lv, float *h1, flo
     return cudaGetLastError();
 }
 
-cudaError_t launch_update(float2 *lv, const float2 *ld, float2 *L, const Lambdas &lam, int n, long V,
-                          cudaStream_t s)
+cudaError_t launch_update(float2 *lv, const float2 *ld, float2 *L, const Lambdas &lam, int n, int nx, int ny,
+                          int nt, float *tmax_v, cudaStream_t s)
 {
-    update_kernel<<<grid_for(V), 256, 0, s>>>(lv, ld, L, lam, n, V);
+    dim3 g((nx + TILE_X - 1) / TILE_X, (ny + TILE_Y - 1) / TILE_Y, nt);
+    update_kernel<<<g, 256, 0, s>>>(lv, ld, L, lam, n, nx, ny, nt, tmax_v);
     return cudaGetLastError();
 }
 

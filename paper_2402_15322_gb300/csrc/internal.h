@@ -11,6 +11,7 @@
 namespace se2ot {
 
 constexpr int MAX_RADIUS = 16;   // the convolution is instantiated for radii 0..16
+constexpr int TILE_X = 32, TILE_Y = 16;   // spatial tile of one convolution CTA (and of the tile maxima)
 
 // Where the result of one convolution goes (the fused epilogues of the barycenter loop).
 enum Epilogue : int {
@@ -29,8 +30,10 @@ struct ConvArgs {
     const float *ls;         // [o][i][dy][dx] spatial part of the tap (FP32)
     const float *ls_lo;      // same layout: FP64 value - ls (rounding residual)
     const float *lsrow;      // [o][i][dy] largest spatial tap of each row
-    const float *tmax;       // [batch][nt][tiles] largest input over each tile's halo
-    float *tmax_w;           // the same buffer, written by the pre-pass
+    const float *tmax;       // [batch][nt][tiles] largest input per tile (see tmax_ready)
+    float *tmax_w;           // the same buffer, written by the pre-pass when tmax_ready == 0
+    int tmax_ready;          // 1: tmax already holds the inner-tile maxima of `in` (zero boundary)
+    float *tmax_out;         // EPI_W/EPI_D: inner-tile maxima of the output (hi), or NULL
     float *hint;             // [batch][nt][ny][nx] shift per output (read; written with c)
     const float2 *aux;       // EPI_W: log2 mu_i; EPI_D: log2 v_i
     float2 *out2;            // EPI_W / EPI_D destination (log2 w_i, log2 d_i)
@@ -73,9 +76,9 @@ struct Lambdas {
 // lmu = log2 mu (caller layout -> slice-major), lv = 0, hint1 = 0, hint2 = lmu
 cudaError_t launch_init(const float *mu, float2 *lmu, float2 *lv, float *h1, float *h2, int n, int nx, int ny,
                         int nt, cudaStream_t s);
-// L = sum_i lambda_i ld_i ; lv_i += L - ld_i
-cudaError_t launch_update(float2 *lv, const float2 *ld, float2 *L, const Lambdas &lam, int n, long V,
-                          cudaStream_t s);
+// L = sum_i lambda_i ld_i ; lv_i += L - ld_i ; tmax_v (if not NULL) = inner-tile maxima of lv
+cudaError_t launch_update(float2 *lv, const float2 *ld, float2 *L, const Lambdas &lam, int n, int nx, int ny,
+                          int nt, float *tmax_v, cudaStream_t s);
 // bary (caller layout) = 2^L
 cudaError_t launch_finalize(const float2 *L, float *bary, int nx, int ny, int nt, cudaStream_t s);
 // scal[0] = sum 2^L, scal[1] = sum_i lambda_i |2^ld_i - 2^L| / scal[0]  (FP64, fixed order)

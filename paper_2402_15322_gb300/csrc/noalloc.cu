@@ -143,6 +143,7 @@ extern "C" se2ot_status se2ot_barycenter_noalloc(const se2ot_kernel_desc *desc, 
     dry.take<float>(npair * D * D);
     dry.take<float>(npair * D);
     dry.take<float>(ntmax);
+    dry.take<float>(ntmax);
     for (int k = 0; k < 4; ++k) dry.take<float2>(nV);
     dry.take<float2>((size_t)V);
     dry.take<float>(nV);
@@ -166,6 +167,7 @@ extern "C" se2ot_status se2ot_barycenter_noalloc(const se2ot_kernel_desc *desc, 
     taps.ls_lo = c.take<float>(npair * D * D);
     taps.lsrow = c.take<float>(npair * D);
     float *tmax = c.take<float>(ntmax);
+    float *tmax2 = c.take<float>(ntmax);
     float2 *lmu = c.take<float2>(nV), *lv = c.take<float2>(nV), *lw = c.take<float2>(nV), *ld = c.take<float2>(nV);
     float2 *L = c.take<float2>((size_t)V);
     float *h1 = c.take<float>(nV), *h2 = c.take<float>(nV);
@@ -184,6 +186,8 @@ extern "C" se2ot_status se2ot_barycenter_noalloc(const se2ot_kernel_desc *desc, 
     NCK(cudaMemsetAsync(totals, 0, 2 * sizeof(unsigned long long), s), "cudaMemsetAsync");
     NCK(build_taps(*desc, taps, s), "tap build");
     NCK(launch_init(mu, lmu, lv, h1, h2, n, desc->nx, desc->ny, nt, s), "init launch");
+    const bool fused_max = desc->boundary == SE2OT_BOUNDARY_ZERO;
+    if (fused_max) NCK(cudaMemsetAsync(tmax, 0, ntmax * sizeof(float), s), "cudaMemsetAsync(tmax)");
     long long launches = 3;
 
     ConvArgs aw;
@@ -211,11 +215,16 @@ extern "C" se2ot_status se2ot_barycenter_noalloc(const se2ot_kernel_desc *desc, 
     aw.hint = h1;
     aw.aux = lmu;
     aw.out2 = lw;
+    aw.tmax_ready = fused_max;
+    aw.tmax_out = fused_max ? tmax2 : nullptr;
     ad.epi = EPI_D;
     ad.in = lw;
     ad.hint = h2;
     ad.aux = lv;
     ad.out2 = ld;
+    ad.tmax = tmax2;
+    ad.tmax_w = tmax2;
+    ad.tmax_ready = fused_max;
 
     int it = 0;
     bool converged = false;
@@ -224,9 +233,9 @@ extern "C" se2ot_status se2ot_barycenter_noalloc(const se2ot_kernel_desc *desc, 
             NCK(cudaMemsetAsync(count, 0, sizeof(unsigned), s), "cudaMemsetAsync");
             NCK(launch_conv(*a, s), "conv launch");
             NCK(launch_redo(*a, 2 * sms, s), "redo launch");
-            launches += 3;
+            launches += fused_max ? 2 : 3;
         }
-        NCK(launch_update(lv, ld, L, lam, n, V, s), "update launch");
+        NCK(launch_update(lv, ld, L, lam, n, desc->nx, desc->ny, nt, fused_max ? tmax : nullptr, s), "update launch");
         ++launches;
         ++it;
         if (o.tol_viol > 0 && o.check_every > 0 && it % o.check_every == 0 && it < o.max_iters) {

@@ -128,8 +128,8 @@ struct se2ot_kernel_s {
     float *hint_ws = nullptr;
     size_t c_hint_ws = 0;
     double *partial = nullptr, *scal = nullptr;
-    float *tmax = nullptr;
-    size_t c_tmax = 0;
+    float *tmax = nullptr, *tmax2 = nullptr;   // tile maxima of lv (and apply inputs), of lw
+    size_t c_tmax = 0, c_tmax2 = 0;
     std::vector<cudaEvent_t> ev;
 };
 
@@ -167,6 +167,7 @@ se2ot_status ensure_solver_ws(se2ot_kernel k, int n)
     CK(grow(k->h2, k->c_h2, nV), "cudaMalloc(hint)");
     CK(grow(k->redo, k->c_redo, nV), "cudaMalloc(redo)");
     CK(grow(k->tmax, k->c_tmax, (size_t)n * k->d.ntheta * conv_tiles(k->d.nx, k->d.ny)), "cudaMalloc(tmax)");
+    CK(grow(k->tmax2, k->c_tmax2, (size_t)n * k->d.ntheta * conv_tiles(k->d.nx, k->d.ny)), "cudaMalloc(tmax)");
     return SE2OT_OK;
 }
 
@@ -204,7 +205,7 @@ se2ot_status run_conv(se2ot_kernel k, const ConvArgs &a, cudaStream_t s, long lo
     CK(launch_conv(a, s), "conv launch");
     if (t1) CK(cudaEventRecord(t1, s), "cudaEventRecord");
     CK(launch_redo(a, 2 * k->sms, s), "redo launch");
-    if (launches) *launches += 3;   // tile-max pre-pass, convolution, exact recompute
+    if (launches) *launches += (a.tmax_ready && !a.periodic) ? 2 : 3;   // [tile-max pre-pass,] conv, recompute
     return SE2OT_OK;
 }
 
@@ -264,7 +265,7 @@ se2ot_status se2ot_kernel_destroy(se2ot_kernel k)
 {
     if (!k) return SE2OT_OK;
     cudaDeviceSynchronize();
-    void *ptrs[] = {k->taps.ltheta, k->taps.ls, k->taps.ls_lo, k->taps.lsrow, k->tmax, k->lmu, k->lv, k->lw, k->ld, k->L, k->lf, k->h1, k->h2, k->hint_ws,
+    void *ptrs[] = {k->taps.ltheta, k->taps.ls, k->taps.ls_lo, k->taps.lsrow, k->tmax, k->tmax2, k->lmu, k->lv, k->lw, k->ld, k->L, k->lf, k->h1, k->h2, k->hint_ws,
                     k->mu_stage, k->bary_stage, k->redo, k->counters, k->redo_total, k->partial, k->scal};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -387,6 +388,10 @@ se2ot_status se2ot_barycenter(se2ot_kernel k, int n, const float *mu, const doub
     // the reductions below once log2 mu exists
     long long launches = 0;
     CK(launch_init(mu_dev, k->lmu, k->lv, k->h1, k->h2, n, k->d.nx, k->d.ny, k->d.ntheta, s), "init launch");
+    // tile maxima of lv = 0 for the first w-convolution (the update kernel writes them afterwards)
+    const bool fused_max = k->d.boundary == SE2OT_BOUNDARY_ZERO;
+    const size_t ntm = (size_t)n * k->d.ntheta * conv_tiles(k->d.nx, k->d.ny);
+    if (fused_max) CK(cudaMemsetAsync(k->tmax, 0, ntm * sizeof(float), s), "cudaMemsetAsync(tmax)");
     ++launches;
 
     const bool timing = (o.flags & SE2OT_FLAG_TIME_CONV) != 0;
@@ -406,11 +411,16 @@ se2ot_status se2ot_barycenter(se2ot_kernel k, int n, const float *mu, const doub
     aw.hint = k->h1;
     aw.aux = k->lmu;
     aw.out2 = k->lw;
+    aw.tmax_ready = fused_max;
+    aw.tmax_out = fused_max ? k->tmax2 : nullptr;   // tile maxima of lw, for the d-convolution
     ConvArgs ad = conv_args(k, n, EPI_D);
     ad.in = k->lw;
     ad.hint = k->h2;
     ad.aux = k->lv;
     ad.out2 = k->ld;
+    ad.tmax = k->tmax2;
+    ad.tmax_w = k->tmax2;
+    ad.tmax_ready = fused_max;
 
     int it = 0;
     double viol = NAN, mass = NAN;
@@ -421,7 +431,8 @@ se2ot_status se2ot_barycenter(se2ot_kernel k, int n, const float *mu, const doub
         if (st != SE2OT_OK) return st;
         st = run_conv(k, ad, s, &launches, e ? e[2] : nullptr, e ? e[3] : nullptr);
         if (st != SE2OT_OK) return st;
-        CK(launch_update(k->lv, k->ld, k->L, lam, n, V, s), "update launch");
+        CK(launch_update(k->lv, k->ld, k->L, lam, n, k->d.nx, k->d.ny, k->d.ntheta, fused_max ? k->tmax : nullptr, s),
+           "update launch");
         ++launches;
         ++it;
         if (o.tol_viol > 0 && o.check_every > 0 && (it % o.check_every == 0) && it < max_it) {
