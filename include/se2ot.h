@@ -171,6 +171,15 @@ SE2OT_API se2ot_status se2ot_interpolate(se2ot_kernel k, const float *mu0, const
                                const se2ot_solve_opts *opts, float *out, se2ot_stats *stats,
                                void *stream);
 
+/* State of the kernel handle's most recent se2ot_barycenter / se2ot_interpolate solve with n
+ * measures, for checkpointing and for checking the iteration's invariants: natural logarithms of
+ * the scaling vectors v_i and of the marginals d_i = v_i (K w_i) (n*V doubles each) and of the
+ * barycenter mu = prod_i d_i^lambda_i (V doubles), in the caller's layout [i][y][x][theta]
+ * (Appendix A, after the last v-update).  Any output pointer may be NULL.  Device pointers only
+ * (EINVAL otherwise); n must equal the solve's.  Enqueued on `stream`. */
+SE2OT_API se2ot_status se2ot_state_export(se2ot_kernel k, int n, double *log_v, double *log_d, double *log_mu,
+                                          void *stream);
+
 /* Size of the device array behind se2ot_barycenter_noalloc: 16 MiB on every GPU that loads the
  * library, held until the process exits. */
 #define SE2OT_NOALLOC_SCRATCH_BYTES (16u << 20)

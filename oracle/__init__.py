@@ -36,6 +36,8 @@ def _lib():
         conv = [_I, _I, _I, _I, _D, _D, _D, _D, _I, _I, _P, _P]
         lib.or_conv_lin.argtypes = conv
         lib.or_conv_log.argtypes = conv
+        lib.or_conv_log_points.argtypes = [_I, _I, _I, _I, _D, _D, _D, _D, _I, _P, ctypes.c_long,
+                                           ctypes.POINTER(ctypes.c_long), _P]
         lib.or_barycenter_lin.argtypes = [_I, _I, _I, _I, _D, _D, _D, _D, _I, _I, _P, _P, _I,
                                           _P, _P, _P, _P, _P]
         lib.or_barycenter_log.argtypes = [_I, _I, _I, _I, _D, _D, _D, _D, _I, _I, _P, _P, _I,
@@ -128,6 +130,16 @@ def conv_log(grid, lf):
     batch = lf.size // grid.V
     out = np.zeros_like(lf)
     _lib().or_conv_log(*grid._args(), int(grid.periodic), batch, _ptr(lf), _ptr(out))
+    return out
+
+
+def conv_log_points(grid, lf, idx):
+    """log(K * exp(lf)) at the flat output indices idx (layout [b, y, x, k]) only."""
+    lf = _arr(lf)
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    out = np.zeros(idx.size)
+    _lib().or_conv_log_points(*grid._args(), int(grid.periodic), _ptr(lf), idx.size,
+                              idx.ctypes.data_as(ctypes.POINTER(ctypes.c_long)), _ptr(out))
     return out
 
 

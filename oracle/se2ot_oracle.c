@@ -21,7 +21,8 @@
  *   or_conv_lin                  -- (K * f)(g) = sum_h K(h^-1 g) f(h), Sec. 4.2, as a
  *                                   plain triple loop (uniform Haar weights, Sec. 2.3).
  *   or_conv_log                  -- log (K * exp(lf)), the same sum in the log domain with
- *                                   a per-output max shift (exact algebra).
+ *                                   a per-output max shift (exact algebra); or_conv_log_points
+ *                                   evaluates it at selected outputs only.
  *   or_barycenter_lin            -- Appendix A algorithm, literally, in the linear domain.
  *   or_barycenter_log            -- Appendix A algorithm with every scaling vector kept as
  *                                   its logarithm (same steps, same order).
@@ -166,10 +167,40 @@ void or_conv_lin(int nx, int ny, int nth, int r, double w1, double w2, double w3
     free(kt);
 }
 
-/* lout = log(K * exp(lf)), computed per output as M + log(sum exp(term - M)) with M the
- * largest term.  A term below M - 746 has exp(term - M) == +0.0 in double precision, so
- * skipping its exp() leaves the sum bit-identical.  Entries of lf equal to -inf are
- * zero densities and contribute no term. */
+/* One output of the log-domain convolution: log sum_{i, dy, dx} exp(lk + lf[b][y-dy][x-dx][i])
+ * evaluated as M + log(sum exp(term - M)) with M the largest term.  A term below M - 746 has
+ * exp(term - M) == +0.0 in double precision, so skipping its exp() leaves the sum bit-identical.
+ * Entries of lf equal to -inf are zero densities and contribute no term. */
+static double or_conv_log_one(int nx, int ny, int nth, int r, const double *lk, int periodic,
+                              const double *lf_b, int y, int x, int o)
+{
+    int D = 2 * r + 1;
+    double M = -INFINITY;
+    for (int i = 0; i < nth; ++i)
+        for (int dy = -r; dy <= r; ++dy)
+            for (int dx = -r; dx <= r; ++dx) {
+                long s = or_src(y, x, dy, dx, nx, ny, periodic);
+                if (s < 0) continue;
+                double t = lk[((size_t)(o * nth + i) * D + (dy + r)) * D + (dx + r)] + lf_b[(size_t)s * nth + i];
+                if (t > M) M = t;
+            }
+    double acc = 0.0;
+    if (M > -INFINITY) {
+        for (int i = 0; i < nth; ++i)
+            for (int dy = -r; dy <= r; ++dy)
+                for (int dx = -r; dx <= r; ++dx) {
+                    long s = or_src(y, x, dy, dx, nx, ny, periodic);
+                    if (s < 0) continue;
+                    double t = lk[((size_t)(o * nth + i) * D + (dy + r)) * D + (dx + r)] +
+                               lf_b[(size_t)s * nth + i] - M;
+                    if (t < -746.0) continue;
+                    acc += exp(t);
+                }
+    }
+    return M + log(acc);
+}
+
+/* lout = log(K * exp(lf)) for every output (Sec. 4.2 in the log domain). */
 void or_conv_log(int nx, int ny, int nth, int r, double w1, double w2, double w3, double eps,
                  int periodic, int batch, const double *lf, double *lout)
 {
@@ -181,32 +212,30 @@ void or_conv_log(int nx, int ny, int nth, int r, double w1, double w2, double w3
     for (int b = 0; b < batch; ++b)
         for (int y = 0; y < ny; ++y)
             for (int x = 0; x < nx; ++x)
-                for (int o = 0; o < nth; ++o) {
-                    double M = -INFINITY;
-                    for (int i = 0; i < nth; ++i)
-                        for (int dy = -r; dy <= r; ++dy)
-                            for (int dx = -r; dx <= r; ++dx) {
-                                long s = or_src(y, x, dy, dx, nx, ny, periodic);
-                                if (s < 0) continue;
-                                double t = lk[((size_t)(o * nth + i) * D + (dy + r)) * D + (dx + r)] +
-                                           lf[b * V + (size_t)s * nth + i];
-                                if (t > M) M = t;
-                            }
-                    double acc = 0.0;
-                    if (M > -INFINITY) {
-                        for (int i = 0; i < nth; ++i)
-                            for (int dy = -r; dy <= r; ++dy)
-                                for (int dx = -r; dx <= r; ++dx) {
-                                    long s = or_src(y, x, dy, dx, nx, ny, periodic);
-                                    if (s < 0) continue;
-                                    double t = lk[((size_t)(o * nth + i) * D + (dy + r)) * D + (dx + r)] +
-                                               lf[b * V + (size_t)s * nth + i] - M;
-                                    if (t < -746.0) continue;
-                                    acc += exp(t);
-                                }
-                    }
-                    lout[b * V + ((size_t)y * nx + x) * nth + o] = M + log(acc);
-                }
+                for (int o = 0; o < nth; ++o)
+                    lout[b * V + ((size_t)y * nx + x) * nth + o] =
+                        or_conv_log_one(nx, ny, nth, r, lk, periodic, lf + b * V, y, x, o);
+    free(lk);
+}
+
+/* The same as or_conv_log at the npts outputs whose flat indices (layout [b][y][x][o]) are idx[k]:
+ * lout[k] = log(K * exp(lf))(idx[k]).  For grids too large to convolve whole on the CPU. */
+void or_conv_log_points(int nx, int ny, int nth, int r, double w1, double w2, double w3, double eps,
+                        int periodic, const double *lf, long npts, const long *idx, double *lout)
+{
+    int D = 2 * r + 1;
+    size_t V = (size_t)nx * ny * nth;
+    double *lk = (double *)malloc(sizeof(double) * (size_t)nth * nth * D * D);
+    or_taps(nx, ny, nth, r, w1, w2, w3, eps, lk);
+#pragma omp parallel for schedule(dynamic, 16)
+    for (long k = 0; k < npts; ++k) {
+        long f = idx[k];
+        long b = f / (long)V, g = f % (long)V;
+        int o = (int)(g % nth);
+        long p = g / nth;
+        int x = (int)(p % nx), y = (int)(p / nx);
+        lout[k] = or_conv_log_one(nx, ny, nth, r, lk, periodic, lf + b * V, y, x, o);
+    }
     free(lk);
 }
 

@@ -74,6 +74,13 @@ __global__ void lin_to_log2_kernel(const float *f, float2 *out, long n, int nx, 
         out[e] = df_from_double(log2((double)f[user_index(e, nx, ny, nt)]));
 }
 
+// state export: slice-major double-float base-2 logs -> natural logs in the caller layout
+__global__ void export_kernel(const float2 *src, double *dst, long n, int nx, int ny, int nt)
+{
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x)
+        dst[user_index(e, nx, ny, nt)] = df_to_double(src[e]) * LN2;
+}
+
 // apply_log: natural logs in the caller layout -> base-2 logs, slice-major double-float
 __global__ void log_to_log2_kernel(const double *f, float2 *out, long n, int nx, int ny, int nt)
 {
@@ -129,6 +136,7 @@ struct se2ot_kernel_s {
     size_t c_hint_ws = 0;
     double *partial = nullptr, *scal = nullptr;
     float *tmax = nullptr, *tmax2 = nullptr;   // tile maxima of lv (and apply inputs), of lw
+    int last_n = 0;                            // measures of the last completed solve
     size_t c_tmax = 0, c_tmax2 = 0;
     std::vector<cudaEvent_t> ev;
 };
@@ -461,6 +469,7 @@ se2ot_status se2ot_barycenter(se2ot_kernel k, int n, const float *mu, const doub
     CK(cudaStreamSynchronize(s), "cudaStreamSynchronize");
     mass = h[0];
     viol = h[1];
+    k->last_n = n;
     const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - wall0).count();
     if (stats) {
         std::memset(stats, 0, sizeof *stats);
@@ -489,6 +498,22 @@ se2ot_status se2ot_barycenter(se2ot_kernel k, int n, const float *mu, const doub
         return fail(SE2OT_ENONFINITE, "non-finite iterate (mass=%g, viol=%g)", mass, viol);
     if (o.tol_viol > 0 && !converged && !(viol <= o.tol_viol))
         return fail(SE2OT_ENOTCONV, "viol=%g > tol=%g after %d iterations", viol, o.tol_viol, it);
+    return SE2OT_OK;
+}
+
+se2ot_status se2ot_state_export(se2ot_kernel k, int n, double *log_v, double *log_d, double *log_mu, void *stream)
+{
+    if (!k) return fail(SE2OT_EINVAL, "NULL kernel");
+    if (k->last_n == 0) return fail(SE2OT_EINVAL, "no completed solve on this kernel handle");
+    if (n != k->last_n) return fail(SE2OT_EINVAL, "n=%d but the last solve had %d measures", n, k->last_n);
+    for (const void *p : {(const void *)log_v, (const void *)log_d, (const void *)log_mu})
+        if (p && !is_device_ptr(p)) return fail(SE2OT_EINVAL, "state export needs device pointers");
+    cudaStream_t s = (cudaStream_t)stream;
+    const long V = k->V, nV = (long)n * V;
+    if (log_v) export_kernel<<<grid_for(nV), 256, 0, s>>>(k->lv, log_v, nV, k->d.nx, k->d.ny, k->d.ntheta);
+    if (log_d) export_kernel<<<grid_for(nV), 256, 0, s>>>(k->ld, log_d, nV, k->d.nx, k->d.ny, k->d.ntheta);
+    if (log_mu) export_kernel<<<grid_for(V), 256, 0, s>>>(k->L, log_mu, V, k->d.nx, k->d.ny, k->d.ntheta);
+    CK(cudaGetLastError(), "export launch");
     return SE2OT_OK;
 }
 

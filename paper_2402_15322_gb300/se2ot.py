@@ -79,13 +79,15 @@ def lib():
                                    ctypes.POINTER(se2ot_stats), vp]
     L.se2ot_interpolate.argtypes = [vp, vp, vp, d, ctypes.POINTER(se2ot_solve_opts), vp,
                                     ctypes.POINTER(se2ot_stats), vp]
+    L.se2ot_state_export.argtypes = [vp, i, vp, vp, vp, vp]
     L.se2ot_barycenter_noalloc.argtypes = [ctypes.POINTER(se2ot_kernel_desc), i, vp, vp,
                                            ctypes.POINTER(se2ot_solve_opts), vp,
                                            ctypes.POINTER(se2ot_stats), vp]
     L.se2ot_last_error.restype = ctypes.c_char_p
     L.se2ot_version.restype = ctypes.c_char_p
     for name in ("se2ot_kernel_build", "se2ot_kernel_destroy", "se2ot_kernel_taps", "se2ot_apply",
-                 "se2ot_apply_log", "se2ot_barycenter", "se2ot_interpolate", "se2ot_barycenter_noalloc"):
+                 "se2ot_apply_log", "se2ot_barycenter", "se2ot_interpolate", "se2ot_barycenter_noalloc",
+                 "se2ot_state_export"):
         getattr(L, name).restype = ctypes.c_int
     _LIB = L
     return L
@@ -210,6 +212,18 @@ def se2ot_barycenter(kernel, mu, lam, opts=None, out=None, stream=None, raise_on
     if raise_on_error:
         _check(status)
     return out, st.as_dict(), status
+
+
+def se2ot_state_export(kernel, n, device="cuda", stream=None):
+    """Natural logs of v_i, d_i ([n, ny, nx, ntheta]) and mu ([ny, nx, ntheta]) after the last solve,
+    as float64 CUDA tensors."""
+    shape = kernel.shape
+    lv = torch.empty((n,) + shape, dtype=torch.float64, device=device)
+    ld = torch.empty_like(lv)
+    lmu = torch.empty(shape, dtype=torch.float64, device=device)
+    _check(lib().se2ot_state_export(kernel.handle, int(n), _ptr(lv, torch.float64), _ptr(ld, torch.float64),
+                                    _ptr(lmu, torch.float64), _stream(stream)))
+    return lv, ld, lmu
 
 
 def se2ot_interpolate(kernel, mu0, mu1, t, opts=None, out=None, stream=None, raise_on_error=True):

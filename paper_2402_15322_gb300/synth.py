@@ -142,3 +142,53 @@ def log_field(shape, seed, scale=1.0, slope=0.0):
         ramp = slope * (np.arange(ny)[:, None] + 0.5 * np.arange(nx)[None, :])
         f = f + ramp[..., None]
     return f
+
+
+def _bezier(p0, p1, p2, t):
+    u = 1.0 - t
+    return (u * u * p0[0] + 2 * u * t * p1[0] + t * t * p2[0],
+            u * u * p0[1] + 2 * u * t * p1[1] + t * t * p2[1])
+
+
+def _bezier_tangent(p0, p1, p2, t):
+    return (2 * (1 - t) * (p1[0] - p0[0]) + 2 * t * (p2[0] - p1[0]),
+            2 * (1 - t) * (p1[1] - p0[1]) + 2 * t * (p2[1] - p1[1]))
+
+
+def draw_curve_bumps(rng, nx, ny, nth, nbumps):
+    """Bumps strung along a quadratic Bezier curve (control points ~ U[0.2, 0.8]^2), each centred
+    at a seeded curve parameter in [0.05, 0.95], oriented along the curve's tangent and elongated
+    along it: sigma_b ~ U[0.7, 2]/N, sigma_a = U[4, 8] * sigma_b, sigma_theta ~ U[0.5, 1.5] * 2 pi /
+    nth, amplitude ~ U[0.5, 1]."""
+    n = max(nx, ny)
+    ctrl = [(rng.uniform(0.2, 0.8), rng.uniform(0.2, 0.8)) for _ in range(3)]
+    out = []
+    for _ in range(nbumps):
+        t = rng.uniform(0.05, 0.95)
+        cx, cy = _bezier(*ctrl, t)
+        tx, ty = _bezier_tangent(*ctrl, t)
+        phi = math.atan2(ty, tx) % (2.0 * math.pi)
+        sb = rng.uniform(0.7, 2.0) / n
+        sa = rng.uniform(4.0, 8.0) * sb
+        st = rng.uniform(0.5, 1.5) * 2.0 * math.pi / nth
+        amp = rng.uniform(0.5, 1.0)
+        out.append((cx, cy, phi, sa, sb, st, amp))
+    return out
+
+
+def curve_measures(n, nx, ny, nth, config_seed, max_shift, problem=0, nbumps=8, nbumps_max=12, floor=1e-6):
+    """n measures sharing one set of U{nbumps..nbumps_max} elongated bumps along a seeded curve,
+    each translated by its own seeded integer offset in [-max_shift, max_shift]^2 voxels.
+    [n, ny, nx, nth]."""
+    base_rng = SplitMix64(stream_seed(config_seed, problem, 1 << 21))
+    k = base_rng.randint(nbumps, nbumps_max)
+    params = draw_curve_bumps(base_rng, nx, ny, nth, k)
+    out = []
+    for m in range(n):
+        rng = SplitMix64(stream_seed(config_seed, problem, m))
+        ox, oy = rng.randint(-max_shift, max_shift), rng.randint(-max_shift, max_shift)
+        f = np.zeros((ny, nx, nth))
+        for (cx, cy, phi, sa, sb, st, amp) in params:
+            f += bump(nx, ny, nth, cx + ox / nx, cy + oy / ny, phi, sa, sb, st, amp)
+        out.append(_finish(f, floor))
+    return np.stack(out)

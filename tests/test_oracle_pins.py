@@ -319,3 +319,11 @@ def test_interpolation_endpoints():
         want = K @ (mu[idx].reshape(-1) / one)
         got = oracle.interpolate_log(g, mu[0], mu[1], t, 6)
         np.testing.assert_allclose(got.reshape(-1), want, rtol=1e-12)
+
+
+def test_pointwise_log_conv_is_the_full_one_at_those_points():
+    g = oracle.Grid(12, 10, 8, 3, W, 5e-3, periodic=True)
+    lf = RNG.normal(size=(2,) + g.shape) * 5.0
+    full = oracle.conv_log(g, lf).reshape(-1)
+    idx = RNG.choice(full.size, 60, replace=False)
+    assert np.array_equal(oracle.conv_log_points(g, lf, idx), full[idx])
