@@ -49,6 +49,40 @@ def inputs(problem=0):
                                   problem=problem).astype(np.float32)
 
 
+# Other workloads (parity cases and scale points; not the headline line): `--config large` is the
+# 512^2 x 32 single solve, `--config batched` the 64 uneven interpolations.
+LARGE = dict(nx=512, ny=512, nt=32, r=15, eps=2e-5, n=3, iters=1000,
+             workload="barycenter of 3 measures of elongated bumps along curves, 512x512x32 SE(2) grid, "
+                      "kernel 31x31x32 (r=15), w=(1,3,0.5), eps=2e-5, 1000 Sinkhorn iterations, FP32 log-domain path")
+BATCH_SIZES = [(64, 64, 8), (128, 128, 16), (192, 192, 16), (256, 256, 32)]
+BATCH = dict(nprob=64, iters=100,
+             workload="64 independent 2-measure interpolations, sizes drawn from 64^2x8 / 128^2x16 / 192^2x16 / "
+                      "256^2x32, radius U{7..15}, eps log-uniform in [5e-5, 5e-4], t ~ U[0,1], 100 Sinkhorn "
+                      "iterations in lockstep, FP32 log-domain path")
+
+
+def large_inputs(problem=0):
+    from paper_2402_15322_gb300 import synth
+    return synth.curve_measures(LARGE["n"], LARGE["nx"], LARGE["ny"], LARGE["nt"], config_seed=5,
+                                max_shift=LARGE["r"] // 2, problem=problem).astype(np.float32)
+
+
+def batch_problems(problem=0):
+    """Seeded uneven batch: (nx, ny, nt, r, eps, t, mu[2]) per problem."""
+    from paper_2402_15322_gb300 import synth
+    rng = synth.SplitMix64(synth.stream_seed(3, problem, 1 << 22))
+    out = []
+    for p in range(BATCH["nprob"]):
+        nx, ny, nt = BATCH_SIZES[rng.randint(0, len(BATCH_SIZES) - 1)]
+        r = rng.randint(7, 15)
+        eps = 10 ** rng.uniform(math.log10(5e-5), math.log10(5e-4))
+        t = rng.uniform(0.0, 1.0)
+        mu = synth.coupled_measures(2, nx, ny, nt, config_seed=3, problem=problem * 1000 + p, max_shift=r // 2,
+                                    nbumps=3).astype(np.float32)
+        out.append((nx, ny, nt, r, eps, t, mu))
+    return out
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -173,19 +207,57 @@ def run_gpu(args):
     device = torch.device("cuda", local)
     torch.cuda.set_device(device)
     build.build()
-    desc = se2ot.make_desc(NX, NY, NT, R, W, EPS)
-    k = se2ot.se2ot_kernel_build(desc)
-    mu_h = torch.from_numpy(inputs(problem=rank))
-    mu = mu_h.to(device)
-    out = torch.empty((NY, NX, NT), dtype=torch.float32, device=device)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=device)   # > L2 (129 MB)
-    iters = args.iters
-    opts = se2ot.solve_opts(iters, flags=se2ot.SE2OT_FLAG_TIME_CONV)
     stream = torch.cuda.current_stream()
+    timed_conv = True
+
+    if args.config == "batched":
+        probs = batch_problems(problem=rank)
+        descs = [se2ot.make_desc(nx, ny, nt, r, W, eps) for (nx, ny, nt, r, eps, t, mu) in probs]
+        mu0 = [torch.from_numpy(p[6][0]).to(device) for p in probs]
+        mu1 = [torch.from_numpy(p[6][1]).to(device) for p in probs]
+        outs = [torch.empty_like(m) for m in mu0]
+        ts = [p[5] for p in probs]
+        iters = args.iters or BATCH["iters"]
+        vox = sum(nx * ny * nt for (nx, ny, nt, r, eps, t, mu) in probs)
+        workload = BATCH["workload"]
+        cfg = {"problems": BATCH["nprob"], "sizes": [list(b) for b in BATCH_SIZES], "radius": "U{7..15}",
+               "eps": "log-uniform [5e-5, 5e-4]", "iterations": iters, "voxels": vox}
+        timed_conv = False
+
+        def solve(e2e=False):
+            _, st, _ = se2ot.se2ot_interpolate_batched(descs, mu0, mu1, ts, se2ot.solve_opts(iters), outs)
+            return st[0]
+    else:
+        if args.config == "large":
+            nx, ny, nt, r, eps, n = (LARGE[k] for k in ("nx", "ny", "nt", "r", "eps", "n"))
+            mu_h = torch.from_numpy(large_inputs(problem=rank))
+            iters = args.iters or LARGE["iters"]
+            workload = LARGE["workload"]
+        else:
+            nx, ny, nt, r, eps, n = NX, NY, NT, R, EPS, N_MEAS
+            mu_h = torch.from_numpy(inputs(problem=rank))
+            iters = args.iters or ITERS
+            workload = WORKLOAD
+        lam = [1.0 / n] * n
+        vox = nx * ny * nt
+        cfg = {"grid": [nx, ny, nt], "radius": r, "measures": n, "iterations": iters, "eps": eps, "w": list(W)}
+        k = se2ot.se2ot_kernel_build(se2ot.make_desc(nx, ny, nt, r, W, eps))
+        mu = mu_h.to(device)
+        out = torch.empty((ny, nx, nt), dtype=torch.float32, device=device)
+        mu_pin = mu_h.pin_memory()
+        out_pin = torch.empty((ny, nx, nt), dtype=torch.float32).pin_memory()
+        opts = se2ot.solve_opts(iters, flags=se2ot.SE2OT_FLAG_TIME_CONV)
+        opts_e2e = se2ot.solve_opts(iters)
+
+        def solve(e2e=False):
+            if e2e:
+                return se2ot.se2ot_barycenter(k, mu_pin, lam, opts_e2e, out_pin)[1]
+            return se2ot.se2ot_barycenter(k, mu, lam, opts, out)[1]
 
     for _ in range(args.warmup):
         flush.fill_(1.0)
-        se2ot.se2ot_barycenter(k, mu, LAM, opts, out)
+        solve()
     torch.cuda.synchronize()
 
     conv_ms = 0.0
@@ -201,7 +273,7 @@ def run_gpu(args):
         ev0.record(stream)
         for _ in range(args.steps):
             flush.fill_(1.0)                      # every step starts with a cold L2
-            _, st, _ = se2ot.se2ot_barycenter(k, mu, LAM, opts, out)
+            st = solve()
             conv_ms += st["conv_ms"]
             conv_launches += st["conv_launches"]
             launches += st["kernel_launches"]
@@ -214,54 +286,55 @@ def run_gpu(args):
     mass, viol = st["mass"], st["viol"]
 
     # end to end through the C ABI with pinned host buffers: copies inside the timed region
-    mu_pin = mu_h.pin_memory()
-    out_pin = torch.empty((NY, NX, NT), dtype=torch.float32).pin_memory()
-    opts_e2e = se2ot.solve_opts(iters)
     e2e_steps = max(1, min(args.steps, 3))
     barrier(world, device)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        se2ot.se2ot_barycenter(k, mu_pin, LAM, opts_e2e, out_pin)
+        solve(e2e=True)
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(time.perf_counter() - t0, world, device)
 
     result = None
     if rank == 0:
-        value = world * V * iters * args.steps / (elapsed_ms * 1e-3)
-        e2e_value = world * V * iters * e2e_steps / e2e_s
-        avg_conv_s = conv_ms * 1e-3 / max(1, conv_launches)
+        value = world * vox * iters * args.steps / (elapsed_ms * 1e-3)
+        e2e_value = world * vox * iters * e2e_steps / e2e_s
         peak = peak_terms_per_s()
-        achieved_tflops = CONV_FLOP_PER_LAUNCH / avg_conv_s / 1e12
         peak_tflops = 2.0 * peak / 1e12
-        eval_tflops = 2.0 * evaluated / max(1e-12, conv_ms * 1e-3) / 1e12
+        cfg.update({"workload": workload, "inputs": "seeded coupled synthetic lifted densities",
+                    "l2": "flushed before every step (256 MB write)",
+                    "parallelism": "replicas" if world > 1 else "single GPU"})
         result = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "grid": [NX, NY, NT], "radius": R, "measures": N_MEAS,
-                       "iterations": iters, "eps": EPS, "w": list(W),
-                       "inputs": "seeded coupled synthetic lifted densities",
-                       "l2": "flushed before every step (256 MB write)",
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(N_MEAS * V * 4),
-                    "d2h_bytes_per_step": int(V * 4)},
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
             "gpu_launches": int(launches),
-            "roofline": {"bound": "alu", "kernel": "conv_tile_kernel<10, false> (+ tile-max pre-pass): log-domain group convolution",
-                         "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
-                         "frac": achieved_tflops / peak_tflops, "traffic": conv_traffic(),
-                         "avg_launch_ms": avg_conv_s * 1e3, "launches": int(conv_launches),
-                         "flop_per_launch": CONV_FLOP_PER_LAUNCH,
-                         "peak_basis": "152 SMs x max SM clock x 32 MUFU ex2/clk x 2 flop per kernel term",
-                         "evaluated": {"achieved": eval_tflops, "frac": eval_tflops / peak_tflops,
-                                       "terms_per_launch": evaluated / max(1, conv_launches),
-                                       "note": "kernel terms actually computed; orientation pairs "
-                                               "below 2^-40 of the output are skipped"}},
             "solve": {"mass": mass, "viol": viol, "redo_outputs_timed": int(redo)},
         }
-        cs = clocks.summary()
-        result["clocks"] = cs
-    k.close()
+        if args.config == "batched":
+            result["e2e"] = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
+                             "note": "device-resident batch (the batched entry point takes device buffers)"}
+        else:
+            result["e2e"] = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(n * vox * 4),
+                             "d2h_bytes_per_step": int(vox * 4)}
+        if timed_conv:
+            avg_conv_s = conv_ms * 1e-3 / max(1, conv_launches)
+            flop_per_launch = 2.0 * n * vox * nt * (2 * r + 1) ** 2
+            achieved_tflops = flop_per_launch / avg_conv_s / 1e12
+            eval_tflops = 2.0 * evaluated / max(1e-12, conv_ms * 1e-3) / 1e12
+            result["roofline"] = {
+                "bound": "alu", "kernel": "conv_tile_kernel<%d, false>: log-domain group convolution" % r,
+                "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved_tflops / peak_tflops,
+                "traffic": conv_traffic() if args.config == "barycenter" else None,
+                "avg_launch_ms": avg_conv_s * 1e3, "launches": int(conv_launches),
+                "flop_per_launch": flop_per_launch,
+                "peak_basis": "152 SMs x max SM clock x 32 MUFU ex2/clk x 2 flop per kernel term",
+                "evaluated": {"achieved": eval_tflops, "frac": eval_tflops / peak_tflops,
+                              "terms_per_launch": evaluated / max(1, conv_launches),
+                              "note": "kernel terms actually computed; orientation pairs, kernel rows and "
+                                      "window blocks below 2^-40 of the output are skipped"}}
+        result["clocks"] = clocks.summary()
     return result
 
 
@@ -317,8 +390,11 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--iters", type=int, default=ITERS,
-                    help="Sinkhorn iterations per solve (profiling runs only; the metric uses 500)")
+    ap.add_argument("--iters", type=int, default=0,
+                    help="Sinkhorn iterations per solve (profiling runs only; default: the workload's)")
+    ap.add_argument("--config", default="barycenter", choices=["barycenter", "large", "batched"],
+                    help="workload: the 128^2x16 barycenter (default, the headline), the 512^2x32 "
+                         "large solve, or the 64-problem uneven batch")
     args = ap.parse_args(argv)
     args.warmup = max(3, args.warmup)   # at least 3 untimed warm-up steps
     if args.impl == "reference":
@@ -329,7 +405,7 @@ def main(argv=None):
     res = run_gpu(args)
     rank, world, _ = dist_env()
     if rank == 0:
-        if world == 1 and not args.no_cpu_baseline:
+        if world == 1 and not args.no_cpu_baseline and args.config == "barycenter":
             res["cpu_baseline"] = cpu_baseline()
         print(json.dumps(res), flush=True)
     if world > 1:

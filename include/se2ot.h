@@ -171,6 +171,24 @@ SE2OT_API se2ot_status se2ot_interpolate(se2ot_kernel k, const float *mu0, const
                                const se2ot_solve_opts *opts, float *out, se2ot_stats *stats,
                                void *stream);
 
+/* nprob independent interpolations Phi_t(mu0[p], mu1[p]) (weights (1 - t[p], t[p])) of uneven grid
+ * sizes, radii, metrics and regularisations, iterated in lockstep for opts->max_iters Sinkhorn
+ * iterations (Appendix A with n = 2 for every problem).  descs[p]: each problem's grid and kernel
+ * (zero boundary only).  mu0[p], mu1[p]: device arrays of V_p floats (caller layout), out[p]: V_p
+ * floats, device.  opts: max_iters >= 1, tol_viol must be 0 (no early stop in a batch), NULL =
+ * 100 iterations.  stats: NULL or an array of nprob entries (ms and kernel_launches are for the
+ * whole batch).
+ * One iteration of the batch is one convolution launch per distinct radius for each of the two
+ * convolution lines (a work list over all tiles of all problems with that radius), one exact
+ * recompute pass per line and one update launch, recorded once as a CUDA graph and replayed.
+ * Each problem's result is bit-identical to se2ot_interpolate on that problem alone.  The
+ * workspace and the graph are kept for the next call with the same descriptors; calls are
+ * serialised by a library-wide lock.  Synchronises `stream` before returning. */
+SE2OT_API se2ot_status se2ot_interpolate_batched(int nprob, const se2ot_kernel_desc *descs, const float *const *mu0,
+                                                 const float *const *mu1, const double *t,
+                                                 const se2ot_solve_opts *opts, float *const *out,
+                                                 se2ot_stats *stats, void *stream);
+
 /* State of the kernel handle's most recent se2ot_barycenter / se2ot_interpolate solve with n
  * measures, for checkpointing and for checking the iteration's invariants: natural logarithms of
  * the scaling vectors v_i and of the marginals d_i = v_i (K w_i) (n*V doubles each) and of the

@@ -1,0 +1,442 @@
+// batch.cu -- se2ot_interpolate_batched: many independent interpolations (Eq. interpolation
+// operator: barycenters of 2 measures with weights (1 - t, t)) of uneven grid sizes, radii and
+// regularisations, iterated in lockstep.
+//
+// One Sinkhorn iteration of the whole batch is: for every radius class, one convolution launch
+// over a work list that covers all tiles of all problems of that radius (w-line), one exact
+// recompute pass shared by all problems, the same for the d-line, and one update launch over the
+// tiles of all problems.  That sequence is captured once as a CUDA graph and replayed.
+//
+// Every problem is computed by exactly the same tile code as a single solve, so each result is
+// bit-identical to se2ot_interpolate on that problem alone.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <vector>
+
+#include "dfloat.cuh"
+#include "internal.h"
+
+using namespace se2ot;
+
+namespace {
+
+struct UpdArgs {
+    float2 *lv;
+    const float2 *ld;
+    float2 *L;
+    float2 lam[2];
+    int nx, ny, nt;
+    float *tmax_v;
+};
+
+// Batched form of the update kernel (elementwise.cu): item = (problem, tile x, tile y, slice).
+__global__ void __launch_bounds__(256) batch_update_kernel(const UpdArgs *args, const int4 *items)
+{
+    const int4 it = items[blockIdx.x];
+    const UpdArgs &u = args[it.x];
+    const int nx = u.nx, ny = u.ny, nt = u.nt, t = it.w;
+    const long plane = (long)nx * ny, V = plane * nt;
+    const int ntx = (nx + TILE_X - 1) / TILE_X, nty = (ny + TILE_Y - 1) / TILE_Y;
+    __shared__ float red[8];
+    long gi[2];
+    bool ok[2];
+    float2 Lg[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int e = threadIdx.x + 256 * k;
+        const int y = it.z * TILE_Y + e / TILE_X, x = it.y * TILE_X + e % TILE_X;
+        ok[k] = y < ny && x < nx;
+        gi[k] = (long)t * plane + (long)y * nx + x;
+        float2 acc = make_float2(0.f, 0.f);
+        if (ok[k])
+            for (int i = 0; i < 2; ++i)
+                if (u.lam[i].x != 0.f) acc = df_add(acc, df_mul(u.ld[(long)i * V + gi[k]], u.lam[i]));
+        Lg[k] = acc;
+        if (ok[k]) u.L[gi[k]] = acc;
+    }
+    for (int i = 0; i < 2; ++i) {
+        float m = -INFINITY;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            if (!ok[k]) continue;
+            const long e = (long)i * V + gi[k];
+            const float2 nv = df_add(u.lv[e], df_add(Lg[k], df_neg(u.ld[e])));
+            u.lv[e] = nv;
+            m = fmaxf(m, nv.x);
+        }
+#pragma unroll
+        for (int off = 16; off; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int w = 1; w < 8; ++w) m = fmaxf(m, red[w]);
+            u.tmax_v[((long)i * nt + t) * ntx * nty + it.z * ntx + it.y] = m;
+        }
+    }
+}
+
+struct Arena {
+    char *base = nullptr;
+    size_t cap = 0, off = 0;
+    template <class T>
+    T *take(size_t n)
+    {
+        off = (off + 255) & ~(size_t)255;
+        T *p = (T *)(base ? base + off : nullptr);
+        off += n * sizeof(T);
+        return p;
+    }
+};
+
+struct Prob {
+    se2ot_kernel_desc d;
+    long V;
+    int tiles;
+    Taps taps;
+    float *mu;                         // [2][V] inputs (caller layout)
+    float2 *lmu, *lv, *lw, *ld, *L;
+    float *h1, *h2, *tmax, *tmax2;
+    double *partial, *scal;
+};
+
+// Everything a batch needs, kept between calls with the same descriptors.
+struct BatchCtx {
+    std::vector<se2ot_kernel_desc> descs;
+    std::vector<Prob> probs;
+    char *arena = nullptr;
+    size_t arena_bytes = 0;
+    ConvArgs *dW = nullptr, *dD = nullptr;      // per-problem conv arguments (device)
+    UpdArgs *dU = nullptr;
+    int4 *items = nullptr, *uitems = nullptr;
+    std::vector<std::pair<int, std::pair<int, int>>> classes;   // radius -> (offset, count) in items
+    std::vector<UpdArgs> hU;                                     // host copy of dU
+    int nuitems = 0;
+    int2 *redo = nullptr;
+    unsigned *count = nullptr;
+    unsigned long long *totals = nullptr;
+    cudaStream_t cs = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    int sms = 152;
+    long long launches_per_iter = 0;
+
+    void release()
+    {
+        if (graph) cudaGraphExecDestroy(graph);
+        for (void *p : {(void *)arena, (void *)dW, (void *)dD, (void *)dU, (void *)items, (void *)uitems,
+                        (void *)redo, (void *)count, (void *)totals})
+            if (p) cudaFree(p);
+        if (cs) cudaStreamDestroy(cs);
+        if (ev_in) cudaEventDestroy(ev_in);
+        if (ev_out) cudaEventDestroy(ev_out);
+        *this = BatchCtx();
+    }
+};
+
+std::mutex g_batch_mu;
+BatchCtx g_batch;
+
+bool same_descs(const std::vector<se2ot_kernel_desc> &a, const se2ot_kernel_desc *b, int n)
+{
+    if ((int)a.size() != n) return false;
+    for (int i = 0; i < n; ++i)
+        if (std::memcmp(&a[i], &b[i], sizeof(se2ot_kernel_desc)) != 0) return false;
+    return true;
+}
+
+#define BCK(call, what)                                                                           \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess) {                                                                  \
+            set_last_error((std::string(what) + ": " + cudaGetErrorString(e_)).c_str());         \
+            return e_ == cudaErrorMemoryAllocation ? SE2OT_ENOMEM : SE2OT_ECUDA;                 \
+        }                                                                                         \
+    } while (0)
+
+bool on_device(const void *p)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Allocate and lay out the batch, build every problem's taps, record the iteration graph.
+se2ot_status setup(BatchCtx &B, int nprob, const se2ot_kernel_desc *descs)
+{
+    B.release();
+    B.descs.assign(descs, descs + nprob);
+    int dev = 0;
+    BCK(cudaGetDevice(&dev), "cudaGetDevice");
+    BCK(cudaDeviceGetAttribute(&B.sms, cudaDevAttrMultiProcessorCount, dev), "cudaDeviceGetAttribute");
+    B.probs.resize(nprob);
+    long total_v2 = 0;
+    for (int pass = 0; pass < 2; ++pass) {   // pass 0 sizes the arena, pass 1 hands out pointers
+        Arena a;
+        a.base = pass ? B.arena : nullptr;
+        for (int p = 0; p < nprob; ++p) {
+            Prob &q = B.probs[p];
+            q.d = descs[p];
+            const int nt = q.d.ntheta, D = 2 * q.d.radius + 1;
+            q.V = (long)q.d.nx * q.d.ny * nt;
+            q.tiles = conv_tiles(q.d.nx, q.d.ny);
+            const size_t npair = (size_t)nt * nt, v2 = 2 * (size_t)q.V;
+            q.taps.ltheta = a.take<float2>(npair);
+            q.taps.ls = a.take<float>(npair * D * D);
+            q.taps.ls_lo = a.take<float>(npair * D * D);
+            q.taps.lsrow = a.take<float>(npair * D);
+            q.mu = a.take<float>(v2);
+            q.lmu = a.take<float2>(v2);
+            q.lv = a.take<float2>(v2);
+            q.lw = a.take<float2>(v2);
+            q.ld = a.take<float2>(v2);
+            q.L = a.take<float2>((size_t)q.V);
+            q.h1 = a.take<float>(v2);
+            q.h2 = a.take<float>(v2);
+            q.tmax = a.take<float>((size_t)2 * nt * q.tiles);
+            q.tmax2 = a.take<float>((size_t)2 * nt * q.tiles);
+            q.partial = a.take<double>(2 * STATS_BLOCKS);
+            q.scal = a.take<double>(4);
+            if (!pass) total_v2 += (long)v2;
+        }
+        if (!pass) {
+            B.arena_bytes = a.off + 256;
+            BCK(cudaMalloc((void **)&B.arena, B.arena_bytes), "cudaMalloc(batch arena)");
+        }
+    }
+    if ((double)total_v2 >= 2147483647.0) return SE2OT_EINVAL;
+    BCK(cudaMalloc((void **)&B.redo, sizeof(int2) * total_v2), "cudaMalloc(redo)");
+    BCK(cudaMalloc((void **)&B.count, 4 * sizeof(unsigned)), "cudaMalloc(count)");
+    BCK(cudaMalloc((void **)&B.totals, 2 * sizeof(unsigned long long)), "cudaMalloc(totals)");
+    BCK(cudaStreamCreateWithFlags(&B.cs, cudaStreamNonBlocking), "cudaStreamCreate");
+    BCK(cudaEventCreateWithFlags(&B.ev_in, cudaEventDisableTiming), "cudaEventCreate");
+    BCK(cudaEventCreateWithFlags(&B.ev_out, cudaEventDisableTiming), "cudaEventCreate");
+
+    // taps
+    for (int p = 0; p < nprob; ++p) BCK(build_taps(B.probs[p].d, B.probs[p].taps, B.cs), "tap build");
+
+    // conv arguments (w-line and d-line) and work lists by radius
+    std::vector<ConvArgs> hW(nprob), hD(nprob);
+    std::vector<UpdArgs> hU(nprob);
+    std::map<int, std::vector<int4>> byr;
+    std::vector<int4> uitems;
+    for (int p = 0; p < nprob; ++p) {
+        const Prob &q = B.probs[p];
+        ConvArgs a;
+        std::memset(&a, 0, sizeof a);
+        a.ltheta = q.taps.ltheta;
+        a.ls = q.taps.ls;
+        a.ls_lo = q.taps.ls_lo;
+        a.lsrow = q.taps.lsrow;
+        a.out_scale = 1.0;
+        a.redo_list = B.redo;
+        a.redo_count = B.count;
+        a.redo_total = B.totals;
+        a.eval_count = B.totals + 1;
+        a.nx = q.d.nx;
+        a.ny = q.d.ny;
+        a.nt = q.d.ntheta;
+        a.r = q.d.radius;
+        a.periodic = 0;
+        a.batch = 2;
+        a.tmax_ready = 1;
+        ConvArgs w = a, d = a;
+        w.epi = EPI_W;
+        w.in = q.lv;
+        w.hint = q.h1;
+        w.aux = q.lmu;
+        w.out2 = q.lw;
+        w.tmax = q.tmax;
+        w.tmax_w = q.tmax;
+        w.tmax_out = q.tmax2;
+        d.epi = EPI_D;
+        d.in = q.lw;
+        d.hint = q.h2;
+        d.aux = q.lv;
+        d.out2 = q.ld;
+        d.tmax = q.tmax2;
+        d.tmax_w = q.tmax2;
+        hW[p] = w;
+        hD[p] = d;
+        hU[p] = UpdArgs{q.lv, q.ld, q.L, {make_float2(0.f, 0.f), make_float2(0.f, 0.f)}, q.d.nx, q.d.ny,
+                        q.d.ntheta, q.tmax};
+        const int ntx = (q.d.nx + TILE_X - 1) / TILE_X, nty = (q.d.ny + TILE_Y - 1) / TILE_Y;
+        std::vector<int4> &v = byr[q.d.radius];
+        for (int bo = 0; bo < 2 * q.d.ntheta; ++bo)
+            for (int ty = 0; ty < nty; ++ty)
+                for (int tx = 0; tx < ntx; ++tx) v.push_back(make_int4(p, bo, tx, ty));
+        for (int t = 0; t < q.d.ntheta; ++t)
+            for (int ty = 0; ty < nty; ++ty)
+                for (int tx = 0; tx < ntx; ++tx) uitems.push_back(make_int4(p, tx, ty, t));
+    }
+    std::vector<int4> items;
+    for (auto &kv : byr) {
+        B.classes.push_back({kv.first, {(int)items.size(), (int)kv.second.size()}});
+        items.insert(items.end(), kv.second.begin(), kv.second.end());
+    }
+    B.nuitems = (int)uitems.size();
+    BCK(cudaMalloc((void **)&B.dW, sizeof(ConvArgs) * nprob), "cudaMalloc");
+    BCK(cudaMalloc((void **)&B.dD, sizeof(ConvArgs) * nprob), "cudaMalloc");
+    BCK(cudaMalloc((void **)&B.dU, sizeof(UpdArgs) * nprob), "cudaMalloc");
+    BCK(cudaMalloc((void **)&B.items, sizeof(int4) * items.size()), "cudaMalloc");
+    BCK(cudaMalloc((void **)&B.uitems, sizeof(int4) * uitems.size()), "cudaMalloc");
+    BCK(cudaMemcpyAsync(B.dW, hW.data(), sizeof(ConvArgs) * nprob, cudaMemcpyHostToDevice, B.cs), "cudaMemcpy");
+    BCK(cudaMemcpyAsync(B.dD, hD.data(), sizeof(ConvArgs) * nprob, cudaMemcpyHostToDevice, B.cs), "cudaMemcpy");
+    BCK(cudaMemcpyAsync(B.dU, hU.data(), sizeof(UpdArgs) * nprob, cudaMemcpyHostToDevice, B.cs), "cudaMemcpy");
+    BCK(cudaMemcpyAsync(B.items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice, B.cs),
+        "cudaMemcpy");
+    BCK(cudaMemcpyAsync(B.uitems, uitems.data(), sizeof(int4) * uitems.size(), cudaMemcpyHostToDevice, B.cs),
+        "cudaMemcpy");
+    BCK(cudaStreamSynchronize(B.cs), "cudaStreamSynchronize");
+
+    B.hU = hU;
+    // record one Sinkhorn iteration of the whole batch as a graph (kernel attributes are set
+    // before the capture: a zero-item launch only configures the kernel)
+    ConvArgs shared = hW[0];
+    for (auto &c : B.classes) BCK(launch_conv_batch(c.first, shared, B.dW, B.items, 0, B.cs), "conv attributes");
+    cudaGraph_t g = nullptr;
+    BCK(cudaStreamBeginCapture(B.cs, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+    long long launches = 0;
+    cudaError_t e = cudaSuccess;
+    for (int line = 0; line < 2 && e == cudaSuccess; ++line) {
+        const ConvArgs *probs = line == 0 ? B.dW : B.dD;
+        e = cudaMemsetAsync(B.count, 0, sizeof(unsigned), B.cs);
+        for (auto &c : B.classes)
+            if (e == cudaSuccess) {
+                e = launch_conv_batch(c.first, shared, probs, B.items + c.second.first, c.second.second, B.cs);
+                ++launches;
+            }
+        if (e == cudaSuccess) e = launch_redo_batch(shared, probs, 2 * B.sms, B.cs);
+        ++launches;
+    }
+    if (e == cudaSuccess) {
+        batch_update_kernel<<<B.nuitems, 256, 0, B.cs>>>(B.dU, B.uitems);
+        e = cudaGetLastError();
+        ++launches;
+    }
+    cudaError_t e2 = cudaStreamEndCapture(B.cs, &g);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&B.graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    BCK(e, "batch iteration graph");
+    B.launches_per_iter = launches;
+    return SE2OT_OK;
+}
+
+}  // namespace
+
+extern "C" se2ot_status se2ot_interpolate_batched(int nprob, const se2ot_kernel_desc *descs, const float *const *mu0,
+                                                  const float *const *mu1, const double *t,
+                                                  const se2ot_solve_opts *opts, float *const *out,
+                                                  se2ot_stats *stats, void *stream)
+{
+    const auto wall0 = std::chrono::steady_clock::now();
+    if (nprob < 1 || !descs || !mu0 || !mu1 || !t || !out) {
+        set_last_error("NULL argument or nprob < 1");
+        return SE2OT_EINVAL;
+    }
+    se2ot_solve_opts o = {100, 0, 0.0, SE2OT_FP32, 0};
+    if (opts) o = *opts;
+    if (o.max_iters < 1 || o.precision != SE2OT_FP32 || o.tol_viol != 0.0) {
+        set_last_error("batched solves run a fixed number (>= 1) of FP32 iterations (tol_viol must be 0)");
+        return SE2OT_EINVAL;
+    }
+    for (int p = 0; p < nprob; ++p) {
+        se2ot_status st = validate_kernel_desc(&descs[p]);
+        if (st != SE2OT_OK) return st;
+        if (descs[p].boundary != SE2OT_BOUNDARY_ZERO) {
+            set_last_error("batched solves support the zero boundary only");
+            return SE2OT_EINVAL;
+        }
+        if (!(t[p] >= 0.0 && t[p] <= 1.0)) {
+            set_last_error("t out of [0, 1]");
+            return SE2OT_EINVAL;
+        }
+        if (!mu0[p] || !mu1[p] || !out[p] || !on_device(mu0[p]) || !on_device(mu1[p]) || !on_device(out[p])) {
+            set_last_error("batched solves take device pointers");
+            return SE2OT_EINVAL;
+        }
+    }
+    std::lock_guard<std::mutex> lock(g_batch_mu);
+    BatchCtx &B = g_batch;
+    if (!same_descs(B.descs, descs, nprob) || !B.graph) {
+        se2ot_status st = setup(B, nprob, descs);
+        if (st != SE2OT_OK) {
+            B.release();
+            return st;
+        }
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    BCK(cudaEventRecord(B.ev_in, s), "cudaEventRecord");
+    BCK(cudaStreamWaitEvent(B.cs, B.ev_in, 0), "cudaStreamWaitEvent");
+    // inputs, weights, first shifts
+    std::vector<UpdArgs> &hU = B.hU;
+    long long launches = 0;
+    for (int p = 0; p < nprob; ++p) {
+        Prob &q = B.probs[p];
+        BCK(cudaMemcpyAsync(q.mu, mu0[p], q.V * sizeof(float), cudaMemcpyDeviceToDevice, B.cs), "cudaMemcpy(mu0)");
+        BCK(cudaMemcpyAsync(q.mu + q.V, mu1[p], q.V * sizeof(float), cudaMemcpyDeviceToDevice, B.cs),
+            "cudaMemcpy(mu1)");
+        BCK(launch_init(q.mu, q.lmu, q.lv, q.h1, q.h2, 2, q.d.nx, q.d.ny, q.d.ntheta, B.cs), "init");
+        BCK(cudaMemsetAsync(q.tmax, 0, sizeof(float) * 2 * q.d.ntheta * q.tiles, B.cs), "cudaMemset(tmax)");
+        const double lam[2] = {1.0 - t[p], t[p]};
+        for (int i = 0; i < 2; ++i) {
+            const float hi = (float)lam[i];
+            hU[p].lam[i] = make_float2(hi, (float)(lam[i] - (double)hi));
+        }
+        ++launches;
+    }
+    BCK(cudaMemcpyAsync(B.dU, hU.data(), sizeof(UpdArgs) * nprob, cudaMemcpyHostToDevice, B.cs), "cudaMemcpy");
+    BCK(cudaMemsetAsync(B.totals, 0, 2 * sizeof(unsigned long long), B.cs), "cudaMemset");
+    for (int it = 0; it < o.max_iters; ++it) BCK(cudaGraphLaunch(B.graph, B.cs), "cudaGraphLaunch");
+    launches += B.launches_per_iter * o.max_iters;
+    for (int p = 0; p < nprob; ++p) {
+        Prob &q = B.probs[p];
+        Lambdas lam;
+        for (int i = 0; i < 64; ++i) lam.v[i] = make_float2(0.f, 0.f);
+        lam.v[0] = hU[p].lam[0];
+        lam.v[1] = hU[p].lam[1];
+        BCK(launch_finalize(q.L, out[p], q.d.nx, q.d.ny, q.d.ntheta, B.cs), "finalize");
+        BCK(launch_stats(q.L, q.ld, lam, 2, q.V, q.partial, q.scal, B.cs), "stats");
+        launches += 3;
+    }
+    std::vector<double> scal(2 * (size_t)nprob);
+    for (int p = 0; p < nprob; ++p)
+        BCK(cudaMemcpyAsync(&scal[2 * p], B.probs[p].scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, B.cs),
+            "cudaMemcpy(stats)");
+    unsigned long long counts[2] = {0, 0};
+    BCK(cudaMemcpyAsync(counts, B.totals, sizeof counts, cudaMemcpyDeviceToHost, B.cs), "cudaMemcpy");
+    BCK(cudaEventRecord(B.ev_out, B.cs), "cudaEventRecord");
+    BCK(cudaStreamWaitEvent(s, B.ev_out, 0), "cudaStreamWaitEvent");
+    BCK(cudaStreamSynchronize(B.cs), "cudaStreamSynchronize");
+    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - wall0).count();
+    bool finite = true;
+    for (int p = 0; p < nprob; ++p) {
+        if (!std::isfinite(scal[2 * p]) || !std::isfinite(scal[2 * p + 1])) finite = false;
+        if (stats) {
+            std::memset(&stats[p], 0, sizeof(se2ot_stats));
+            stats[p].iters = o.max_iters;
+            stats[p].mass = scal[2 * p];
+            stats[p].viol = scal[2 * p + 1];
+            stats[p].ms = ms;
+            stats[p].voxel_iters_per_s = ms > 0 ? (double)B.probs[p].V * o.max_iters / (ms * 1e-3) : 0.0;
+            stats[p].kernel_launches = launches;
+            stats[p].redo_outputs = (long long)counts[0];
+            stats[p].evaluated_terms = (long long)counts[1];
+        }
+    }
+    if (!finite) {
+        set_last_error("non-finite iterate in the batch");
+        return SE2OT_ENONFINITE;
+    }
+    return SE2OT_OK;
+}

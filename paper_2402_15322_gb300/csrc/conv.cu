@@ -8,9 +8,12 @@
 
 namespace se2ot {
 
-bool launch_tile_a(int r, bool maxpass, const ConvArgs &a, cudaStream_t s, cudaError_t *err);
-bool launch_tile_b(int r, bool maxpass, const ConvArgs &a, cudaStream_t s, cudaError_t *err);
-bool launch_tile_c(int r, bool maxpass, const ConvArgs &a, cudaStream_t s, cudaError_t *err);
+bool launch_tile_a(int r, bool maxpass, const ConvArgs &a, const ConvArgs *probs, const int4 *items, int nitems,
+                   cudaStream_t s, cudaError_t *err);
+bool launch_tile_b(int r, bool maxpass, const ConvArgs &a, const ConvArgs *probs, const int4 *items, int nitems,
+                   cudaStream_t s, cudaError_t *err);
+bool launch_tile_c(int r, bool maxpass, const ConvArgs &a, const ConvArgs *probs, const int4 *items, int nitems,
+                   cudaStream_t s, cudaError_t *err);
 
 namespace {
 
@@ -56,17 +59,20 @@ __global__ void __launch_bounds__(256) tile_max_kernel(ConvArgs a)
 }
 
 // Exact recomputation of queued outputs: one warp per output, FP64 terms, shift = largest term.
-__global__ void redo_kernel(ConvArgs a)
+// Entries are (problem, flat index); probs == NULL means every entry belongs to a0.
+__global__ void redo_kernel(ConvArgs a0, const ConvArgs *probs)
 {
-    const unsigned n = *a.redo_count;
+    const unsigned n = *a0.redo_count;
     const int lane = threadIdx.x & 31;
     const int wpb = blockDim.x >> 5;
     const long nwarps = (long)gridDim.x * wpb;
-    const int r = a.r, D = 2 * r + 1, nx = a.nx, ny = a.ny, nt = a.nt;
-    const long plane = (long)nx * ny;
-    const long T = (long)nt * D * D;
     for (long k = blockIdx.x * (long)wpb + (threadIdx.x >> 5); k < n; k += nwarps) {
-        const long flat = a.redo_list[k];
+        const int2 ent = a0.redo_list[k];
+        const ConvArgs &a = probs ? probs[ent.x] : a0;
+        const int r = a.r, D = 2 * r + 1, nx = a.nx, ny = a.ny, nt = a.nt;
+        const long plane = (long)nx * ny;
+        const long T = (long)nt * D * D;
+        const long flat = ent.y;
         const long bo = flat / plane, p = flat - bo * plane;
         const int b = (int)(bo / nt), o = (int)(bo - (long)b * nt);
         const int y = (int)(p / nx), x = (int)(p - (long)y * nx);
@@ -104,14 +110,16 @@ __global__ void redo_kernel(ConvArgs a)
             tile::write_out(a, flat, b, o, y, x, cd.x, cd.y);
         }
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0 && a.redo_total) atomicAdd(a.redo_total, (unsigned long long)n);
+    if (blockIdx.x == 0 && threadIdx.x == 0 && a0.redo_total) atomicAdd(a0.redo_total, (unsigned long long)n);
 }
 
-cudaError_t dispatch(const ConvArgs &a, bool maxpass, cudaStream_t s)
+cudaError_t dispatch(int r, const ConvArgs &a, bool maxpass, const ConvArgs *probs, const int4 *items, int nitems,
+                     cudaStream_t s)
 {
     cudaError_t e = cudaSuccess;
-    if (launch_tile_a(a.r, maxpass, a, s, &e) || launch_tile_b(a.r, maxpass, a, s, &e) ||
-        launch_tile_c(a.r, maxpass, a, s, &e))
+    if (launch_tile_a(r, maxpass, a, probs, items, nitems, s, &e) ||
+        launch_tile_b(r, maxpass, a, probs, items, nitems, s, &e) ||
+        launch_tile_c(r, maxpass, a, probs, items, nitems, s, &e))
         return e;
     return cudaErrorInvalidValue;
 }
@@ -130,14 +138,26 @@ cudaError_t launch_conv(const ConvArgs &a, cudaStream_t s)
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    return dispatch(a, false, s);
+    return dispatch(a.r, a, false, nullptr, nullptr, 0, s);
 }
 
-cudaError_t launch_conv_max(const ConvArgs &a, cudaStream_t s) { return dispatch(a, true, s); }
+cudaError_t launch_conv_max(const ConvArgs &a, cudaStream_t s) { return dispatch(a.r, a, true, nullptr, nullptr, 0, s); }
 
 cudaError_t launch_redo(const ConvArgs &a, int max_blocks, cudaStream_t s)
 {
-    redo_kernel<<<max_blocks, 256, 0, s>>>(a);
+    redo_kernel<<<max_blocks, 256, 0, s>>>(a, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_conv_batch(int r, const ConvArgs &shared, const ConvArgs *probs, const int4 *items, int nitems,
+                              cudaStream_t s)
+{
+    return dispatch(r, shared, false, probs, items, nitems, s);
+}
+
+cudaError_t launch_redo_batch(const ConvArgs &shared, const ConvArgs *probs, int max_blocks, cudaStream_t s)
+{
+    redo_kernel<<<max_blocks, 256, 0, s>>>(shared, probs);
     return cudaGetLastError();
 }
 

@@ -93,9 +93,26 @@ __device__ __forceinline__ void write_out(const ConvArgs &a, long flat, int b, i
     }
 }
 
-template <int R, bool MAXPASS>
-__global__ void __launch_bounds__(THREADS, 6) conv_tile_kernel(const ConvArgs a)
+// Single problem (BATCHED false): tile (blockIdx.x, blockIdx.y) of field*orientation blockIdx.z of
+// a0, read from the kernel parameters.  Batch: CTA k works on items[k] = (problem, field * nt +
+// orientation, tile x, tile y), the problem's arguments read from probs.
+template <int R, bool MAXPASS, bool BATCHED>
+__global__ void __launch_bounds__(THREADS, 6) conv_tile_kernel(const ConvArgs a0, const ConvArgs *probs,
+                                                               const int4 *items)
 {
+    int p = 0, bo, tx, ty;
+    if (BATCHED) {
+        const int4 it = items[blockIdx.x];
+        p = it.x;
+        bo = it.y;
+        tx = it.z;
+        ty = it.w;
+    } else {
+        bo = blockIdx.z;
+        tx = blockIdx.x;
+        ty = blockIdx.y;
+    }
+    const ConvArgs &a = BATCHED ? probs[p] : a0;
     constexpr int D = 2 * R + 1;
     constexpr int HX = TX + 2 * R, HY = TY + 2 * R, HXP = halo_pitch(HX), TP = tap_pitch(D);
     constexpr int WIN = XQ + 2 * R;        // window of one thread row: x' in [xl, xl + WIN)
@@ -112,8 +129,9 @@ __global__ void __launch_bounds__(THREADS, 6) conv_tile_kernel(const ConvArgs a)
     const int nx = a.nx, ny = a.ny, nt = a.nt;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int xl = (lane % ROW_LANES) * XQ, yl = warp * WARP_ROWS + lane / ROW_LANES;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int b = blockIdx.z / nt, o = blockIdx.z - b * nt;
+    const int x0 = tx * TX, y0 = ty * TY;
+    const int ntx = (nx + TX - 1) / TX, nty = (ny + TY - 1) / TY;
+    const int b = bo / nt, o = bo - b * nt;
     const long plane = (long)nx * ny;
     const float2 *in_b = a.in + (long)b * nt * plane;
     const int gy = y0 + yl;
@@ -149,7 +167,7 @@ __global__ void __launch_bounds__(THREADS, 6) conv_tile_kernel(const ConvArgs a)
     }
 
     // which input slices can contribute: one thread per slice, from the tile-max pre-pass
-    const long ntiles = (long)gridDim.x * gridDim.y;
+    const long ntiles = (long)ntx * nty;
     for (int i = tid; i < nt; i += THREADS) {
         const float2 lt = a.ltheta[o * nt + i];
         lts[i] = lt;
@@ -159,13 +177,12 @@ __global__ void __launch_bounds__(THREADS, 6) conv_tile_kernel(const ConvArgs a)
             const float *tmi = a.tmax + ((long)b * nt + i) * ntiles;
             float tm;
             if (a.periodic) {
-                tm = tmi[blockIdx.y * gridDim.x + blockIdx.x];
+                tm = tmi[ty * ntx + tx];
             } else {
                 tm = -INFINITY;
-                for (int ty = (int)blockIdx.y - 1; ty <= (int)blockIdx.y + 1; ++ty)
-                    for (int tx = (int)blockIdx.x - 1; tx <= (int)blockIdx.x + 1; ++tx)
-                        if (ty >= 0 && ty < (int)gridDim.y && tx >= 0 && tx < (int)gridDim.x)
-                            tm = fmaxf(tm, tmi[ty * gridDim.x + tx]);
+                for (int jy = ty - 1; jy <= ty + 1; ++jy)
+                    for (int jx = tx - 1; jx <= tx + 1; ++jx)
+                        if (jy >= 0 && jy < nty && jx >= 0 && jx < ntx) tm = fmaxf(tm, tmi[jy * ntx + jx]);
             }
             nd = !(lt.x + tm + 1.0f < smin - SKIP_MARGIN);
         }
@@ -306,7 +323,7 @@ __global__ void __launch_bounds__(THREADS, 6) conv_tile_kernel(const ConvArgs a)
         const float lacc = log2f(acc[j]);
         if (!(lacc >= ACC_LO && lacc <= ACC_HI)) {
             const unsigned k = atomicAdd(a.redo_count, 1u);
-            a.redo_list[k] = (int)flat;
+            a.redo_list[k] = make_int2(p, (int)flat);
             omax = INFINITY;          // value unknown until the exact recompute: no skipping on it
             continue;
         }
@@ -321,24 +338,32 @@ __global__ void __launch_bounds__(THREADS, 6) conv_tile_kernel(const ConvArgs a)
         __syncthreads();
         if (tid == 0) {
             for (int w = 1; w < THREADS / 32; ++w) omax = fmaxf(omax, red[w]);
-            a.tmax_out[((long)b * nt + o) * ntiles + blockIdx.y * gridDim.x + blockIdx.x] = omax;
+            a.tmax_out[((long)b * nt + o) * ntiles + ty * ntx + tx] = omax;
         }
     }
 }
 
 template <int R, bool MAXPASS>
-cudaError_t launch_tile(const ConvArgs &a, cudaStream_t s)
+cudaError_t launch_tile(const ConvArgs &a, const ConvArgs *probs, const int4 *items, int nitems, cudaStream_t s)
 {
     const size_t smem = sizeof(float) * smem_floats(R);
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(conv_tile_kernel<R, MAXPASS>,
+        cudaError_t e = cudaFuncSetAttribute(conv_tile_kernel<R, MAXPASS, false>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess && !MAXPASS)
+            e = cudaFuncSetAttribute(conv_tile_kernel<R, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem);
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    dim3 grid((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY, a.batch * a.nt);
-    conv_tile_kernel<R, MAXPASS><<<grid, THREADS, smem, s>>>(a);
+    if (items) {
+        if (MAXPASS) return cudaErrorInvalidValue;   // batches never need the max pass
+        if (nitems > 0) conv_tile_kernel<R, false, true><<<nitems, THREADS, smem, s>>>(a, probs, items);
+    } else {
+        dim3 grid((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY, a.batch * a.nt);
+        conv_tile_kernel<R, MAXPASS, false><<<grid, THREADS, smem, s>>>(a, nullptr, nullptr);
+    }
     return cudaGetLastError();
 }
 

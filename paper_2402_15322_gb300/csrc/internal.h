@@ -40,7 +40,7 @@ struct ConvArgs {
     double *out64;           // EPI_LOG_OUT destination
     float *out32;            // EPI_LIN_OUT destination
     double out_scale;        // EPI_LOG_OUT: ln 2 for natural-log output
-    int *redo_list;          // outputs to recompute exactly (slice-major flat index)
+    int2 *redo_list;         // outputs to recompute exactly: (problem, slice-major flat index)
     unsigned *redo_count;    // entries in redo_list
     unsigned long long *redo_total;  // running total for statistics
     unsigned long long *eval_count;  // kernel terms evaluated (not skipped)
@@ -62,6 +62,12 @@ cudaError_t launch_conv(const ConvArgs &a, cudaStream_t s);
 // same tiling, writing the largest term of every output to a.hint (the shift of a later launch)
 cudaError_t launch_conv_max(const ConvArgs &a, cudaStream_t s);
 cudaError_t launch_redo(const ConvArgs &a, int max_blocks, cudaStream_t s);
+// Batched launches: one convolution (all problems of one radius class: probs[p].r == r) over the
+// work list items[0..nitems) = (problem, field * nt + orientation, tile x, tile y), and the exact
+// recompute of the list shared by the problems of probs.
+cudaError_t launch_conv_batch(int r, const ConvArgs &shared, const ConvArgs *probs, const int4 *items, int nitems,
+                              cudaStream_t s);
+cudaError_t launch_redo_batch(const ConvArgs &shared, const ConvArgs *probs, int max_blocks, cudaStream_t s);
 int conv_tiles(int nx, int ny);          // spatial tiles of one slice (size of tmax per slice)
 size_t conv_smem_bytes(int r);           // dynamic shared memory of one convolution CTA
 

@@ -148,7 +148,7 @@ extern "C" se2ot_status se2ot_barycenter_noalloc(const se2ot_kernel_desc *desc, 
     dry.take<float2>((size_t)V);
     dry.take<float>(nV);
     dry.take<float>(nV);
-    dry.take<int>(nV);
+    dry.take<int2>(nV);
     dry.take<unsigned>(4);
     dry.take<unsigned long long>(2);
     dry.take<double>(2 * STATS_BLOCKS);
@@ -171,7 +171,7 @@ extern "C" se2ot_status se2ot_barycenter_noalloc(const se2ot_kernel_desc *desc, 
     float2 *lmu = c.take<float2>(nV), *lv = c.take<float2>(nV), *lw = c.take<float2>(nV), *ld = c.take<float2>(nV);
     float2 *L = c.take<float2>((size_t)V);
     float *h1 = c.take<float>(nV), *h2 = c.take<float>(nV);
-    int *redo = c.take<int>(nV);
+    int2 *redo = c.take<int2>(nV);
     unsigned *count = c.take<unsigned>(4);
     unsigned long long *totals = c.take<unsigned long long>(2);
     double *partial = c.take<double>(2 * STATS_BLOCKS);

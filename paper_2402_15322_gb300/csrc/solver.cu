@@ -128,7 +128,7 @@ struct se2ot_kernel_s {
     size_t c_lmu = 0, c_lv = 0, c_lw = 0, c_ld = 0, c_L = 0, c_lf = 0;
     float *h1 = nullptr, *h2 = nullptr, *mu_stage = nullptr, *bary_stage = nullptr;
     size_t c_h1 = 0, c_h2 = 0, c_mus = 0, c_bs = 0;
-    int *redo = nullptr;
+    int2 *redo = nullptr;
     size_t c_redo = 0;
     unsigned *counters = nullptr;           // [0] redo count
     unsigned long long *redo_total = nullptr;   // [0] redo outputs, [1] evaluated warp-slices

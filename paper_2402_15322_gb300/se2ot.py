@@ -80,6 +80,10 @@ def lib():
     L.se2ot_interpolate.argtypes = [vp, vp, vp, d, ctypes.POINTER(se2ot_solve_opts), vp,
                                     ctypes.POINTER(se2ot_stats), vp]
     L.se2ot_state_export.argtypes = [vp, i, vp, vp, vp, vp]
+    L.se2ot_interpolate_batched.argtypes = [i, ctypes.POINTER(se2ot_kernel_desc), ctypes.POINTER(vp),
+                                            ctypes.POINTER(vp), ctypes.POINTER(d),
+                                            ctypes.POINTER(se2ot_solve_opts), ctypes.POINTER(vp),
+                                            ctypes.POINTER(se2ot_stats), vp]
     L.se2ot_barycenter_noalloc.argtypes = [ctypes.POINTER(se2ot_kernel_desc), i, vp, vp,
                                            ctypes.POINTER(se2ot_solve_opts), vp,
                                            ctypes.POINTER(se2ot_stats), vp]
@@ -87,7 +91,7 @@ def lib():
     L.se2ot_version.restype = ctypes.c_char_p
     for name in ("se2ot_kernel_build", "se2ot_kernel_destroy", "se2ot_kernel_taps", "se2ot_apply",
                  "se2ot_apply_log", "se2ot_barycenter", "se2ot_interpolate", "se2ot_barycenter_noalloc",
-                 "se2ot_state_export"):
+                 "se2ot_state_export", "se2ot_interpolate_batched"):
         getattr(L, name).restype = ctypes.c_int
     _LIB = L
     return L
@@ -258,3 +262,23 @@ def se2ot_barycenter_noalloc(desc, mu, lam, opts=None, out=None, stream=None, ra
     if raise_on_error:
         _check(status)
     return out, st.as_dict(), status
+
+
+def se2ot_interpolate_batched(descs, mu0s, mu1s, ts, opts=None, outs=None, stream=None, raise_on_error=True):
+    """Batched interpolations: descs, mu0s, mu1s (CUDA float32 tensors [ny, nx, ntheta] per problem),
+    ts (floats).  Returns (outs, list of stats dicts, status)."""
+    n = len(descs)
+    if outs is None:
+        outs = [torch.empty_like(m) for m in mu0s]
+    darr = (se2ot_kernel_desc * n)(*descs)
+    p0 = (ctypes.c_void_p * n)(*[_ptr(m, torch.float32).value for m in mu0s])
+    p1 = (ctypes.c_void_p * n)(*[_ptr(m, torch.float32).value for m in mu1s])
+    po = (ctypes.c_void_p * n)(*[_ptr(m, torch.float32).value for m in outs])
+    tt = (ctypes.c_double * n)(*[float(x) for x in ts])
+    st = (se2ot_stats * n)()
+    status = lib().se2ot_interpolate_batched(n, darr, p0, p1, tt,
+                                             ctypes.byref(opts if opts is not None else solve_opts()),
+                                             po, st, _stream(stream))
+    if raise_on_error:
+        _check(status)
+    return outs, [s.as_dict() for s in st], status
