@@ -189,6 +189,41 @@ SE2OT_API se2ot_status se2ot_interpolate_batched(int nprob, const se2ot_kernel_d
                                                  const se2ot_solve_opts *opts, float *const *out,
                                                  se2ot_stats *stats, void *stream);
 
+/* Serving: a request loop for barycenter solves with continuous batching (no counterpart in the
+ * paper; the solve of every request is se2ot_barycenter's).  A server owns one worker thread on
+ * `device`.  Requests wait in FIFO order until a slot (at most max_slots run at once) and their
+ * device state (tap table, inputs, workspace; about 90 bytes per voxel and measure) fit in
+ * device_budget_bytes; an admitted request gets its own stream and stream-ordered memory and is
+ * advanced in chunks of check_every iterations (50 without a tolerance), each followed by the
+ * FP64 marginal violation; it completes when viol <= tol_viol or after max_iters iterations.
+ * Chunks of all admitted requests overlap on the device; memory is returned and the next request
+ * admitted as each completes.  A request's result does not depend on the other requests. */
+typedef struct se2ot_server_s *se2ot_server;
+
+/* Start a server.  EINVAL for max_slots < 1, a zero budget or an unknown device. */
+SE2OT_API se2ot_status se2ot_serve_create(size_t device_budget_bytes, int max_slots, int device, se2ot_server *out);
+
+/* Queue a barycenter of n measures (arguments as in se2ot_barycenter; mu host or device memory,
+ * copied before return so the caller may free it).  ticket receives the request's id.  ENOMEM if
+ * the request can never fit the budget, EINVAL for invalid arguments, ESHUTDOWN after destroy
+ * began. */
+SE2OT_API se2ot_status se2ot_serve_submit(se2ot_server sv, const se2ot_kernel_desc *desc, int n, const float *mu,
+                                          const double *lambda, const se2ot_solve_opts *opts, uint64_t *ticket);
+
+/* done = 1 once the request has finished (successfully or not). */
+SE2OT_API se2ot_status se2ot_serve_poll(se2ot_server sv, uint64_t ticket, int *done);
+
+/* Wait up to timeout_ms (< 0: forever) for the request, then copy its barycenter (V floats, host or
+ * device) to out (may be NULL) and its statistics (ms = latency from submit) to stats, and forget
+ * the ticket.  Returns the request's status (OK, ENOTCONV if the tolerance was not reached,
+ * ENONFINITE, ENOMEM if admission failed, ESHUTDOWN), or ETIMEOUT (the ticket stays valid). */
+SE2OT_API se2ot_status se2ot_serve_wait(se2ot_server sv, uint64_t ticket, float *out, se2ot_stats *stats,
+                                        int timeout_ms);
+
+/* Stop the server: queued requests finish with ESHUTDOWN, admitted ones run to completion, then
+ * the worker exits.  Tickets not yet waited for become invalid. */
+SE2OT_API se2ot_status se2ot_serve_destroy(se2ot_server sv);
+
 /* State of the kernel handle's most recent se2ot_barycenter / se2ot_interpolate solve with n
  * measures, for checkpointing and for checking the iteration's invariants: natural logarithms of
  * the scaling vectors v_i and of the marginals d_i = v_i (K w_i) (n*V doubles each) and of the

@@ -87,11 +87,18 @@ def lib():
     L.se2ot_barycenter_noalloc.argtypes = [ctypes.POINTER(se2ot_kernel_desc), i, vp, vp,
                                            ctypes.POINTER(se2ot_solve_opts), vp,
                                            ctypes.POINTER(se2ot_stats), vp]
+    L.se2ot_serve_create.argtypes = [ctypes.c_size_t, i, i, ctypes.POINTER(vp)]
+    L.se2ot_serve_submit.argtypes = [vp, ctypes.POINTER(se2ot_kernel_desc), i, vp, ctypes.POINTER(d),
+                                     ctypes.POINTER(se2ot_solve_opts), ctypes.POINTER(ctypes.c_uint64)]
+    L.se2ot_serve_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(i)]
+    L.se2ot_serve_wait.argtypes = [vp, ctypes.c_uint64, vp, ctypes.POINTER(se2ot_stats), i]
+    L.se2ot_serve_destroy.argtypes = [vp]
     L.se2ot_last_error.restype = ctypes.c_char_p
     L.se2ot_version.restype = ctypes.c_char_p
     for name in ("se2ot_kernel_build", "se2ot_kernel_destroy", "se2ot_kernel_taps", "se2ot_apply",
                  "se2ot_apply_log", "se2ot_barycenter", "se2ot_interpolate", "se2ot_barycenter_noalloc",
-                 "se2ot_state_export", "se2ot_interpolate_batched"):
+                 "se2ot_state_export", "se2ot_interpolate_batched", "se2ot_serve_create", "se2ot_serve_submit",
+                 "se2ot_serve_poll", "se2ot_serve_wait", "se2ot_serve_destroy"):
         getattr(L, name).restype = ctypes.c_int
     _LIB = L
     return L
@@ -282,3 +289,48 @@ def se2ot_interpolate_batched(descs, mu0s, mu1s, ts, opts=None, outs=None, strea
     if raise_on_error:
         _check(status)
     return outs, [s.as_dict() for s in st], status
+
+
+SE2OT_ETIMEOUT = 6
+SE2OT_ESHUTDOWN = 8
+
+
+class Server:
+    """se2ot_serve_*: continuous-batching request loop for barycenter solves."""
+
+    def __init__(self, budget_bytes, max_slots=8, device=0):
+        h = ctypes.c_void_p()
+        _check(lib().se2ot_serve_create(int(budget_bytes), int(max_slots), int(device), ctypes.byref(h)))
+        self.handle = h
+
+    def submit(self, desc, mu, lam, opts=None):
+        """Queue a barycenter of mu [n, ny, nx, ntheta] (float32, CPU or CUDA); returns a ticket."""
+        n = mu.shape[0]
+        t = ctypes.c_uint64()
+        lam_c = (ctypes.c_double * n)(*[float(x) for x in lam])
+        _check(lib().se2ot_serve_submit(self.handle, ctypes.byref(desc), n, _ptr(mu, torch.float32), lam_c,
+                                        ctypes.byref(opts if opts is not None else solve_opts()), ctypes.byref(t)))
+        return t.value
+
+    def poll(self, ticket):
+        d = ctypes.c_int()
+        _check(lib().se2ot_serve_poll(self.handle, ticket, ctypes.byref(d)))
+        return bool(d.value)
+
+    def wait(self, ticket, out, timeout_ms=-1):
+        """Copy the result into out (float32 tensor, CPU or CUDA); returns (stats dict, status)."""
+        st = se2ot_stats()
+        status = lib().se2ot_serve_wait(self.handle, ticket, _ptr(out, torch.float32) if out is not None else None,
+                                        ctypes.byref(st), int(timeout_ms))
+        return st.as_dict(), status
+
+    def close(self):
+        if self.handle:
+            lib().se2ot_serve_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

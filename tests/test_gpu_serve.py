@@ -1,0 +1,111 @@
+"""Serving with continuous batching (se2ot_serve_*): requests admitted by slots and a device-memory
+budget, their chunks overlapping on the device.  A request's result must be the same alone and in
+the mix (bit-for-bit: every request runs its own deterministic kernel sequence) and equal to
+se2ot_barycenter with the same options."""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2402_15322_gb300 import build, se2ot, synth
+
+pytestmark = pytest.mark.gpu
+
+W = (1.0, 3.0, 0.5)
+
+REQUESTS = [  # nx, ny, nt, r, eps, n, max_iters, check_every, tol
+    (32, 32, 8, 3, 0.1, 2, 600, 10, 5e-3),
+    (48, 40, 16, 4, 0.1, 3, 600, 10, 5e-3),
+    (40, 40, 8, 5, 1e-3, 4, 60, 0, 0.0),
+    (64, 48, 16, 6, 0.1, 2, 600, 20, 5e-3),
+    (36, 36, 4, 3, 5e-3, 5, 80, 0, 0.0),
+    (33, 29, 16, 4, 0.1, 2, 600, 10, 5e-3),
+    (56, 56, 8, 7, 0.1, 3, 600, 10, 5e-3),
+    (30, 30, 32, 3, 2e-2, 2, 50, 0, 0.0),
+]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+    se2ot.lib()
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+
+
+def make(k):
+    nx, ny, nt, r, eps, n, iters, check, tol = REQUESTS[k]
+    desc = se2ot.make_desc(nx, ny, nt, r, W, eps)
+    mu = synth.coupled_measures(n, nx, ny, nt, config_seed=40 + k, max_shift=1, nbumps=3).astype(np.float32)
+    lam = np.linspace(1.0, 2.0, n)
+    lam = (lam / lam.sum()).tolist()
+    return desc, torch.from_numpy(mu), lam, se2ot.solve_opts(iters, check, tol)
+
+
+def serve(reqs, budget, slots):
+    sv = se2ot.Server(budget, slots)
+    tickets = [sv.submit(d, mu, lam, o) for (d, mu, lam, o) in reqs]
+    results = []
+    for (d, mu, lam, o), t in zip(reqs, tickets):
+        out = torch.empty(mu.shape[1:], dtype=torch.float32)
+        st, status = sv.wait(t, out)
+        results.append((out, st, status))
+    sv.close()
+    return results
+
+
+def test_mix_equals_alone_and_single_solves():
+    reqs = [make(k) for k in range(len(REQUESTS))]
+    mixed = serve(reqs, budget=1 << 30, slots=4)
+    for k, (d, mu, lam, o) in enumerate(reqs):
+        alone = serve([reqs[k]], budget=1 << 30, slots=1)[0]
+        assert mixed[k][2] == alone[2] == se2ot.SE2OT_OK, (k, mixed[k][2], alone[2])
+        assert torch.equal(mixed[k][0], alone[0]), k
+        assert mixed[k][1]["iters"] == alone[1]["iters"]
+        kern = se2ot.se2ot_kernel_build(d)
+        single, sst, status = se2ot.se2ot_barycenter(kern, mu.cuda(), lam, o)
+        assert status == se2ot.SE2OT_OK
+        assert torch.equal(single.cpu(), mixed[k][0]), k
+        assert sst["iters"] == mixed[k][1]["iters"]
+        if o.tol_viol > 0:
+            assert mixed[k][1]["viol"] <= o.tol_viol
+        kern.close()
+
+
+def test_budget_admits_as_memory_frees_up():
+    """A budget that holds about one request at a time: everything still completes, in order."""
+    reqs = [make(k) for k in (0, 1, 3, 5)]
+    big = max(4 * 90 * r[0].nx * r[0].ny * r[0].ntheta * r[1].shape[0] for r in reqs)
+    res = serve(reqs, budget=big, slots=4)
+    ref = serve(reqs, budget=1 << 30, slots=4)
+    for (a, sa, ka), (b, sb, kb) in zip(res, ref):
+        assert ka == kb == se2ot.SE2OT_OK
+        assert torch.equal(a, b)
+
+
+def test_request_larger_than_budget_is_refused_and_timeouts():
+    d, mu, lam, o = make(6)
+    sv = se2ot.Server(1 << 20, 2)   # 1 MiB: too small for this request
+    with pytest.raises(se2ot.SE2OTError):
+        sv.submit(d, mu, lam, o)
+    sv.close()
+    sv = se2ot.Server(1 << 30, 2)
+    t = sv.submit(*make(6))
+    _, status = sv.wait(t, None, timeout_ms=0)
+    assert status in (se2ot.SE2OT_ETIMEOUT, se2ot.SE2OT_OK)
+    if status == se2ot.SE2OT_ETIMEOUT:
+        out = torch.empty(mu.shape[1:], dtype=torch.float32)
+        _, status = sv.wait(t, out)
+        assert status == se2ot.SE2OT_OK and torch.isfinite(out).all()
+    sv.close()
+
+
+def test_injected_admission_failure_rejects_only_that_request():
+    os.environ["SE2OT_TEST_FAIL_ADMISSION"] = "1"    # the second admission fails
+    try:
+        reqs = [make(k) for k in (0, 2, 4)]
+        res = serve(reqs, budget=1 << 30, slots=1)
+    finally:
+        del os.environ["SE2OT_TEST_FAIL_ADMISSION"]
+    assert [r[2] for r in res] == [se2ot.SE2OT_OK, se2ot.SE2OT_ENOMEM, se2ot.SE2OT_OK]
+    assert torch.isfinite(res[0][0]).all() and torch.isfinite(res[2][0]).all()
