@@ -61,6 +61,103 @@ BATCH = dict(nprob=64, iters=100,
                       "iterations in lockstep, FP32 log-domain path")
 
 
+SERVE = dict(requests=300, rate=25.0, slots=16, budget=16 << 30, sizes=[(64, 64, 16), (128, 128, 16)],
+             workload="Poisson stream of barycenter requests, n ~ U{2..8} measures, "
+                      "lambda ~ Dirichlet(1), grids 64^2x16 / 128^2x16, r ~ U{3..7}, eps log-uniform [1e-3, 1e-2], "
+                      "tol 1e-3 on the marginal violation (checked every 20 iterations, cap 2000)")
+
+
+def serve_requests(seed=6, rate=None, count=None):
+    """Seeded request stream: (arrival s, nx, ny, nt, r, eps, lambda, mu[n])."""
+    from paper_2402_15322_gb300 import synth
+    rng = synth.SplitMix64(synth.stream_seed(seed, 0, 1 << 23))
+    rate = rate or SERVE["rate"]
+    t = 0.0
+    out = []
+    for k in range(count or SERVE["requests"]):
+        t += -math.log(1.0 - rng.uniform()) / rate
+        nx, ny, nt = SERVE["sizes"][rng.randint(0, len(SERVE["sizes"]) - 1)]
+        n = rng.randint(2, 8)
+        r = rng.randint(3, 7)
+        eps = 10 ** rng.uniform(-3.0, -2.0)
+        g = [-math.log(1.0 - rng.uniform()) for _ in range(n)]   # Dirichlet(1) via exponentials
+        lam = [x / sum(g) for x in g]
+        mu = synth.coupled_measures(n, nx, ny, nt, config_seed=seed, problem=k, max_shift=1, nbumps=3)
+        out.append((t, nx, ny, nt, r, eps, lam, mu.astype(np.float32)))
+    return out
+
+
+def run_serve(args):
+    """Serving latency (p50/p99) and throughput under continuous batching, against serving the
+    same stream one request at a time through se2ot_barycenter."""
+    import threading
+
+    import torch
+
+    from paper_2402_15322_gb300 import build, se2ot
+    build.build()
+    torch.cuda.set_device(0)
+    rate = args.rate or SERVE["rate"]
+    count = args.requests or SERVE["requests"]
+    reqs = serve_requests(rate=rate, count=count)
+    opts = se2ot.solve_opts(2000, 20, 1e-3)
+    descs = [se2ot.make_desc(nx, ny, nt, r, W, eps) for (_, nx, ny, nt, r, eps, _, _) in reqs]
+    mus = [torch.from_numpy(q[7]) for q in reqs]
+    # warm-up: one request of each size
+    sv = se2ot.Server(SERVE["budget"], SERVE["slots"])
+    for k in range(min(4, len(reqs))):
+        out = torch.empty(mus[k].shape[1:], dtype=torch.float32)
+        sv.wait(sv.submit(descs[k], mus[k], reqs[k][6], opts), out)
+    tickets = [None] * len(reqs)
+    t0 = time.perf_counter()
+
+    def producer():
+        for k, q in enumerate(reqs):
+            delay = q[0] - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            tickets[k] = sv.submit(descs[k], mus[k], q[6], opts)
+
+    th = threading.Thread(target=producer)
+    th.start()
+    th.join()
+    lat, vox_it, statuses = [], 0, []
+    for k, q in enumerate(reqs):
+        out = torch.empty(mus[k].shape[1:], dtype=torch.float32)
+        st, status = sv.wait(tickets[k], out)
+        lat.append(st["ms"])
+        vox_it += q[1] * q[2] * q[3] * st["iters"]
+        statuses.append(status)
+    wall = time.perf_counter() - t0
+    sv.close()
+    # one at a time (FP32 single-solve path), same stream, same options: latency by a virtual clock
+    clock, slat, svox = 0.0, [], 0
+    kernels = {}
+    for k, q in enumerate(reqs):
+        key = (q[1], q[2], q[3], q[4], q[5])
+        if key not in kernels:
+            kernels[key] = se2ot.se2ot_kernel_build(descs[k])
+        mu_d = mus[k].cuda()
+        torch.cuda.synchronize()
+        s0 = time.perf_counter()
+        _, st, _ = se2ot.se2ot_barycenter(kernels[key], mu_d, q[6], opts, raise_on_error=False)
+        dt = time.perf_counter() - s0
+        clock = max(clock, q[0]) + dt
+        slat.append((clock - q[0]) * 1e3)
+        svox += q[1] * q[2] * q[3] * st["iters"]
+    for kern in kernels.values():
+        kern.close()
+    p = lambda a, f: float(np.percentile(np.asarray(a), f))
+    return {"metric": "SE(2) serving latency p50/p99 ms", "value": p(lat, 50), "unit": "ms", "n_gpus": 1,
+            "steps": 1, "warmup": 4, "higher_is_better": False, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": SERVE["workload"], "rate_per_s": rate, "requests": count, "slots": SERVE["slots"],
+                       "budget_bytes": SERVE["budget"]},
+            "serve": {"p50_ms": p(lat, 50), "p99_ms": p(lat, 99), "voxel_iters_per_s": vox_it / wall,
+                      "wall_s": wall, "ok": statuses.count(0), "not_converged": statuses.count(5)},
+            "one_at_a_time": {"p50_ms": p(slat, 50), "p99_ms": p(slat, 99), "voxel_iters_per_s": svox / clock,
+                              "wall_s": clock}}
+
+
 def large_inputs(problem=0):
     from paper_2402_15322_gb300 import synth
     return synth.curve_measures(LARGE["n"], LARGE["nx"], LARGE["ny"], LARGE["nt"], config_seed=5,
@@ -392,7 +489,9 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--iters", type=int, default=0,
                     help="Sinkhorn iterations per solve (profiling runs only; default: the workload's)")
-    ap.add_argument("--config", default="barycenter", choices=["barycenter", "large", "batched"],
+    ap.add_argument("--rate", type=float, default=0.0, help="serve: Poisson arrival rate (req/s)")
+    ap.add_argument("--requests", type=int, default=0, help="serve: number of requests")
+    ap.add_argument("--config", default="barycenter", choices=["barycenter", "large", "batched", "serve"],
                     help="workload: the 128^2x16 barycenter (default, the headline), the 512^2x32 "
                          "large solve, or the 64-problem uneven batch")
     args = ap.parse_args(argv)
@@ -401,6 +500,9 @@ def main(argv=None):
         res = run_reference(args)
         if res is not None:
             print(json.dumps(res), flush=True)
+        return 0
+    if args.config == "serve":
+        print(json.dumps(run_serve(args)), flush=True)
         return 0
     res = run_gpu(args)
     rank, world, _ = dist_env()
