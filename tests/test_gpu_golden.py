@@ -1,0 +1,60 @@
+"""The full 4-measure 128 x 128 x 16 barycenter (r = 10, w = (1, 3, 0.5), eps = 1e-4, 500 Sinkhorn
+iterations of Appendix A) on the device, in the launch configuration the benchmark times, against
+stored values of the FP64 oracle's run of the same solve (tests/golden/make_golden.py, which calls
+only the oracle).  The oracle takes hours on this size, so the file holds a seeded sample of 4096
+voxels and reductions the test recomputes from the device result: 8 x 8 spatial block sums, the
+per-orientation sums and the mass.  Bar: 1e-5 relative L1 (the FP32 path's target)."""
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2402_15322_gb300 import build, se2ot, synth
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "barycenter_128x128x16_r10_500it.json")
+
+
+@pytest.fixture(scope="module")
+def golden():
+    build.build()
+    se2ot.lib()
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    with open(GOLDEN) as f:
+        return json.load(f)
+
+
+def rel_l1(got, want):
+    got, want = np.asarray(got, np.float64), np.asarray(want, np.float64)
+    return np.abs(got - want).sum() / np.abs(want).sum()
+
+
+@pytest.mark.parametrize("flags", [se2ot.SE2OT_FLAG_TIME_CONV, 0])
+def test_500_iterations_against_stored_oracle(golden, flags):
+    nx, ny, nt = golden["grid"]
+    n = golden["measures"]
+    mu = synth.coupled_measures(n, nx, ny, nt, config_seed=2, max_shift=golden["radius"] // 2, nbumps=5)
+    mu = torch.from_numpy(mu.astype(np.float32)).cuda()
+    k = se2ot.se2ot_kernel_build(se2ot.make_desc(nx, ny, nt, golden["radius"], golden["w"], golden["eps"]))
+    out, st, status = se2ot.se2ot_barycenter(k, mu, golden["lambda"],
+                                             se2ot.solve_opts(golden["iterations"], flags=flags))
+    k.close()
+    assert status == se2ot.SE2OT_OK and st["iters"] == golden["iterations"]
+    bary = out.cpu().double().numpy()
+    assert np.isfinite(bary).all() and (bary >= 0).all()
+    flat = bary.reshape(-1)
+    idx = np.asarray(golden["sample_index"])
+    e_sample = rel_l1(flat[idx], golden["sample_value"])
+    blocks = bary.reshape(ny // 8, 8, nx // 8, 8, nt).sum(axis=(1, 3, 4)).reshape(-1)
+    e_block = rel_l1(blocks, golden["block_sum_8x8"])
+    e_slice = rel_l1(bary.sum(axis=(0, 1)), golden["slice_sum"])
+    e_mass = abs(bary.sum() - golden["mass"]) / golden["mass"]
+    print(f"sample {e_sample:.3e} block {e_block:.3e} slice {e_slice:.3e} mass {e_mass:.3e} "
+          f"viol {st['viol']:.6e} (oracle {golden['viol']:.6e})")
+    assert e_sample <= 1e-5 and e_block <= 1e-5 and e_slice <= 1e-5 and e_mass <= 1e-5
+    # the reported statistics are the FP64 reductions of the device state
+    assert abs(st["mass"] - golden["mass"]) / golden["mass"] <= 1e-5
+    assert abs(st["viol"] - golden["viol"]) / golden["viol"] <= 1e-3
