@@ -107,7 +107,7 @@ __global__ void redo_kernel(ConvArgs a0, const ConvArgs *probs)
         else c = m + log2(s);
         if (lane == 0) {
             const float2 cd = df_from_double(c);   // c as an exact-enough hi + lo pair
-            tile::write_out(a, flat, b, o, y, x, cd.x, cd.y);
+            tile::write_out(a, flat, b, o, y, x, make_float2(cd.x, 0.f), cd.y);
         }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0 && a0.redo_total) atomicAdd(a0.redo_total, (unsigned long long)n);

@@ -21,6 +21,17 @@
 // of FP32's).  Outputs whose log2 sum leaves [-24, 16] are queued for the exact FP64 recompute of
 // conv.cu.
 //
+// Affine shift (the common case): the scaling vectors are smooth on the grid, so the XQ shifts of
+// a thread usually lie close to a line, S_j ~ T_j = S_0 + g j (g on a 2^-6 grid, |g| <= 32).  With
+// that shift the term splits exactly into a part of the input position alone and a part of the
+// tap alone,
+//   t = u_k + tp(dx),  u_k = in_k - (S_0 - lt) - g k,  tp(dx) = ls(dx) + g (2R - dx index),
+// since dx index = j - k + 2R: u_k is formed once per window position and tp once per kernel row,
+// and each term costs one add, one ex2 and the accumulation.  A warp takes this path when every
+// shift of its threads is within DEV_MAX of the thread's line (the result of output j is then
+// T_j + log2 acc_j, accepted for log2 acc_j within [-24 - DEV_MAX, 16 + DEV_MAX]); otherwise it
+// takes the per-output form above.
+//
 // Skipping (exact at FP32 resolution): a pair (o, i) is skipped by the CTA when lt(o, i) +
 // max(in over the tile's halo of slice i) (from the tile-max pre-pass; the spatial taps are <= 0)
 // is 2^-64 below the smallest shift of the CTA; a kernel row dy is skipped by a warp when the same
@@ -41,6 +52,8 @@ constexpr int ROW_LANES = TX / XQ;         // lanes per output row
 constexpr int MAX_NT = 64;   // largest ntheta (validated by the library)
 constexpr float SKIP_MARGIN = 64.f;
 constexpr float ACC_LO = -24.f, ACC_HI = 16.f;
+constexpr float G_MAX = 32.f;      // largest slope of an affine shift (log2 units per voxel)
+constexpr float DEV_MAX = 8.f;     // largest distance of a shift from its thread's line
 
 __device__ __forceinline__ float ex2(float x)
 {
@@ -70,26 +83,31 @@ __device__ __forceinline__ int wrapi(int v, int n)
     return v < 0 ? v + n : v;
 }
 
-// Epilogue of one output, c = log2 (K * 2^in)(g, o) given exactly as s + l (two floats).  flat
-// indexes the slice-major arrays; the apply epilogues write the caller's [b][y][x][o] in FP64
-// arithmetic (not on the Sinkhorn loop); the Sinkhorn epilogues stay in FP32 double-floats.
-__device__ __forceinline__ void write_out(const ConvArgs &a, long flat, int b, int o, int y, int x, float s, float l)
+// Epilogue of one output, c = log2 (K * 2^in)(g, o) given exactly as sh + l (shift sh a
+// double-float, l = log2 of the accumulated sum).  flat indexes the slice-major arrays; the apply
+// epilogues write the caller's [b][y][x][o] in FP64 arithmetic (not on the Sinkhorn loop); the
+// Sinkhorn epilogues stay in FP32 double-floats.
+__device__ __forceinline__ void write_out(const ConvArgs &a, long flat, int b, int o, int y, int x, float2 sh, float l)
 {
     switch (a.epi) {
     case EPI_LOG_OUT:
-        a.out64[(((long)b * a.ny + y) * a.nx + x) * a.nt + o] = ((double)s + (double)l) * a.out_scale;
+        a.out64[(((long)b * a.ny + y) * a.nx + x) * a.nt + o] = ((double)sh.x + (double)sh.y + (double)l) * a.out_scale;
         break;
     case EPI_LIN_OUT:
-        a.out32[(((long)b * a.ny + y) * a.nx + x) * a.nt + o] = (float)exp2((double)s + (double)l);
+        a.out32[(((long)b * a.ny + y) * a.nx + x) * a.nt + o] = (float)exp2((double)sh.x + (double)sh.y + (double)l);
         break;
-    case EPI_W:
-        a.out2[flat] = df_add(a.aux[flat], df_neg(df_two_sum(s, l)));   // w_i = mu_i / K v_i
-        a.hint[flat] = s + l;
+    case EPI_W: {
+        const float2 c = df_add(sh, make_float2(l, 0.f));
+        a.out2[flat] = df_add(a.aux[flat], df_neg(c));   // w_i = mu_i / K v_i
+        a.hint[flat] = c.x + c.y;
         break;
-    default:
-        a.out2[flat] = df_add(a.aux[flat], df_two_sum(s, l));           // d_i = v_i K w_i
-        a.hint[flat] = s + l;
+    }
+    default: {
+        const float2 c = df_add(sh, make_float2(l, 0.f));
+        a.out2[flat] = df_add(a.aux[flat], c);           // d_i = v_i K w_i
+        a.hint[flat] = c.x + c.y;
         break;
+    }
     }
 }
 
@@ -151,6 +169,24 @@ __global__ void __launch_bounds__(THREADS, 6) conv_tile_kernel(const ConvArgs a0
         }
         S[j] = s;
         acc[j] = MAXPASS ? -INFINITY : 0.f;
+    }
+    // affine shift T_j = S_0 + g j of the thread's outputs, and whether the whole warp can use it
+    const float S0 = S[0];
+    float g = 0.f;
+    bool fast = false;
+    if (!MAXPASS) {
+        int jl = 0;
+#pragma unroll
+        for (int j = 1; j < XQ; ++j)
+            if (valid[j]) jl = j;
+        if (jl > 0) g = (S[jl] - S0) / (float)jl;
+        g = rintf(fminf(fmaxf(g, -G_MAX), G_MAX) * 64.f) * (1.f / 64.f);
+        float dev = 0.f;
+#pragma unroll
+        for (int j = 1; j < XQ; ++j)
+            if (valid[j]) dev = fmaxf(dev, fabsf(S[j] - fmaf((float)j, g, S0)));
+        fast = __all_sync(0xffffffffu, dev <= DEV_MAX);
+        if (!fast) g = 0.f;   // the tilted taps below are then the plain taps
     }
     float wmin = smin;   // smallest shift of the warp's outputs (row/column skipping)
     if (!MAXPASS) {
@@ -266,14 +302,39 @@ __global__ void __launch_bounds__(THREADS, 6) conv_tile_kernel(const ConvArgs a0
             rows_eval += (unsigned)(min(WIN4 - 1, khi >> 2) - (klo >> 2) + 1);
             const float *rh = hhi + (yl + 2 * R - dyi) * HXP + xl;
             const float *rl = hlo + (yl + 2 * R - dyi) * HXP + xl;
+            // taps of the row, tilted by the affine shift (g = 0: the plain taps, exactly)
             float th[D];
 #pragma unroll
             for (int d4 = 0; d4 < TP / 4; ++d4) {
                 const float4 t4 = *reinterpret_cast<const float4 *>(ts + dyi * TP + 4 * d4);
-                if (4 * d4 + 0 < D) th[4 * d4 + 0] = t4.x;
-                if (4 * d4 + 1 < D) th[4 * d4 + 1] = t4.y;
-                if (4 * d4 + 2 < D) th[4 * d4 + 2] = t4.z;
-                if (4 * d4 + 3 < D) th[4 * d4 + 3] = t4.w;
+                const float tv[4] = {t4.x, t4.y, t4.z, t4.w};
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    if (4 * d4 + c < D) th[4 * d4 + c] = fmaf(g, (float)(2 * R - 4 * d4 - c), tv[c]);
+            }
+            if (!MAXPASS && fast) {   // uniform over the warp
+#pragma unroll
+                for (int k4 = 0; k4 < WIN4; ++k4) {
+                    if (4 * k4 + 3 < klo || 4 * k4 > khi) continue;
+                    const float4 h4 = *reinterpret_cast<const float4 *>(rh + 4 * k4);
+                    const float4 l4 = *reinterpret_cast<const float4 *>(rl + 4 * k4);
+                    const float wh4[4] = {h4.x, h4.y, h4.z, h4.w};
+                    const float wl4[4] = {l4.x, l4.y, l4.z, l4.w};
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) {
+                        const int k = 4 * k4 + kk;
+                        if (k >= WIN) continue;
+                        // u_k = in_k - (S_0 - lt) - g k
+                        const float u = fmaf(-(float)k, g, wh4[kk] - Shi[0]) + (wl4[kk] - Slo[0]);
+#pragma unroll
+                        for (int j = 0; j < XQ; ++j) {
+                            const int dxi = j - k + 2 * R;
+                            if (dxi < 0 || dxi >= D) continue;
+                            acc[j] += ex2(u + th[dxi]);
+                        }
+                    }
+                }
+                continue;
             }
 #pragma unroll
             for (int k4 = 0; k4 < WIN4; ++k4) {
@@ -321,13 +382,15 @@ __global__ void __launch_bounds__(THREADS, 6) conv_tile_kernel(const ConvArgs a0
             continue;
         }
         const float lacc = log2f(acc[j]);
-        if (!(lacc >= ACC_LO && lacc <= ACC_HI)) {
+        const float wlo = fast ? ACC_LO - DEV_MAX : ACC_LO, whi = fast ? ACC_HI + DEV_MAX : ACC_HI;
+        if (!(lacc >= wlo && lacc <= whi)) {
             const unsigned k = atomicAdd(a.redo_count, 1u);
             a.redo_list[k] = make_int2(p, (int)flat);
             omax = INFINITY;          // value unknown until the exact recompute: no skipping on it
             continue;
         }
-        write_out(a, flat, b, o, gy, x0 + xl + j, S[j], lacc);
+        const float2 sh = fast ? df_two_sum(S0, g * (float)j) : make_float2(S[j], 0.f);   // g j is exact
+        write_out(a, flat, b, o, gy, x0 + xl + j, sh, lacc);
         if (a.tmax_out) omax = fmaxf(omax, a.out2[flat].x);
     }
     if (!MAXPASS && a.tmax_out) {   // uniform over the CTA
