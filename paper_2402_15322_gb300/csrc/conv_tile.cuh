@@ -7,9 +7,12 @@
 //
 // One CTA computes one output orientation o of a TY x TX spatial tile of one field; each thread
 // owns XQ consecutive x positions of one row.  For every input orientation i that can
-// contribute (see skipping), the CTA stages slice i of the input halo ((32 + 2R)^2, FP64 split
-// into FP32 hi + lo) and the (2R+1)^2 spatial taps of the pair in shared memory, then each thread
-// walks the rows of the window; the (2R+1)-tap row is fully unrolled (R is a template parameter).
+// contribute (see skipping), the CTA stages slice i of the input halo ((TY + 2R) x (TX + 2R)
+// double-floats, split into an FP32 hi and a lo plane) and the (2R+1)^2 spatial taps of the pair
+// in shared memory, then each thread walks the rows of the window; the (2R+1)-tap row is fully
+// unrolled (R is a template parameter).  Staging is asynchronous (cp.async) and double-buffered:
+// the next contributing slice is copied while the current one is summed.  Halo cells outside the
+// grid (zero boundary) are set to 2^-inf once per CTA; the copies only write cells inside it.
 //
 // Shift and precision: output j of a thread is evaluated as
 //   S_j + log2 sum 2^t,  t = ((in_hi - S'_j,hi) + ls) + (in_lo - S'_j,lo),   S'_j = S_j - lt(o, i)
@@ -62,20 +65,30 @@ __device__ __forceinline__ float ex2(float x)
     return y;
 }
 
-__host__ __device__ constexpr int halo_pitch(int hx)
-{
-    // >= hx, multiple of 4 (16-byte rows for float4 loads) and 4 mod 32: the 8 lanes of a
-    // quarter-warp (x-groups of XQ floats over 32 / XQ rows) hit 32 distinct banks
-    return ((hx + 27) / 32) * 32 + 4;
-}
+// Row pitch of a staged plane: 16-byte rows for float4 loads.  A quarter-warp reads 8
+// consecutive float4 of one row, so any pitch is free of bank conflicts.
+__host__ __device__ constexpr int halo_pitch(int hx) { return (hx + 3) & ~3; }
 
 __host__ __device__ constexpr int tap_pitch(int d) { return (d + 3) & ~3; }
 
+// One staging buffer: hi and lo planes of the halo, then the taps of the pair.
+__host__ __device__ constexpr int stage_floats(int r)
+{
+    return 2 * (TY + 2 * r) * halo_pitch(TX + 2 * r) + (2 * r + 1) * tap_pitch(2 * r + 1);
+}
+
 __host__ __device__ constexpr size_t smem_floats(int r)
 {
-    return (size_t)2 * (TY + 2 * r) * halo_pitch(TX + 2 * r) + (size_t)(2 * r + 1) * tap_pitch(2 * r + 1) +
-           (size_t)(TY + 2 * r) + 8 + 3 * MAX_NT + 8;
+    return (size_t)2 * stage_floats(r) + (size_t)(TY + 2 * r) + 8 + 4 * MAX_NT + 8;
 }
+
+__device__ __forceinline__ void cp_async4(float *dst, const float *src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 __device__ __forceinline__ int wrapi(int v, int n)
 {
@@ -135,14 +148,14 @@ __global__ void __launch_bounds__(THREADS, 6) conv_tile_kernel(const ConvArgs a0
     constexpr int HX = TX + 2 * R, HY = TY + 2 * R, HXP = halo_pitch(HX), TP = tap_pitch(D);
     constexpr int WIN = XQ + 2 * R;        // window of one thread row: x' in [xl, xl + WIN)
     constexpr int WIN4 = (WIN + 3) / 4;
+    constexpr int SF = stage_floats(R);
+    // two staging buffers, each [HY][HXP] hi, [HY][HXP] lo, [D][TP] spatial taps of the pair
     extern __shared__ __align__(16) float smem[];
-    float *hhi = smem;
-    float *hlo = hhi + HY * HXP;
-    float *ts = hlo + HY * HXP;            // [D][TP] spatial taps of the pair (hi)
-    float *rowmax = ts + D * TP;           // [HY]
+    float *rowmax = smem + 2 * SF;         // [HY]
     float *red = rowmax + HY;              // [THREADS / 32]
     float2 *lts = (float2 *)(red + 8);     // [nt] orientation factors lt(o, i)
     int *need = (int *)(lts + MAX_NT);     // [nt] slice i contributes
+    int *nlist = need + MAX_NT;            // [nt] contributing slices, in order; nlist[MAX_NT]: count
 
     const int nx = a.nx, ny = a.ny, nt = a.nt;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -224,36 +237,72 @@ __global__ void __launch_bounds__(THREADS, 6) conv_tile_kernel(const ConvArgs a0
         }
         need[i] = nd;
     }
-    __syncthreads();
-
-    unsigned rows_eval = 0;
-    for (int i = 0; i < nt; ++i) {
-        if (!need[i]) continue;   // uniform over the CTA
-        const float2 lt = lts[i];
-        __syncthreads();   // the previous slice is no longer read
-        const float2 *src = in_b + (long)i * plane;
-#pragma unroll 8
+    // cells the copies never write: the taps' padding columns and (zero boundary) the halo cells
+    // outside the grid, in both buffers
+    for (int idx = tid; idx < D * (TP - D); idx += THREADS) {
+        const int dy = idx / (TP - D), dx = D + idx - dy * (TP - D);
+        smem[2 * HY * HXP + dy * TP + dx] = -INFINITY;
+        smem[SF + 2 * HY * HXP + dy * TP + dx] = -INFINITY;
+    }
+    if (!a.periodic && (x0 < R || y0 < R || x0 + TX + R > nx || y0 + TY + R > ny)) {
         for (int idx = tid; idx < HY * HX; idx += THREADS) {
             const int hy = idx / HX, hx = idx - hy * HX;
-            int sy = y0 - R + hy, sx = x0 - R + hx;
-            bool inside = true;
-            if (a.periodic) {
-                sy = wrapi(sy, ny);
-                sx = wrapi(sx, nx);
-            } else {
-                inside = sy >= 0 && sy < ny && sx >= 0 && sx < nx;
+            const int sy = y0 - R + hy, sx = x0 - R + hx;
+            if (sy >= 0 && sy < ny && sx >= 0 && sx < nx) continue;
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                smem[q * SF + hy * HXP + hx] = -INFINITY;
+                smem[q * SF + HY * HXP + hy * HXP + hx] = 0.f;
             }
-            float2 v = make_float2(-INFINITY, 0.f);
-            if (inside) v = src[(long)sy * nx + sx];
-            hhi[hy * HXP + hx] = v.x;
-            hlo[hy * HXP + hx] = v.y;
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int c = 0;
+        for (int i = 0; i < nt; ++i)
+            if (need[i]) nlist[c++] = i;
+        nlist[MAX_NT] = c;
+    }
+    __syncthreads();
+    const int nn = nlist[MAX_NT];
+
+    // asynchronous copy of slice i and its taps into buffer q: one warp per halo row
+    auto stage = [&](int i, int q) {
+        float *bh = smem + q * SF, *bl = bh + HY * HXP, *bt = bl + HY * HXP;
+        const float *src = reinterpret_cast<const float *>(in_b + (long)i * plane);
+        for (int hy = warp; hy < HY; hy += THREADS / 32) {
+            int sy = y0 - R + hy;
+            if (a.periodic) sy = wrapi(sy, ny);
+            else if (sy < 0 || sy >= ny) continue;
+            const float *srow = src + 2 * (long)sy * nx;
+#pragma unroll
+            for (int c = 0; c < (HX + 31) / 32; ++c) {
+                const int hx = lane + 32 * c;
+                if (hx >= HX) continue;
+                int sx = x0 - R + hx;
+                if (a.periodic) sx = wrapi(sx, nx);
+                else if (sx < 0 || sx >= nx) continue;
+                cp_async4(bh + hy * HXP + hx, srow + 2 * sx);
+                cp_async4(bl + hy * HXP + hx, srow + 2 * sx + 1);
+            }
         }
         const float *tsrc = a.ls + ((long)o * nt + i) * D * D;
-        for (int idx = tid; idx < D * TP; idx += THREADS) {
-            const int dy = idx / TP, dx = idx - dy * TP;
-            ts[idx] = dx < D ? tsrc[dy * D + dx] : -INFINITY;
+        for (int idx = tid; idx < D * D; idx += THREADS) {
+            const int dy = idx / D;
+            cp_async4(bt + dy * TP + idx - dy * D, tsrc + idx);
         }
-        __syncthreads();
+        cp_async_commit();
+    };
+    if (nn > 0) stage(nlist[0], 0);
+
+    unsigned rows_eval = 0;
+    for (int qi = 0; qi < nn; ++qi) {
+        const int i = nlist[qi];
+        const float2 lt = lts[i];
+        const float *hhi = smem + (qi & 1) * SF, *hlo = hhi + HY * HXP, *ts = hlo + HY * HXP;
+        cp_async_wait_all();
+        __syncthreads();   // slice qi has landed; nobody reads the other buffer (slice qi - 1) any more
+        if (qi + 1 < nn) stage(nlist[qi + 1], (qi + 1) & 1);
         if (!MAXPASS) {
             // row maxima of the staged halo: one warp per row, lanes across the row
             for (int hy = warp; hy < HY; hy += THREADS / 32) {
@@ -284,9 +333,10 @@ __global__ void __launch_bounds__(THREADS, 6) conv_tile_kernel(const ConvArgs a0
                 // kernel row dyi for this warp: its WARP_ROWS output rows read halo rows
                 // wy + 2R - dyi .. wy + 2R - dyi + WARP_ROWS - 1 (wy = WARP_ROWS * warp).  Largest
                 // input there:
-                float m = lane < WARP_ROWS ? rowmax[WARP_ROWS * warp + 2 * R - dyi + lane] : -INFINITY;
+                const float *rm = rowmax + WARP_ROWS * warp + 2 * R - dyi;
+                float m = rm[0];
 #pragma unroll
-                for (int off = 16; off; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+                for (int r = 1; r < WARP_ROWS; ++r) m = fmaxf(m, rm[r]);
                 // taps that can matter: ls >= thr.  The spatial taps of a row are a concave
                 // quadratic in dx, so they form one interval [lo, hi] of dx indices; a thread's
                 // window positions that meet them are k in [2R - hi, 2R - lo + XQ - 1].
