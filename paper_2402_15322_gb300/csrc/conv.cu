@@ -126,6 +126,24 @@ cudaError_t dispatch(int r, const ConvArgs &a, bool maxpass, const ConvArgs *pro
 
 }  // namespace
 
+namespace {
+__global__ void order_init_kernel(unsigned *order, unsigned *cost, long n)
+{
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        order[i] = (unsigned)i;
+        cost[i] = 0;
+    }
+}
+}  // namespace
+
+cudaError_t launch_order_init(unsigned *order, unsigned *cost, unsigned *done, long count, cudaStream_t s)
+{
+    if (count > 0) order_init_kernel<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(order, cost, count);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? cudaMemsetAsync(done, 0, sizeof(unsigned), s) : e;
+}
+
 int conv_tiles(int nx, int ny) { return ((nx + tile::TX - 1) / tile::TX) * ((ny + tile::TY - 1) / tile::TY); }
 
 size_t conv_smem_bytes(int r) { return sizeof(float) * tile::smem_floats(r); }

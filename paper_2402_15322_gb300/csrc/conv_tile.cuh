@@ -124,6 +124,38 @@ __device__ __forceinline__ void write_out(const ConvArgs &a, long flat, int b, i
     }
 }
 
+// The tiles by decreasing cost (bucketed: NB buckets of equal width up to the largest cost,
+// arbitrary order within a bucket), by one CTA.  hist and cur hold NB ints of shared memory.
+constexpr int NB = 64;
+__device__ __forceinline__ void lpt_order(unsigned *order, const unsigned *cost, unsigned total, int *hist, int *cur)
+{
+    const int tid = threadIdx.x;
+    unsigned mx = 0;
+    for (unsigned t = tid; t < total; t += THREADS) mx = max(mx, __ldcg(cost + t));
+#pragma unroll
+    for (int off = 16; off; off >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    if (tid < NB) hist[tid] = 0;
+    if (tid == 0) cur[0] = 0;
+    __syncthreads();
+    if ((tid & 31) == 0) atomicMax((unsigned *)cur, mx);   // cur[0]: the largest cost
+    __syncthreads();
+    mx = (unsigned)cur[0];
+    auto bucket = [&](unsigned c) {   // 0: the heaviest
+        return NB - 1 - (int)min((unsigned long long)NB - 1, (unsigned long long)c * NB / ((unsigned long long)mx + 1));
+    };
+    for (unsigned t = tid; t < total; t += THREADS) atomicAdd(hist + bucket(__ldcg(cost + t)), 1);
+    __syncthreads();
+    if (tid == 0) {
+        int run = 0;
+        for (int k = 0; k < NB; ++k) {
+            cur[k] = run;
+            run += hist[k];
+        }
+    }
+    __syncthreads();
+    for (unsigned t = tid; t < total; t += THREADS) order[atomicAdd(cur + bucket(__ldcg(cost + t)), 1)] = t;
+}
+
 // Single problem (BATCHED false): tile (blockIdx.x, blockIdx.y) of field*orientation blockIdx.z of
 // a0, read from the kernel parameters.  Batch: CTA k works on items[k] = (problem, field * nt +
 // orientation, tile x, tile y), the problem's arguments read from probs.
@@ -132,6 +164,7 @@ __global__ void __launch_bounds__(THREADS, 6) conv_tile_kernel(const ConvArgs a0
                                                                const int4 *items)
 {
     int p = 0, bo, tx, ty;
+    unsigned tile_id = 0;   // single problem: (bo * tiles y + ty) * tiles x + tx
     if (BATCHED) {
         const int4 it = items[blockIdx.x];
         p = it.x;
@@ -139,10 +172,13 @@ __global__ void __launch_bounds__(THREADS, 6) conv_tile_kernel(const ConvArgs a0
         tx = it.z;
         ty = it.w;
     } else {
-        bo = blockIdx.z;
-        tx = blockIdx.x;
-        ty = blockIdx.y;
+        tile_id = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+        if (a0.order) tile_id = a0.order[tile_id];
+        tx = tile_id % gridDim.x;
+        ty = (tile_id / gridDim.x) % gridDim.y;
+        bo = tile_id / (gridDim.x * gridDim.y);
     }
+    const long long t_start = clock64();
     const ConvArgs &a = BATCHED ? probs[p] : a0;
     constexpr int D = 2 * R + 1;
     constexpr int HX = TX + 2 * R, HY = TY + 2 * R, HXP = halo_pitch(HX), TP = tap_pitch(D);
@@ -452,6 +488,22 @@ __global__ void __launch_bounds__(THREADS, 6) conv_tile_kernel(const ConvArgs a0
         if (tid == 0) {
             for (int w = 1; w < THREADS / 32; ++w) omax = fmaxf(omax, red[w]);
             a.tmax_out[((long)b * nt + o) * ntiles + ty * ntx + tx] = omax;
+        }
+    }
+    if (!BATCHED && a.order) {   // uniform over the CTA
+        __shared__ int s_last;
+        const unsigned total = gridDim.x * gridDim.y * gridDim.z;
+        __syncthreads();
+        if (tid == 0) {
+            a.cost[tile_id] = (unsigned)min(clock64() - t_start, 0xffffffffLL);
+            __threadfence();
+            s_last = atomicAdd(a.done, 1u) == total - 1;
+        }
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            lpt_order(a.order, a.cost, total, nlist, need);
+            if (tid == 0) *a.done = 0;
         }
     }
 }

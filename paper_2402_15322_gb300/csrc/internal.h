@@ -44,6 +44,11 @@ struct ConvArgs {
     unsigned *redo_count;    // entries in redo_list
     unsigned long long *redo_total;  // running total for statistics
     unsigned long long *eval_count;  // kernel terms evaluated (not skipped)
+    // Launch order of the tiles (single-problem launches, optional): CTA k computes tile order[k]
+    // and records its duration in cost[tile]; the last CTA to finish (counted in *done, 0 between
+    // launches) writes into order the tiles by decreasing cost for the next launch with these
+    // arguments.  Any permutation gives the same results; heavy tiles first shortens the tail.
+    unsigned *order, *cost, *done;
     int nx, ny, nt, r, periodic, batch, epi;
 };
 
@@ -69,6 +74,8 @@ cudaError_t launch_conv_batch(int r, const ConvArgs &shared, const ConvArgs *pro
                               cudaStream_t s);
 cudaError_t launch_redo_batch(const ConvArgs &shared, const ConvArgs *probs, int max_blocks, cudaStream_t s);
 int conv_tiles(int nx, int ny);          // spatial tiles of one slice (size of tmax per slice)
+// order[k] = k for k < count, cost = 0, *done = 0 (the identity launch order).
+cudaError_t launch_order_init(unsigned *order, unsigned *cost, unsigned *done, long count, cudaStream_t s);
 size_t conv_smem_bytes(int r);           // dynamic shared memory of one convolution CTA
 
 // Host helpers of solver.cu shared with other entry points.

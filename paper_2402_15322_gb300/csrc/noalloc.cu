@@ -149,6 +149,7 @@ extern "C" se2ot_status se2ot_barycenter_noalloc(const se2ot_kernel_desc *desc, 
     dry.take<float>(nV);
     dry.take<float>(nV);
     dry.take<int2>(nV);
+    dry.take<unsigned>(4 * ntmax + 2);
     dry.take<unsigned>(4);
     dry.take<unsigned long long>(2);
     dry.take<double>(2 * STATS_BLOCKS);
@@ -172,6 +173,7 @@ extern "C" se2ot_status se2ot_barycenter_noalloc(const se2ot_kernel_desc *desc, 
     float2 *L = c.take<float2>((size_t)V);
     float *h1 = c.take<float>(nV), *h2 = c.take<float>(nV);
     int2 *redo = c.take<int2>(nV);
+    unsigned *ord = c.take<unsigned>(4 * ntmax + 2);
     unsigned *count = c.take<unsigned>(4);
     unsigned long long *totals = c.take<unsigned long long>(2);
     double *partial = c.take<double>(2 * STATS_BLOCKS);
@@ -188,7 +190,7 @@ extern "C" se2ot_status se2ot_barycenter_noalloc(const se2ot_kernel_desc *desc, 
     NCK(launch_init(mu, lmu, lv, h1, h2, n, desc->nx, desc->ny, nt, s), "init launch");
     const bool fused_max = desc->boundary == SE2OT_BOUNDARY_ZERO;
     if (fused_max) NCK(cudaMemsetAsync(tmax, 0, ntmax * sizeof(float), s), "cudaMemsetAsync(tmax)");
-    long long launches = 3;
+    long long launches = 5;
 
     ConvArgs aw;
     std::memset(&aw, 0, sizeof aw);
@@ -225,6 +227,14 @@ extern "C" se2ot_status se2ot_barycenter_noalloc(const se2ot_kernel_desc *desc, 
     ad.tmax = tmax2;
     ad.tmax_w = tmax2;
     ad.tmax_ready = fused_max;
+    aw.order = ord;
+    aw.cost = ord + ntmax;
+    aw.done = ord + 4 * ntmax;
+    ad.order = ord + 2 * ntmax;
+    ad.cost = ord + 3 * ntmax;
+    ad.done = ord + 4 * ntmax + 1;
+    NCK(launch_order_init(aw.order, aw.cost, aw.done, (long)ntmax, s), "order init");
+    NCK(launch_order_init(ad.order, ad.cost, ad.done, (long)ntmax, s), "order init");
 
     int it = 0;
     bool converged = false;

@@ -138,6 +138,8 @@ struct se2ot_kernel_s {
     float *tmax = nullptr, *tmax2 = nullptr;   // tile maxima of lv (and apply inputs), of lw
     int last_n = 0;                            // measures of the last completed solve
     size_t c_tmax = 0, c_tmax2 = 0;
+    unsigned *ord = nullptr;                   // tile launch orders and costs of the two convolutions, 2 counters
+    size_t c_ord = 0;
     std::vector<cudaEvent_t> ev;
 };
 
@@ -176,6 +178,7 @@ se2ot_status ensure_solver_ws(se2ot_kernel k, int n)
     CK(grow(k->redo, k->c_redo, nV), "cudaMalloc(redo)");
     CK(grow(k->tmax, k->c_tmax, (size_t)n * k->d.ntheta * conv_tiles(k->d.nx, k->d.ny)), "cudaMalloc(tmax)");
     CK(grow(k->tmax2, k->c_tmax2, (size_t)n * k->d.ntheta * conv_tiles(k->d.nx, k->d.ny)), "cudaMalloc(tmax)");
+    CK(grow(k->ord, k->c_ord, 4 * (size_t)n * k->d.ntheta * conv_tiles(k->d.nx, k->d.ny) + 2), "cudaMalloc(order)");
     return SE2OT_OK;
 }
 
@@ -274,7 +277,7 @@ se2ot_status se2ot_kernel_destroy(se2ot_kernel k)
     if (!k) return SE2OT_OK;
     cudaDeviceSynchronize();
     void *ptrs[] = {k->taps.ltheta, k->taps.ls, k->taps.ls_lo, k->taps.lsrow, k->tmax, k->tmax2, k->lmu, k->lv, k->lw, k->ld, k->L, k->lf, k->h1, k->h2, k->hint_ws,
-                    k->mu_stage, k->bary_stage, k->redo, k->counters, k->redo_total, k->partial, k->scal};
+                    k->mu_stage, k->bary_stage, k->redo, k->counters, k->redo_total, k->partial, k->scal, k->ord};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : k->ev) cudaEventDestroy(e);
@@ -421,7 +424,17 @@ se2ot_status se2ot_barycenter(se2ot_kernel k, int n, const float *mu, const doub
     aw.out2 = k->lw;
     aw.tmax_ready = fused_max;
     aw.tmax_out = fused_max ? k->tmax2 : nullptr;   // tile maxima of lw, for the d-convolution
+    const long ntile = (long)n * k->d.ntheta * conv_tiles(k->d.nx, k->d.ny);
+    aw.order = k->ord;
+    aw.cost = k->ord + ntile;
+    aw.done = k->ord + 4 * ntile;
+    CK(launch_order_init(aw.order, aw.cost, aw.done, ntile, s), "order init");
     ConvArgs ad = conv_args(k, n, EPI_D);
+    ad.order = k->ord + 2 * ntile;
+    ad.cost = k->ord + 3 * ntile;
+    ad.done = k->ord + 4 * ntile + 1;
+    CK(launch_order_init(ad.order, ad.cost, ad.done, ntile, s), "order init");
+    launches += 2;
     ad.in = k->lw;
     ad.hint = k->h2;
     ad.aux = k->lv;

@@ -41,6 +41,7 @@ void layout(SolveState &st, Carve &c)
     st.tmax = c.take<float>(ntm);
     st.tmax2 = c.take<float>(ntm);
     st.redo = c.take<int2>(nV);
+    st.ord = c.take<unsigned>(4 * ntm + 2);
     st.count = c.take<unsigned>(4);
     st.totals = c.take<unsigned long long>(2);
     st.partial = c.take<double>(2 * STATS_BLOCKS);
@@ -111,6 +112,13 @@ void state_bind(SolveState &st, const se2ot_kernel_desc &d, int n, const double 
     st.ad.tmax = st.tmax2;
     st.ad.tmax_w = st.tmax2;
     st.ad.tmax_ready = st.fused_max;
+    const long ntile = (long)n * d.ntheta * conv_tiles(d.nx, d.ny);
+    st.aw.order = st.ord;
+    st.aw.cost = st.ord + ntile;
+    st.aw.done = st.ord + 4 * ntile;
+    st.ad.order = st.ord + 2 * ntile;
+    st.ad.cost = st.ord + 3 * ntile;
+    st.ad.done = st.ord + 4 * ntile + 1;
 }
 
 cudaError_t state_begin(SolveState &st, cudaStream_t s)
@@ -120,6 +128,8 @@ cudaError_t state_begin(SolveState &st, cudaStream_t s)
     const size_t ntm = (size_t)st.n * st.d.ntheta * conv_tiles(st.d.nx, st.d.ny);
     if (e == cudaSuccess && st.fused_max) e = cudaMemsetAsync(st.tmax, 0, ntm * sizeof(float), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(st.totals, 0, 2 * sizeof(unsigned long long), s);
+    if (e == cudaSuccess) e = launch_order_init(st.aw.order, st.aw.cost, st.aw.done, (long)ntm, s);
+    if (e == cudaSuccess) e = launch_order_init(st.ad.order, st.ad.cost, st.ad.done, (long)ntm, s);
     return e;
 }
 
