@@ -50,6 +50,10 @@ __global__ void init_kernel(const float *mu, float2 *lmu, float2 *lv, float *h1,
 // One CTA per (spatial tile of the convolution, orientation slice): 256 threads over the tile's
 // voxels.  Besides the update it writes the inner-tile maximum of every new lv_i (hi part), which
 // the next w-convolution uses to skip orientation pairs.
+// The first UC measures' d_i and v_i are loaded up front and kept in registers (the loads of all
+// measures are in flight together); the tile maxima of all measures take one barrier.
+constexpr int UC = 4;
+
 __global__ void __launch_bounds__(256) update_kernel(float2 *lv, const float2 *ld, float2 *L, Lambdas lam, int n,
                                                      int nx, int ny, int nt, float *tmax_v)
 {
@@ -58,43 +62,77 @@ __global__ void __launch_bounds__(256) update_kernel(float2 *lv, const float2 *l
     const long plane = (long)nx * ny, V = plane * nt;
     const int t = blockIdx.z;
     const long ntiles = (long)gridDim.x * gridDim.y;
-    __shared__ float red[8];
+    __shared__ float red[64][8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     long gi[2];
     bool ok[2];
-    float2 Lg[2];
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
         const int e = threadIdx.x + 256 * k;            // TX * TY = 512 voxels, 2 per thread
         const int y = blockIdx.y * TY + e / TX, x = blockIdx.x * TX + e % TX;
         ok[k] = y < ny && x < nx;
         gi[k] = (long)t * plane + (long)y * nx + x;
+    }
+    float2 dc[UC][2], vc[UC][2];
+#pragma unroll
+    for (int i = 0; i < UC; ++i)
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const bool use = i < n && ok[k];
+            dc[i][k] = use ? ld[(long)i * V + gi[k]] : make_float2(0.f, 0.f);
+            vc[i][k] = use ? lv[(long)i * V + gi[k]] : make_float2(0.f, 0.f);
+        }
+    // L = sum_i lambda_i ld_i in measure order
+    float2 Lg[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
         float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int i = 0; i < UC; ++i)
+            if (i < n && lam.v[i].x != 0.f) acc = df_add(acc, df_mul(dc[i][k], lam.v[i]));
         if (ok[k])
-            for (int i = 0; i < n; ++i)
+            for (int i = UC; i < n; ++i)
                 if (lam.v[i].x != 0.f) acc = df_add(acc, df_mul(ld[(long)i * V + gi[k]], lam.v[i]));
         Lg[k] = acc;
         if (ok[k]) L[gi[k]] = acc;
     }
-    for (int i = 0; i < n; ++i) {
+    // lv_i += L - ld_i, and the warp maxima of the new lv_i
+    auto step = [&](int i, const float2 *d, const float2 *v) {
         float m = -INFINITY;
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
             if (!ok[k]) continue;
-            const long e = (long)i * V + gi[k];
-            const float2 nv = df_add(lv[e], df_add(Lg[k], df_neg(ld[e])));
-            lv[e] = nv;
+            const float2 nv = df_add(v[k], df_add(Lg[k], df_neg(d[k])));
+            lv[(long)i * V + gi[k]] = nv;
             m = fmaxf(m, nv.x);
         }
-        if (!tmax_v) continue;   // uniform
+        if (!tmax_v) return;   // uniform
 #pragma unroll
         for (int off = 16; off; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
-        __syncthreads();
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            for (int w = 1; w < 8; ++w) m = fmaxf(m, red[w]);
-            tmax_v[((long)i * nt + t) * ntiles + blockIdx.y * gridDim.x + blockIdx.x] = m;
+        if (lane == 0) red[i][warp] = m;
+    };
+#pragma unroll
+    for (int i = 0; i < UC; ++i) {
+        if (i >= n) break;
+        step(i, dc[i], vc[i]);
+    }
+    for (int i = UC; i < n; ++i) {
+        float2 d[2], v[2];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            d[k] = ok[k] ? ld[(long)i * V + gi[k]] : make_float2(0.f, 0.f);
+            v[k] = ok[k] ? lv[(long)i * V + gi[k]] : make_float2(0.f, 0.f);
         }
+        step(i, d, v);
+    }
+    if (!tmax_v) return;
+    __syncthreads();
+    if (threadIdx.x < n) {
+        const int i = threadIdx.x;
+        float m = red[i][0];
+#pragma unroll
+        for (int w = 1; w < 8; ++w) m = fmaxf(m, red[i][w]);
+        tmax_v[((long)i * nt + t) * ntiles + blockIdx.y * gridDim.x + blockIdx.x] = m;
     }
 }
 
