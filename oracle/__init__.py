@@ -42,6 +42,8 @@ def _lib():
                                           _P, _P, _P, _P, _P]
         lib.or_barycenter_log.argtypes = [_I, _I, _I, _I, _D, _D, _D, _D, _I, _I, _P, _P, _I,
                                           _P, _P, _P, _P, _P, _P]
+        lib.or_cost_taps.argtypes = [_I, _I, _I, _I, _D, _D, _D, _D, _P]
+        lib.or_w2_log.argtypes = [_I, _I, _I, _I, _D, _D, _D, _D, _I, _P, _P, _I, _P, _P, _P]
         _LIB = lib
     return _LIB
 
@@ -178,3 +180,27 @@ def interpolate_log(grid, mu0, mu1, t, iters, want_state=False):
     operator; the weight order is read so that t = 0 returns the first input's side)."""
     mu = np.stack([_arr(mu0), _arr(mu1)])
     return barycenter_log(grid, mu, [1.0 - t, t], iters, want_state)
+
+
+def cost_taps(grid):
+    """log(c K) per tap, c = rho_b^2 (layout of taps()): the kernel of the plan's transport cost."""
+    D = 2 * grid.r + 1
+    out = np.zeros((grid.nth, grid.nth, D, D))
+    _lib().or_cost_taps(*grid._args(), _ptr(out))
+    return out
+
+
+def w2_log(grid, mu, nu, iters, want_state=False):
+    """Entropic transport between mu and nu (Sec. 4.1, scaling iterations with both marginals
+    prescribed): cost <c, pi>, dual eps(<mu, log a> + <nu, log b>), plan mass and the first
+    marginal's violation after `iters` iterations from b = 1."""
+    mu, nu = _arr(mu), _arr(nu)
+    res = np.zeros(4)
+    la = np.zeros_like(mu) if want_state else None
+    lb = np.zeros_like(mu) if want_state else None
+    _lib().or_w2_log(*grid._args(), int(grid.periodic), _ptr(mu), _ptr(nu), int(iters), _ptr(res),
+                     _ptr(la), _ptr(lb))
+    out = {"cost": res[0], "dual": res[1], "mass": res[2], "viol": res[3]}
+    if want_state:
+        out["la"], out["lb"] = la, lb
+    return out

@@ -26,6 +26,12 @@
  *   or_barycenter_lin            -- Appendix A algorithm, literally, in the linear domain.
  *   or_barycenter_log            -- Appendix A algorithm with every scaling vector kept as
  *                                   its logarithm (same steps, same order).
+ *   or_cost_taps                 -- log(c K) with c = rho_b^2: the kernel weighted by the cost,
+ *                                   whose convolution gives the transport cost of a plan.
+ *   or_w2_log                    -- entropic transport between two measures, Sec. 4.1: the
+ *                                   scaling iterations with the marginal-constraint prox
+ *                                   (a = mu / K b, b = nu / K a), in the log domain, and the
+ *                                   cost <c, pi> of the plan pi = a K b (Eq. (L^{W_p}), p = 2).
  *
  * Grid and layout.  Voxel (ix, iy, k) of an Nx x Ny x Nth grid stands for the group element
  * (ix/Nx, iy/Ny, 2 pi k/Nth).  Arrays are f[((b*Ny + y)*Nx + x)*Nth + k] (orientation
@@ -344,4 +350,92 @@ void or_barycenter_log(int nx, int ny, int nth, int r, double w1, double w2, dou
         free(d);
     }
     free(lmu); free(lv); free(lw); free(ld); free(lkv); free(L);
+}
+
+/* Cost-weighted tap table: lkc = log(c(h^-1 g) K(h^-1 g)) = log(rho_b^2) - rho_b^2 / eps in the
+ * layout of or_taps; -inf where the cost vanishes (the identity tap). */
+void or_cost_taps(int nx, int ny, int nth, int r, double w1, double w2, double w3, double eps,
+                  double *lkc)
+{
+    int D = 2 * r + 1;
+    for (int o = 0; o < nth; ++o)
+        for (int i = 0; i < nth; ++i)
+            for (int dy = -r; dy <= r; ++dy)
+                for (int dx = -r; dx <= r; ++dx) {
+                    double g[3] = {(double)dx / nx, (double)dy / ny, 2.0 * OR_PI * o / nth};
+                    double h[3] = {0.0, 0.0, 2.0 * OR_PI * i / nth};
+                    double hi[3], u[3];
+                    or_group_inv(h, hi);
+                    or_group_mul(hi, g, u);
+                    double c = or_rho_b2(u[0], u[1], u[2], w1, w2, w3);
+                    lkc[((size_t)(o * nth + i) * D + (dy + r)) * D + (dx + r)] =
+                        (c > 0.0 ? log(c) : -INFINITY) - c / eps;
+                }
+}
+
+/* lout = log(sum_h T(h^-1 g) exp(lf(h))) for a tabulated log-kernel T (layout of or_taps). */
+static void or_conv_log_table(int nx, int ny, int nth, int r, const double *lk, int periodic,
+                              const double *lf, double *lout)
+{
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x)
+            for (int o = 0; o < nth; ++o)
+                lout[((size_t)y * nx + x) * nth + o] = or_conv_log_one(nx, ny, nth, r, lk, periodic, lf, y, x, o);
+}
+
+/* Entropic transport between mu and nu (Sec. 4.1).  The scaling iterations with both marginals
+ * prescribed, started from b = 1, `iters` times:
+ *   log a = log mu - log(K b),   log b = log nu - log(K a)
+ * (K symmetric, so K^T = K).  Then, for the plan pi(g, h) = a(g) K(h^-1 g) b(h):
+ *   res[0] = <c, pi> = sum_g a(g) (cK * b)(g)          transport cost, c = rho_b^2
+ *   res[1] = eps (<mu, log a> + <nu, log b>)            dual objective (entries with mu or nu = 0 skipped)
+ *   res[2] = sum pi = sum_g a(g) (K * b)(g)             plan mass
+ *   res[3] = ||a (K * b) - mu||_1 / ||mu||_1            first-marginal violation (the second
+ *                                                       holds exactly after the b-step)
+ * la_out / lb_out (may be NULL) receive log a and log b. */
+void or_w2_log(int nx, int ny, int nth, int r, double w1, double w2, double w3, double eps,
+               int periodic, const double *mu, const double *nu, int iters, double *res,
+               double *la_out, double *lb_out)
+{
+    int D = 2 * r + 1;
+    size_t V = (size_t)nx * ny * nth, ntap = (size_t)nth * nth * D * D;
+    double *lk = (double *)malloc(sizeof(double) * ntap);
+    double *lkc = (double *)malloc(sizeof(double) * ntap);
+    or_taps(nx, ny, nth, r, w1, w2, w3, eps, lk);
+    or_cost_taps(nx, ny, nth, r, w1, w2, w3, eps, lkc);
+    double *la = (double *)malloc(sizeof(double) * V);
+    double *lb = (double *)malloc(sizeof(double) * V);
+    double *t = (double *)malloc(sizeof(double) * V);
+    for (size_t g = 0; g < V; ++g) {
+        la[g] = 0.0;
+        lb[g] = 0.0;
+    }
+    for (int j = 0; j < iters; ++j) {
+        or_conv_log_table(nx, ny, nth, r, lk, periodic, lb, t);
+        for (size_t g = 0; g < V; ++g) la[g] = log(mu[g]) - t[g];
+        or_conv_log_table(nx, ny, nth, r, lk, periodic, la, t);
+        for (size_t g = 0; g < V; ++g) lb[g] = log(nu[g]) - t[g];
+    }
+    double mass = 0.0, dev = 0.0, msum = 0.0, cost = 0.0, dual = 0.0;
+    or_conv_log_table(nx, ny, nth, r, lk, periodic, lb, t);
+    for (size_t g = 0; g < V; ++g) {
+        double m = exp(la[g] + t[g]);
+        mass += m;
+        dev += fabs(m - mu[g]);
+        msum += mu[g];
+    }
+    or_conv_log_table(nx, ny, nth, r, lkc, periodic, lb, t);
+    for (size_t g = 0; g < V; ++g) {
+        cost += exp(la[g] + t[g]);
+        if (mu[g] > 0.0) dual += mu[g] * la[g];
+        if (nu[g] > 0.0) dual += nu[g] * lb[g];
+    }
+    res[0] = cost;
+    res[1] = eps * dual;
+    res[2] = mass;
+    res[3] = dev / msum;
+    if (la_out) memcpy(la_out, la, sizeof(double) * V);
+    if (lb_out) memcpy(lb_out, lb, sizeof(double) * V);
+    free(lk); free(lkc); free(la); free(lb); free(t);
 }

@@ -327,3 +327,80 @@ def test_pointwise_log_conv_is_the_full_one_at_those_points():
     full = oracle.conv_log(g, lf).reshape(-1)
     idx = RNG.choice(full.size, 60, replace=False)
     assert np.array_equal(oracle.conv_log_points(g, lf, idx), full[idx])
+
+
+# ------------------------------------------------- two-marginal transport (Sec. 4.1)
+def _w2_inputs(g, seed):
+    rng = np.random.default_rng(seed)
+    mu = rng.uniform(0.05, 1.0, size=g.shape)
+    nu = rng.uniform(0.05, 1.0, size=g.shape)
+    return mu / mu.sum(), nu / nu.sum()
+
+
+@pytest.mark.parametrize("periodic", [False, True])
+def test_w2_matches_dense_sinkhorn(periodic):
+    """The log-domain scaling iterations against plain Sinkhorn on the explicit kernel matrix
+    (group law from 3x3 matrices), and the plan's cost against the dense cost matrix
+    c = rho_b^2 of every coupled pair."""
+    g = oracle.Grid(5, 6, 4, 2, W, 0.05, periodic)
+    LK = refmath.dense_log_kernel(g.nx, g.ny, g.nth, g.r, _rho2, g.eps, periodic)
+    K = np.exp(LK)
+    C = np.where(np.isfinite(LK), -g.eps * LK, 0.0)
+    mu, nu = _w2_inputs(g, 5)
+    m, n_ = mu.reshape(-1), nu.reshape(-1)
+    b = np.ones(g.V)
+    for _ in range(30):
+        a = m / (K @ b)
+        b = n_ / (K.T @ a)
+    P = a[:, None] * K * b[None, :]
+    got = oracle.w2_log(g, mu, nu, 30)
+    np.testing.assert_allclose(got["cost"], (P * C).sum(), rtol=1e-11)
+    np.testing.assert_allclose(got["dual"], g.eps * (m @ np.log(a) + n_ @ np.log(b)), rtol=1e-11)
+    np.testing.assert_allclose(got["mass"], P.sum(), rtol=1e-12)
+    np.testing.assert_allclose(got["viol"], np.abs(P.sum(axis=1) - m).sum() / m.sum(), rtol=1e-8)
+
+
+def test_w2_uniform_closed_form():
+    """mu = nu = uniform on a periodic square grid with 4 orientations: K 1 = kappa (the sum of
+    the taps of any output orientation) everywhere, so a = mu / kappa and b = 1 after one
+    step; the cost is the kernel's mean cost and the dual eps log(1 / (V kappa))."""
+    g = oracle.Grid(8, 8, 4, 2, W, 0.05, True)
+    lk = oracle.taps(g)
+    K0 = np.exp(lk[0])
+    kappa, kappa_c = K0.sum(), (K0 * (-g.eps * lk[0])).sum()
+    np.testing.assert_allclose(np.exp(lk).sum(axis=(1, 2, 3)), kappa, rtol=1e-13)
+    u = np.full(g.shape, 1.0 / g.V)
+    for iters in (1, 5):
+        got = oracle.w2_log(g, u, u, iters)
+        np.testing.assert_allclose(got["cost"], kappa_c / kappa, rtol=1e-12)
+        np.testing.assert_allclose(got["dual"], g.eps * np.log(1.0 / (g.V * kappa)), rtol=1e-12)
+        assert abs(got["mass"] - 1.0) < 1e-13 and got["viol"] < 1e-13
+
+
+def test_w2_invariant_under_left_translation():
+    """W((L_g)# mu, (L_g)# nu) = W(mu, nu) (Lemma on invariance, Corollary for the entropic
+    scheme): 90-degree rotation with the orientation shift, and an integer translation."""
+    g = oracle.Grid(8, 8, 8, 2, W, 0.05, True)
+    mu, nu = _w2_inputs(g, 9)
+    base = oracle.w2_log(g, mu, nu, 20)
+    for T in (refmath.rot90, lambda f: np.roll(f, (3, -2), axis=(0, 1))):
+        got = oracle.w2_log(g, T(mu), T(nu), 20)
+        for key in ("cost", "dual", "mass", "viol"):
+            np.testing.assert_allclose(got[key], base[key], rtol=1e-11)
+
+
+def test_w2_converged_plan_is_symmetric_and_has_both_marginals():
+    """At convergence the explicit plan a K b has row sums mu and column sums nu, and swapping
+    the measures gives the same cost and dual (K is symmetric)."""
+    g = oracle.Grid(5, 5, 4, 2, W, 0.2)
+    K = _dense_K(g)
+    mu, nu = _w2_inputs(g, 12)
+    st = oracle.w2_log(g, mu, nu, 300, want_state=True)
+    assert st["viol"] < 1e-12
+    a, b = np.exp(st["la"]).reshape(-1), np.exp(st["lb"]).reshape(-1)
+    P = a[:, None] * K * b[None, :]
+    np.testing.assert_allclose(P.sum(axis=1), mu.reshape(-1), rtol=1e-10)
+    np.testing.assert_allclose(P.sum(axis=0), nu.reshape(-1), rtol=1e-10)
+    rev = oracle.w2_log(g, nu, mu, 300)
+    np.testing.assert_allclose(rev["cost"], st["cost"], rtol=1e-10)
+    np.testing.assert_allclose(rev["dual"], st["dual"], rtol=1e-10)
