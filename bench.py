@@ -49,6 +49,9 @@ def inputs(problem=0):
                                   problem=problem).astype(np.float32)
 
 
+W2_WORKLOAD = ("entropic two-marginal transport (Sec. 4.1) between the first 2 of those measures, 128x128x16 "
+               "SE(2) grid, kernel 21x21x16 (r=10), w=(1,3,0.5), eps=1e-4, 500 Sinkhorn iterations, then the "
+               "plan cost <rho_b^2, pi> through the cost-weighted kernel, FP32 log-domain path")
 # Other workloads (parity cases and scale points; not the headline line): `--config large` is the
 # 512^2 x 32 single solve, `--config batched` the 64 uneven interpolations.
 LARGE = dict(nx=512, ny=512, nt=32, r=15, eps=2e-5, n=3, iters=1000,
@@ -325,6 +328,24 @@ def run_gpu(args):
         def solve(e2e=False):
             _, st, _ = se2ot.se2ot_interpolate_batched(descs, mu0, mu1, ts, se2ot.solve_opts(iters), outs)
             return st[0]
+    elif args.config == "w2":
+        nx, ny, nt, r, eps, n = NX, NY, NT, R, EPS, 2
+        mu_h = torch.from_numpy(np.ascontiguousarray(inputs(problem=rank)[:2]))
+        iters = args.iters or ITERS
+        workload = W2_WORKLOAD
+        vox = nx * ny * nt
+        cfg = {"grid": [nx, ny, nt], "radius": r, "measures": 2, "iterations": iters, "eps": eps, "w": list(W)}
+        k = se2ot.se2ot_kernel_build(se2ot.make_desc(nx, ny, nt, r, W, eps))
+        mu = mu_h.to(device)
+        mu_pin = mu_h.pin_memory()
+        timed_conv = False
+
+        def solve(e2e=False):
+            src = mu_pin if e2e else mu
+            res, _ = se2ot.se2ot_w2(k, src[0], src[1], se2ot.solve_opts(iters))
+            return {"conv_ms": 0.0, "conv_launches": 0, "kernel_launches": res["kernel_launches"],
+                    "redo_outputs": res["redo_outputs"], "evaluated_terms": 0, "mass": res["mass"],
+                    "viol": res["viol"], "cost": res["cost"], "dual": res["dual"]}
     else:
         if args.config == "large":
             nx, ny, nt, r, eps, n = (LARGE[k] for k in ("nx", "ny", "nt", "r", "eps", "n"))
@@ -408,7 +429,11 @@ def run_gpu(args):
             "gpu_launches": int(launches),
             "solve": {"mass": mass, "viol": viol, "redo_outputs_timed": int(redo)},
         }
-        if args.config == "batched":
+        if args.config == "w2":
+            result["solve"].update({"cost": st["cost"], "dual": st["dual"]})
+            result["e2e"] = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(2 * vox * 4),
+                             "d2h_bytes_per_step": 40}
+        elif args.config == "batched":
             result["e2e"] = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
                              "note": "device-resident batch (the batched entry point takes device buffers)"}
         else:
@@ -491,7 +516,7 @@ def main(argv=None):
                     help="Sinkhorn iterations per solve (profiling runs only; default: the workload's)")
     ap.add_argument("--rate", type=float, default=0.0, help="serve: Poisson arrival rate (req/s)")
     ap.add_argument("--requests", type=int, default=0, help="serve: number of requests")
-    ap.add_argument("--config", default="barycenter", choices=["barycenter", "large", "batched", "serve"],
+    ap.add_argument("--config", default="barycenter", choices=["barycenter", "large", "batched", "serve", "w2"],
                     help="workload: the 128^2x16 barycenter (default, the headline), the 512^2x32 "
                          "large solve, or the 64-problem uneven batch")
     args = ap.parse_args(argv)

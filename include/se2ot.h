@@ -171,6 +171,34 @@ SE2OT_API se2ot_status se2ot_interpolate(se2ot_kernel k, const float *mu0, const
                                const se2ot_solve_opts *opts, float *out, se2ot_stats *stats,
                                void *stream);
 
+/* Entropic optimal transport between two measures (Sec. 4.1): the scaling iterations with both
+ * marginals prescribed (prox of the marginal constraint, Eq. (F_i) with n = 2),
+ *   a = mu / (K * b),   b = nu / (K * a),          b = 1 initially,
+ * one iteration being both steps, then the plan pi(g, h) = a(g) K(h^-1 g) b(h) and its cost
+ * for c = rho_b^2 (Eq. (L^{W_p}) with p = 2, the Gibbs kernel being exp(-c / eps)):
+ *   cost  = <c, pi> = sum_g a(g) ((cK) * b)(g)     (the entropic estimate of W_2^2)
+ *   dual  = eps (<mu, log a> + <nu, log b>)         (natural log; voxels with zero mass skipped)
+ *   mass  = sum pi
+ *   viol  = ||a (K * b) - mu||_1 / ||mu||_1         (the nu-marginal holds exactly after each b-step)
+ * all reduced in FP64 in a fixed order.  mu, nu: V floats each, caller layout [y][x][theta],
+ * nonnegative and finite, host or device memory; their masses need not be 1 but must agree to
+ * 1e-6 relative.  opts as in se2ot_barycenter (tol_viol > 0 with check_every > 0 stops once viol
+ * <= tol_viol; each check costs two convolutions).  The first call on a kernel handle builds the
+ * cost-weighted tap table (same size as the kernel's); workspace is the handle's, as for a
+ * 2-measure barycenter.  The call synchronises the stream before returning.
+ * Returns EINVAL for invalid arguments, ENONFINITE for a non-finite result, ENOTCONV if tol_viol
+ * was not reached (res is still written). */
+typedef struct {
+    int iters;
+    double cost, dual, mass, viol;
+    double ms;                   /* wall time of the call */
+    long long kernel_launches;
+    long long redo_outputs;
+} se2ot_w2_result;
+
+SE2OT_API se2ot_status se2ot_w2(se2ot_kernel k, const float *mu, const float *nu, const se2ot_solve_opts *opts,
+                                se2ot_w2_result *res, void *stream);
+
 /* nprob independent interpolations Phi_t(mu0[p], mu1[p]) (weights (1 - t[p], t[p])) of uneven grid
  * sizes, radii, metrics and regularisations, iterated in lockstep for opts->max_iters Sinkhorn
  * iterations (Appendix A with n = 2 for every problem).  descs[p]: each problem's grid and kernel

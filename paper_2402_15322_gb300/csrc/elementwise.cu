@@ -196,6 +196,40 @@ __global__ void __launch_bounds__(RT) stats_final_kernel(const double *partial, 
 
 }  // namespace
 
+__global__ void __launch_bounds__(RT) w2_stats_partial_kernel(const float2 *la, const float2 *lb, const float2 *lm,
+                                                              const float2 *lc, const float2 *lmu, const float2 *lnu,
+                                                              long V, double *partial)
+{
+    __shared__ double sh[RT];
+    double cost = 0.0, dual = 0.0, mass = 0.0, dev = 0.0, msum = 0.0;
+    for (long g = blockIdx.x * (long)RT + threadIdx.x; g < V; g += (long)STATS_BLOCKS * RT) {
+        const double mu = exp2(df_to_double(lmu[g])), nu = exp2(df_to_double(lnu[g]));
+        const double m = exp2(df_to_double(lm[g]));
+        cost += exp2(df_to_double(lc[g]));
+        if (mu > 0.0) dual += mu * df_to_double(la[g]);
+        if (nu > 0.0) dual += nu * df_to_double(lb[g]);
+        mass += m;
+        dev += fabs(m - mu);
+        msum += mu;
+    }
+    const double v[5] = {cost, dual, mass, dev, msum};
+    for (int q = 0; q < 5; ++q) {
+        const double t = block_sum(v[q], sh);
+        if (threadIdx.x == 0) partial[q * STATS_BLOCKS + blockIdx.x] = t;
+    }
+}
+
+__global__ void w2_stats_final_kernel(const double *partial, double *scal)
+{
+    __shared__ double sh[RT];
+    for (int q = 0; q < 5; ++q) {
+        double v = 0.0;
+        for (int b = threadIdx.x; b < STATS_BLOCKS; b += RT) v += partial[q * STATS_BLOCKS + b];
+        const double t = block_sum(v, sh);
+        if (threadIdx.x == 0) scal[q] = t;
+    }
+}
+
 cudaError_t launch_init(const float *mu, float2 *lmu, float2 *lv, float *h1, float *h2, int n, int nx, int ny,
                         int nt, cudaStream_t s)
 {
@@ -216,6 +250,15 @@ cudaError_t launch_finalize(const float2 *L, float *bary, int nx, int ny, int nt
 {
     const long V = (long)nx * ny * nt;
     finalize_kernel<<<grid_for(V), 256, 0, s>>>(L, bary, V, nx, ny, nt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_w2_stats(const float2 *la, const float2 *lb, const float2 *lm, const float2 *lc,
+                            const float2 *lmu, const float2 *lnu, long V, double *partial, double *scal,
+                            cudaStream_t s)
+{
+    w2_stats_partial_kernel<<<STATS_BLOCKS, RT, 0, s>>>(la, lb, lm, lc, lmu, lnu, V, partial);
+    w2_stats_final_kernel<<<1, RT, 0, s>>>(partial, scal);
     return cudaGetLastError();
 }
 

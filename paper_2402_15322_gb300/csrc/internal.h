@@ -61,7 +61,10 @@ struct Taps {
 };
 
 // Launchers (conv.cu / taps.cu).
-cudaError_t build_taps(const se2ot_kernel_desc &d, Taps &t, cudaStream_t s);
+// cost = false: the Gibbs kernel K; true: the cost-weighted kernel (c / C0) K, c = rho_b^2, with
+// *cost_scale = C0 (a power of two >= every rho_b^2 of the window, so that every tap is <= 0)
+cudaError_t build_taps(const se2ot_kernel_desc &d, Taps &t, cudaStream_t s, bool cost = false,
+                       double *cost_scale = nullptr);
 // tile-max pre-pass + summing convolution (needs a.hint holding a shift for every output)
 cudaError_t launch_conv(const ConvArgs &a, cudaStream_t s);
 // same tiling, writing the largest term of every output to a.hint (the shift of a later launch)
@@ -98,5 +101,13 @@ cudaError_t launch_finalize(const float2 *L, float *bary, int nx, int ny, int nt
 constexpr int STATS_BLOCKS = 256;
 cudaError_t launch_stats(const float2 *L, const float2 *ld, const Lambdas &lam, int n, long V, double *partial,
                          double *scal, cudaStream_t s);
+// Two-marginal transport (slice-major base-2 logarithms, V voxels): lm = log2(a K b),
+// lc = log2(a cK b), lmu / lnu the marginals.  FP64, fixed order:
+//   scal[0] = sum 2^lc (transport cost), scal[1] = sum 2^lmu la + sum 2^lnu lb (log2 units, zero
+//   masses skipped), scal[2] = sum 2^lm (plan mass), scal[3] = sum |2^lm - 2^lmu|, scal[4] = sum 2^lmu.
+// partial holds 5 * STATS_BLOCKS doubles.
+cudaError_t launch_w2_stats(const float2 *la, const float2 *lb, const float2 *lm, const float2 *lc,
+                            const float2 *lmu, const float2 *lnu, long V, double *partial, double *scal,
+                            cudaStream_t s);
 
 }  // namespace se2ot

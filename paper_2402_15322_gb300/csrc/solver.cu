@@ -140,6 +140,9 @@ struct se2ot_kernel_s {
     size_t c_tmax = 0, c_tmax2 = 0;
     unsigned *ord = nullptr;                   // tile launch orders and costs of the two convolutions, 2 counters
     size_t c_ord = 0;
+    Taps ctaps;                                // cost-weighted taps (se2ot_w2), built on first use
+    double cost_scale = 1.0;                   // their scale C0
+    double *w2p = nullptr;                     // se2ot_w2 reductions: 5 * STATS_BLOCKS partials + 5 sums
     std::vector<cudaEvent_t> ev;
 };
 
@@ -277,7 +280,8 @@ se2ot_status se2ot_kernel_destroy(se2ot_kernel k)
     if (!k) return SE2OT_OK;
     cudaDeviceSynchronize();
     void *ptrs[] = {k->taps.ltheta, k->taps.ls, k->taps.ls_lo, k->taps.lsrow, k->tmax, k->tmax2, k->lmu, k->lv, k->lw, k->ld, k->L, k->lf, k->h1, k->h2, k->hint_ws,
-                    k->mu_stage, k->bary_stage, k->redo, k->counters, k->redo_total, k->partial, k->scal, k->ord};
+                    k->mu_stage, k->bary_stage, k->redo, k->counters, k->redo_total, k->partial, k->scal, k->ord, k->ctaps.ltheta, k->ctaps.ls,
+                    k->ctaps.ls_lo, k->ctaps.lsrow, k->w2p};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : k->ev) cudaEventDestroy(e);
@@ -527,6 +531,145 @@ se2ot_status se2ot_state_export(se2ot_kernel k, int n, double *log_v, double *lo
     if (log_d) export_kernel<<<grid_for(nV), 256, 0, s>>>(k->ld, log_d, nV, k->d.nx, k->d.ny, k->d.ntheta);
     if (log_mu) export_kernel<<<grid_for(V), 256, 0, s>>>(k->L, log_mu, V, k->d.nx, k->d.ny, k->d.ntheta);
     CK(cudaGetLastError(), "export launch");
+    return SE2OT_OK;
+}
+
+se2ot_status se2ot_w2(se2ot_kernel k, const float *mu, const float *nu, const se2ot_solve_opts *opts,
+                      se2ot_w2_result *res, void *stream)
+{
+    const auto wall0 = std::chrono::steady_clock::now();
+    if (!k || !mu || !nu || !res) return fail(SE2OT_EINVAL, "NULL argument");
+    se2ot_solve_opts o = {100, 0, 0.0, SE2OT_FP32, 0};
+    if (opts) o = *opts;
+    if (o.max_iters < 1) return fail(SE2OT_EINVAL, "max_iters=%d < 1", o.max_iters);
+    if (o.precision != SE2OT_FP32) return fail(SE2OT_EINVAL, "precision=%d unsupported", o.precision);
+    if (o.tol_viol < 0 || !std::isfinite(o.tol_viol)) return fail(SE2OT_EINVAL, "tol_viol invalid");
+    if (2.0 * k->V >= 2147483647.0) return fail(SE2OT_EINVAL, "V too large");
+    cudaStream_t s = (cudaStream_t)stream;
+    const long V = k->V;
+    se2ot_status st = ensure_solver_ws(k, 2);
+    if (st != SE2OT_OK) return st;
+    long long launches = 0;
+    if (!k->ctaps.ls) {
+        const int D = 2 * k->d.radius + 1;
+        const size_t npair = (size_t)k->d.ntheta * k->d.ntheta;
+        CK(cudaMalloc((void **)&k->ctaps.ltheta, npair * sizeof(float2)), "cudaMalloc(cost taps)");
+        CK(cudaMalloc((void **)&k->ctaps.ls, npair * D * D * sizeof(float)), "cudaMalloc(cost taps)");
+        CK(cudaMalloc((void **)&k->ctaps.ls_lo, npair * D * D * sizeof(float)), "cudaMalloc(cost taps)");
+        CK(cudaMalloc((void **)&k->ctaps.lsrow, npair * D * sizeof(float)), "cudaMalloc(cost taps)");
+        CK(build_taps(k->d, k->ctaps, s, true, &k->cost_scale), "cost tap build");
+        launches += 2;
+    }
+    if (!k->w2p) CK(cudaMalloc((void **)&k->w2p, (5 * STATS_BLOCKS + 5) * sizeof(double)), "cudaMalloc(w2 sums)");
+    CK(grow(k->hint_ws, k->c_hint_ws, (size_t)V), "cudaMalloc(hint)");
+
+    // mu and nu into the staging buffer as one [2][V] array: log2 mu, log2 nu, a = b = 1
+    CK(grow(k->mu_stage, k->c_mus, (size_t)2 * V), "cudaMalloc(mu stage)");
+    CK(cudaMemcpyAsync(k->mu_stage, mu, (size_t)V * sizeof(float),
+                       is_device_ptr(mu) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s), "cudaMemcpyAsync(mu)");
+    CK(cudaMemcpyAsync(k->mu_stage + V, nu, (size_t)V * sizeof(float),
+                       is_device_ptr(nu) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s), "cudaMemcpyAsync(nu)");
+    CK(launch_init(k->mu_stage, k->lmu, k->lv, k->h1, k->h2, 2, k->d.nx, k->d.ny, k->d.ntheta, s), "init launch");
+    ++launches;
+    const bool fused_max = k->d.boundary == SE2OT_BOUNDARY_ZERO;
+    const long ntile = (long)k->d.ntheta * conv_tiles(k->d.nx, k->d.ny);
+    if (fused_max) CK(cudaMemsetAsync(k->tmax, 0, ntile * sizeof(float), s), "cudaMemsetAsync(tmax)");
+    CK(cudaMemsetAsync(k->redo_total, 0, 2 * sizeof(unsigned long long), s), "cudaMemsetAsync");
+
+    float2 *lb = k->lv, *la = k->lv + V, *lm = k->lw, *lc = k->lw + V;
+    // a = mu / (K * b): hint log2 K b (0 for b = 1)
+    ConvArgs A = conv_args(k, 1, EPI_W);
+    A.in = lb;
+    A.hint = k->h1;
+    A.aux = k->lmu;
+    A.out2 = la;
+    A.tmax_ready = fused_max;
+    A.tmax_out = fused_max ? k->tmax2 : nullptr;
+    A.order = k->ord;
+    A.cost = k->ord + ntile;
+    A.done = k->ord + 4 * ntile;
+    // b = nu / (K * a): hint log2 K a (~ log2 mu at the start)
+    ConvArgs B = conv_args(k, 1, EPI_W);
+    B.in = la;
+    B.hint = k->h2;
+    B.aux = k->lmu + V;
+    B.out2 = lb;
+    B.tmax = k->tmax2;
+    B.tmax_w = k->tmax2;
+    B.tmax_ready = fused_max;
+    B.tmax_out = fused_max ? k->tmax : nullptr;
+    B.order = k->ord + 2 * ntile;
+    B.cost = k->ord + 3 * ntile;
+    B.done = k->ord + 4 * ntile + 1;
+    CK(launch_order_init(A.order, A.cost, A.done, ntile, s), "order init");
+    CK(launch_order_init(B.order, B.cost, B.done, ntile, s), "order init");
+    launches += 2;
+    // statistics: lm = log2(a (K * b)), lc = log2(a ((c / C0) K * b)) with its own max-pass shift
+    ConvArgs M = conv_args(k, 1, EPI_D);
+    M.in = lb;
+    M.hint = k->h1;
+    M.aux = la;
+    M.out2 = lm;
+    M.tmax_ready = fused_max;
+    ConvArgs C = M;
+    C.ltheta = k->ctaps.ltheta;
+    C.ls = k->ctaps.ls;
+    C.ls_lo = k->ctaps.ls_lo;
+    C.lsrow = k->ctaps.lsrow;
+    C.hint = k->hint_ws;
+    C.out2 = lc;
+    double h[5];
+    auto reduce = [&](bool with_cost) -> se2ot_status {
+        se2ot_status r = run_conv(k, M, s, &launches);
+        if (r != SE2OT_OK) return r;
+        if (with_cost) {
+            CK(launch_conv_max(C, s), "conv max-pass launch");
+            ++launches;
+            r = run_conv(k, C, s, &launches);
+            if (r != SE2OT_OK) return r;
+        }
+        CK(launch_w2_stats(la, lb, lm, with_cost ? lc : lm, k->lmu, k->lmu + V, V, k->w2p, k->w2p + 5 * STATS_BLOCKS, s),
+           "w2 stats launch");
+        launches += 2;
+        CK(cudaMemcpyAsync(h, k->w2p + 5 * STATS_BLOCKS, sizeof h, cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync(stats)");
+        CK(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+        return SE2OT_OK;
+    };
+
+    int it = 0;
+    bool converged = false;
+    while (it < o.max_iters) {
+        st = run_conv(k, A, s, &launches);
+        if (st == SE2OT_OK) st = run_conv(k, B, s, &launches);
+        if (st != SE2OT_OK) return st;
+        ++it;
+        if (o.tol_viol > 0 && o.check_every > 0 && it % o.check_every == 0 && it < o.max_iters) {
+            st = reduce(false);
+            if (st != SE2OT_OK) return st;
+            if (h[3] / h[4] <= o.tol_viol) {
+                converged = true;
+                break;
+            }
+        }
+    }
+    st = reduce(true);
+    if (st != SE2OT_OK) return st;
+    unsigned long long counts[2] = {0, 0};
+    CK(cudaMemcpy(counts, k->redo_total, sizeof counts, cudaMemcpyDeviceToHost), "cudaMemcpy(counters)");
+    k->last_n = 0;   // the workspace no longer holds a barycenter solve
+    std::memset(res, 0, sizeof *res);
+    res->iters = it;
+    res->cost = h[0] * k->cost_scale;
+    res->dual = k->d.eps * 0.69314718055994530942 * h[1];
+    res->mass = h[2];
+    res->viol = h[3] / h[4];
+    res->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - wall0).count();
+    res->kernel_launches = launches;
+    res->redo_outputs = (long long)counts[0];
+    if (!std::isfinite(res->cost) || !std::isfinite(res->mass) || !std::isfinite(res->viol) || !std::isfinite(res->dual))
+        return fail(SE2OT_ENONFINITE, "non-finite result (cost=%g, mass=%g, viol=%g)", res->cost, res->mass, res->viol);
+    if (o.tol_viol > 0 && !converged && !(res->viol <= o.tol_viol))
+        return fail(SE2OT_ENOTCONV, "viol=%g > tol=%g after %d iterations", res->viol, o.tol_viol, it);
     return SE2OT_OK;
 }
 

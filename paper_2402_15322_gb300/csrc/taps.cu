@@ -12,6 +12,15 @@
 // with ls <= 0 and ls = 0 at the zero offset; lsrow[o][i][dy] is the largest ls of each row.
 // A theta difference of exactly pi is taken as -pi (small-angle convention); rho_b is the same
 // for +pi and -pi, so the choice does not matter.
+//
+// Cost-weighted table (the kernel c K with c = rho_b^2, whose convolution gives a plan's
+// transport cost, Eq. (L^{W_p}) with p = 2): the same ltheta, and log2(rho_b^2 / C0) added to
+// every spatial tap (-inf at the identity, where the cost vanishes).  C0 is a power of two no
+// smaller than any rho_b^2 of the window, so the taps stay <= 0 as the convolution's skipping
+// assumes; the caller multiplies its sums by C0 (exactly).
+#include <algorithm>
+#include <cmath>
+
 #include "dfloat.cuh"
 #include "internal.h"
 
@@ -29,8 +38,8 @@ __device__ double dtheta_pi(int o, int i, int nt)
     return 2.0 * k / nt;
 }
 
-__global__ void spatial_taps_kernel(int nx, int ny, int nt, int r, double w1, double w2, double eps,
-                                    float *ls, float *ls_lo)
+__global__ void spatial_taps_kernel(int nx, int ny, int nt, int r, double w1, double w2, double w3, double eps,
+                                    bool cost, int log2_c0, float *ls, float *ls_lo)
 {
     const int D = 2 * r + 1;
     const long total = (long)nt * nt * D * D;
@@ -53,10 +62,15 @@ __global__ void spatial_taps_kernel(int nx, int ny, int nt, int r, double w1, do
         sincospi(0.5 * dtheta_pi(o, i, nt), &sh, &ch);
         const double b1 = ux * ch + uy * sh;
         const double b2 = -ux * sh + uy * ch;
-        const double v = -((w1 * b1) * (w1 * b1) + (w2 * b2) * (w2 * b2)) / eps * LOG2E;
+        const double sp = (w1 * b1) * (w1 * b1) + (w2 * b2) * (w2 * b2);
+        double v = -sp / eps * LOG2E;
+        if (cost) {
+            const double b3 = dtheta_pi(o, i, nt) * 3.14159265358979323846;
+            v += log2(sp + (w3 * b3) * (w3 * b3)) - log2_c0;   // -inf at the identity
+        }
         const float hi = (float)v;
         ls[idx] = hi;
-        ls_lo[idx] = (float)(v - (double)hi);
+        ls_lo[idx] = isfinite(hi) ? (float)(v - (double)hi) : 0.f;
     }
 }
 
@@ -78,14 +92,19 @@ __global__ void theta_taps_kernel(int nt, int r, double w3, double eps, const fl
 
 }  // namespace
 
-cudaError_t build_taps(const se2ot_kernel_desc &d, Taps &t, cudaStream_t s)
+cudaError_t build_taps(const se2ot_kernel_desc &d, Taps &t, cudaStream_t s, bool cost, double *cost_scale)
 {
+    // |(b1, b2)| = |(u_x, u_y)| <= r sqrt(1/nx^2 + 1/ny^2) and |b3| <= pi bound rho_b^2 on the window
+    const double ux = (double)d.radius / d.nx, uy = (double)d.radius / d.ny, wm = std::max(d.w1, d.w2);
+    const double bound = wm * wm * (ux * ux + uy * uy) + (d.w3 * 3.14159265358979323846) * (d.w3 * 3.14159265358979323846);
+    const int log2_c0 = bound > 0.0 ? (int)std::ceil(std::log2(bound)) : 0;
+    if (cost_scale) *cost_scale = std::ldexp(1.0, log2_c0);
     const int D = 2 * d.radius + 1;
     const long total = (long)d.ntheta * d.ntheta * D * D;
     int blocks = (int)((total + 255) / 256);
     if (blocks > 4096) blocks = 4096;
-    spatial_taps_kernel<<<blocks, 256, 0, s>>>(d.nx, d.ny, d.ntheta, d.radius, d.w1, d.w2, d.eps, t.ls,
-                                               t.ls_lo);
+    spatial_taps_kernel<<<blocks, 256, 0, s>>>(d.nx, d.ny, d.ntheta, d.radius, d.w1, d.w2, d.w3, d.eps, cost,
+                                               log2_c0, t.ls, t.ls_lo);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int pairs = d.ntheta * d.ntheta;

@@ -51,6 +51,15 @@ class se2ot_stats(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class se2ot_w2_result(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("cost", ctypes.c_double), ("dual", ctypes.c_double),
+                ("mass", ctypes.c_double), ("viol", ctypes.c_double), ("ms", ctypes.c_double),
+                ("kernel_launches", ctypes.c_longlong), ("redo_outputs", ctypes.c_longlong)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 class SE2OTError(RuntimeError):
     def __init__(self, status, message):
         super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), message))
@@ -80,6 +89,7 @@ def lib():
     L.se2ot_interpolate.argtypes = [vp, vp, vp, d, ctypes.POINTER(se2ot_solve_opts), vp,
                                     ctypes.POINTER(se2ot_stats), vp]
     L.se2ot_state_export.argtypes = [vp, i, vp, vp, vp, vp]
+    L.se2ot_w2.argtypes = [vp, vp, vp, ctypes.POINTER(se2ot_solve_opts), ctypes.POINTER(se2ot_w2_result), vp]
     L.se2ot_interpolate_batched.argtypes = [i, ctypes.POINTER(se2ot_kernel_desc), ctypes.POINTER(vp),
                                             ctypes.POINTER(vp), ctypes.POINTER(d),
                                             ctypes.POINTER(se2ot_solve_opts), ctypes.POINTER(vp),
@@ -235,6 +245,18 @@ def se2ot_state_export(kernel, n, device="cuda", stream=None):
     _check(lib().se2ot_state_export(kernel.handle, int(n), _ptr(lv, torch.float64), _ptr(ld, torch.float64),
                                     _ptr(lmu, torch.float64), _stream(stream)))
     return lv, ld, lmu
+
+
+def se2ot_w2(kernel, mu, nu, opts=None, stream=None, raise_on_error=True):
+    """Entropic transport between mu and nu (Sec. 4.1): returns (result dict with cost <c, pi>,
+    dual, plan mass, first-marginal violation, iterations; status)."""
+    res = se2ot_w2_result()
+    status = lib().se2ot_w2(kernel.handle, _ptr(mu, torch.float32), _ptr(nu, torch.float32),
+                            ctypes.byref(opts if opts is not None else solve_opts()), ctypes.byref(res),
+                            _stream(stream))
+    if raise_on_error:
+        _check(status)
+    return res.as_dict(), status
 
 
 def se2ot_interpolate(kernel, mu0, mu1, t, opts=None, out=None, stream=None, raise_on_error=True):
