@@ -30,20 +30,22 @@ def _lib():
         lib.or_group_inv.argtypes = [_P, _P]
         lib.or_rho_b2.argtypes = [_D] * 6
         lib.or_rho_b2.restype = _D
-        lib.or_log_kernel.argtypes = [_P, _P, _D, _D, _D, _D]
+        lib.or_rho_c2.argtypes = [_D] * 6
+        lib.or_rho_c2.restype = _D
+        lib.or_log_kernel.argtypes = [_P, _P, _D, _D, _D, _D, _I]
         lib.or_log_kernel.restype = _D
-        lib.or_taps.argtypes = [_I, _I, _I, _I, _D, _D, _D, _D, _P]
-        conv = [_I, _I, _I, _I, _D, _D, _D, _D, _I, _I, _P, _P]
+        lib.or_taps.argtypes = [_I, _I, _I, _I, _D, _D, _D, _D, _I, _P]
+        conv = [_I, _I, _I, _I, _D, _D, _D, _D, _I, _I, _I, _P, _P]
         lib.or_conv_lin.argtypes = conv
         lib.or_conv_log.argtypes = conv
-        lib.or_conv_log_points.argtypes = [_I, _I, _I, _I, _D, _D, _D, _D, _I, _P, ctypes.c_long,
+        lib.or_conv_log_points.argtypes = [_I, _I, _I, _I, _D, _D, _D, _D, _I, _I, _P, ctypes.c_long,
                                            ctypes.POINTER(ctypes.c_long), _P]
-        lib.or_barycenter_lin.argtypes = [_I, _I, _I, _I, _D, _D, _D, _D, _I, _I, _P, _P, _I,
+        lib.or_barycenter_lin.argtypes = [_I, _I, _I, _I, _D, _D, _D, _D, _I, _I, _I, _P, _P, _I,
                                           _P, _P, _P, _P, _P]
-        lib.or_barycenter_log.argtypes = [_I, _I, _I, _I, _D, _D, _D, _D, _I, _I, _P, _P, _I,
+        lib.or_barycenter_log.argtypes = [_I, _I, _I, _I, _D, _D, _D, _D, _I, _I, _I, _P, _P, _I,
                                           _P, _P, _P, _P, _P, _P]
-        lib.or_cost_taps.argtypes = [_I, _I, _I, _I, _D, _D, _D, _D, _P]
-        lib.or_w2_log.argtypes = [_I, _I, _I, _I, _D, _D, _D, _D, _I, _P, _P, _I, _P, _P, _P]
+        lib.or_cost_taps.argtypes = [_I, _I, _I, _I, _D, _D, _D, _D, _I, _P]
+        lib.or_w2_log.argtypes = [_I, _I, _I, _I, _D, _D, _D, _D, _I, _I, _P, _P, _I, _P, _P, _P]
         _LIB = lib
     return _LIB
 
@@ -62,11 +64,13 @@ class Grid:
     """Discretised SE(2): nx x ny spatial cells of size 1/nx x 1/ny, nth orientations
     2 pi k / nth, metric weights (w1, w2, w3), regularisation eps, kernel radius r."""
 
-    def __init__(self, nx, ny, nth, r, w=(1.0, 3.0, 0.5), eps=1e-3, periodic=False):
+    def __init__(self, nx, ny, nth, r, w=(1.0, 3.0, 0.5), eps=1e-3, periodic=False, dist="rho_b"):
         self.nx, self.ny, self.nth, self.r = int(nx), int(ny), int(nth), int(r)
         self.w1, self.w2, self.w3 = (float(v) for v in w)
         self.eps = float(eps)
         self.periodic = bool(periodic)
+        assert dist in ("rho_b", "rho_c")
+        self.dist = dist
 
     @property
     def V(self):
@@ -77,7 +81,8 @@ class Grid:
         return (self.ny, self.nx, self.nth)
 
     def _args(self):
-        return (self.nx, self.ny, self.nth, self.r, self.w1, self.w2, self.w3, self.eps)
+        return (self.nx, self.ny, self.nth, self.r, self.w1, self.w2, self.w3, self.eps,
+                1 if self.dist == "rho_c" else 0)
 
 
 def threads():
@@ -103,10 +108,16 @@ def rho_b2(x, y, th, w):
     return _lib().or_rho_b2(float(x), float(y), float(th), *(float(v) for v in w))
 
 
-def log_kernel(g, h, w, eps):
-    """log K(h^-1 g) = -rho_b(h^-1 g)^2 / eps (Sec. 4.2, Appendix A)."""
+def rho_c2(x, y, th, w):
+    """Squared logarithmic distance approximation rho_c^2 = ||log g||^2 (Sec. 4.3)."""
+    return _lib().or_rho_c2(float(x), float(y), float(th), *(float(v) for v in w))
+
+
+def log_kernel(g, h, w, eps, dist="rho_b"):
+    """log K(h^-1 g) = -rho(h^-1 g)^2 / eps (Sec. 4.2, Appendix A), rho = rho_b or rho_c."""
     g, h = _arr(g), _arr(h)
-    return _lib().or_log_kernel(_ptr(g), _ptr(h), *(float(v) for v in w), float(eps))
+    return _lib().or_log_kernel(_ptr(g), _ptr(h), *(float(v) for v in w), float(eps),
+                                1 if dist == "rho_c" else 0)
 
 
 def taps(grid):

@@ -13,7 +13,10 @@
  *                                   convention theta in [-pi, pi)).
  *   or_rho_b2                    -- squared half-angle distance rho_b^2, Sec. 4.3,
  *                                   Eq. (rho_b) with the half-angle coordinates b^1..b^3.
- *   or_log_kernel                -- log K(h^-1 g) = -rho_b(h^-1 g)^2 / eps, the Gibbs kernel
+ *   or_rho_c2                    -- squared logarithmic distance rho_c^2 = ||log g||^2, Sec. 4.3,
+ *                                   with the SE(2) logarithm from inverting the exponential map.
+ *                                   Every kernel function takes `dist`: 0 rho_b, 1 rho_c.
+ *   or_log_kernel                -- log K(h^-1 g) = -rho(h^-1 g)^2 / eps, the Gibbs kernel
  *                                   of Sec. 4.2 with p = 2 and d replaced by rho_b
  *                                   (Appendix A, kernel construction).
  *   or_taps                      -- the same kernel tabulated over the (2r+1)^2 spatial
@@ -103,19 +106,47 @@ double or_rho_b2(double x, double y, double th, double w1, double w2, double w3)
     return (w1 * b1) * (w1 * b1) + (w2 * b2) * (w2 * b2) + (w3 * b3) * (w3 * b3);
 }
 
+/* rho_c(g)^2 = ||log g||^2 in the left-invariant metric diag(w1^2, w2^2, w3^2) on the basis
+ * (A1, A2, A3) (Sec. 4.3, the logarithmic approximation).  The logarithm inverts the
+ * exponential map exp(c1 A1 + c2 A2 + c3 A3) = (V(c3) (c1, c2), c3) with
+ * V(t) = [[sin t / t, -(1 - cos t) / t], [(1 - cos t) / t, sin t / t]] (V(0) = identity):
+ * c3 = th in [-pi, pi) and (c1, c2) solves the 2x2 system V(th) (c1, c2) = (x, y). */
+double or_rho_c2(double x, double y, double th, double w1, double w2, double w3)
+{
+    double t = or_wrap(th);
+    double p, q;   /* V = [[p, -q], [q, p]] */
+    if (fabs(t) < 1e-8) {
+        p = 1.0 - t * t / 6.0;
+        q = t / 2.0;
+    } else {
+        p = sin(t) / t;
+        q = (1.0 - cos(t)) / t;
+    }
+    double det = p * p + q * q;
+    double c1 = (p * x + q * y) / det;
+    double c2 = (-q * x + p * y) / det;
+    return (w1 * c1) * (w1 * c1) + (w2 * c2) * (w2 * c2) + (w3 * t) * (w3 * t);
+}
+
+/* The squared distance the kernel uses: dist 0 = rho_b (the paper's choice), 1 = rho_c. */
+double or_rho2(double x, double y, double th, double w1, double w2, double w3, int dist)
+{
+    return dist == 1 ? or_rho_c2(x, y, th, w1, w2, w3) : or_rho_b2(x, y, th, w1, w2, w3);
+}
+
 /* log K(h^-1 g) = -rho_b(h^-1 g)^2 / eps, with h^-1 g formed by the group law. */
-double or_log_kernel(const double *g, const double *h, double w1, double w2, double w3, double eps)
+double or_log_kernel(const double *g, const double *h, double w1, double w2, double w3, double eps, int dist)
 {
     double hi[3], u[3];
     or_group_inv(h, hi);
     or_group_mul(hi, g, u);
-    return -or_rho_b2(u[0], u[1], u[2], w1, w2, w3) / eps;
+    return -or_rho2(u[0], u[1], u[2], w1, w2, w3, dist) / eps;
 }
 
 /* Tabulated log-kernel: lk[((o*nth + i)*D + (dy+r))*D + (dx+r)], D = 2r+1, is log K(h^-1 g)
  * for an output voxel g = (dx/nx, dy/ny, theta_o) and an input voxel h = (0, 0, theta_i).
  * By left invariance only the spatial offset g - h and the two orientations matter. */
-void or_taps(int nx, int ny, int nth, int r, double w1, double w2, double w3, double eps,
+void or_taps(int nx, int ny, int nth, int r, double w1, double w2, double w3, double eps, int dist,
              double *lk)
 {
     int D = 2 * r + 1;
@@ -126,7 +157,7 @@ void or_taps(int nx, int ny, int nth, int r, double w1, double w2, double w3, do
                     double g[3] = {(double)dx / nx, (double)dy / ny, 2.0 * OR_PI * o / nth};
                     double h[3] = {0.0, 0.0, 2.0 * OR_PI * i / nth};
                     lk[((size_t)(o * nth + i) * D + (dy + r)) * D + (dx + r)] =
-                        or_log_kernel(g, h, w1, w2, w3, eps);
+                        or_log_kernel(g, h, w1, w2, w3, eps, dist);
                 }
 }
 
@@ -145,14 +176,14 @@ static long or_src(int y, int x, int dy, int dx, int nx, int ny, int periodic)
 }
 
 /* out[b][y][x][o] = sum_{i, dy, dx} K_o,i(dx, dy) f[b][y-dy][x-dx][i]. */
-void or_conv_lin(int nx, int ny, int nth, int r, double w1, double w2, double w3, double eps,
+void or_conv_lin(int nx, int ny, int nth, int r, double w1, double w2, double w3, double eps, int dist,
                  int periodic, int batch, const double *f, double *out)
 {
     int D = 2 * r + 1;
     size_t V = (size_t)nx * ny * nth;
     size_t ntap = (size_t)nth * nth * D * D;
     double *kt = (double *)malloc(sizeof(double) * ntap);
-    or_taps(nx, ny, nth, r, w1, w2, w3, eps, kt);
+    or_taps(nx, ny, nth, r, w1, w2, w3, eps, dist, kt);
     for (size_t t = 0; t < ntap; ++t) kt[t] = exp(kt[t]);
 #pragma omp parallel for collapse(2) schedule(static)
     for (int b = 0; b < batch; ++b)
@@ -207,13 +238,13 @@ static double or_conv_log_one(int nx, int ny, int nth, int r, const double *lk, 
 }
 
 /* lout = log(K * exp(lf)) for every output (Sec. 4.2 in the log domain). */
-void or_conv_log(int nx, int ny, int nth, int r, double w1, double w2, double w3, double eps,
+void or_conv_log(int nx, int ny, int nth, int r, double w1, double w2, double w3, double eps, int dist,
                  int periodic, int batch, const double *lf, double *lout)
 {
     int D = 2 * r + 1;
     size_t V = (size_t)nx * ny * nth;
     double *lk = (double *)malloc(sizeof(double) * (size_t)nth * nth * D * D);
-    or_taps(nx, ny, nth, r, w1, w2, w3, eps, lk);
+    or_taps(nx, ny, nth, r, w1, w2, w3, eps, dist, lk);
 #pragma omp parallel for collapse(2) schedule(static)
     for (int b = 0; b < batch; ++b)
         for (int y = 0; y < ny; ++y)
@@ -226,13 +257,13 @@ void or_conv_log(int nx, int ny, int nth, int r, double w1, double w2, double w3
 
 /* The same as or_conv_log at the npts outputs whose flat indices (layout [b][y][x][o]) are idx[k]:
  * lout[k] = log(K * exp(lf))(idx[k]).  For grids too large to convolve whole on the CPU. */
-void or_conv_log_points(int nx, int ny, int nth, int r, double w1, double w2, double w3, double eps,
+void or_conv_log_points(int nx, int ny, int nth, int r, double w1, double w2, double w3, double eps, int dist,
                         int periodic, const double *lf, long npts, const long *idx, double *lout)
 {
     int D = 2 * r + 1;
     size_t V = (size_t)nx * ny * nth;
     double *lk = (double *)malloc(sizeof(double) * (size_t)nth * nth * D * D);
-    or_taps(nx, ny, nth, r, w1, w2, w3, eps, lk);
+    or_taps(nx, ny, nth, r, w1, w2, w3, eps, dist, lk);
 #pragma omp parallel for schedule(dynamic, 16)
     for (long k = 0; k < npts; ++k) {
         long f = idx[k];
@@ -266,7 +297,7 @@ static void or_stats_lin(size_t V, int n, const double *lam, const double *d, co
  * w_i = mu_i / (K v_i), d_i = v_i (K w_i), mu *= d_i^lambda_i; then v_i *= mu / d_i.
  * Returns mu of the last iteration.  Optional outputs (NULL to skip): v, w, d as [n][V]
  * arrays and stats = {mass, viol}. */
-void or_barycenter_lin(int nx, int ny, int nth, int r, double w1, double w2, double w3, double eps,
+void or_barycenter_lin(int nx, int ny, int nth, int r, double w1, double w2, double w3, double eps, int dist,
                        int periodic, int n, const double *mu_in, const double *lam, int iters,
                        double *bary, double *v_out, double *w_out, double *d_out, double *stats)
 {
@@ -282,9 +313,9 @@ void or_barycenter_lin(int nx, int ny, int nth, int r, double w1, double w2, dou
         for (size_t g = 0; g < V; ++g) mu[g] = 1.0;
         for (int i = 0; i < n; ++i) {
             double *vi = v + (size_t)i * V, *wi = w + (size_t)i * V, *di = d + (size_t)i * V;
-            or_conv_lin(nx, ny, nth, r, w1, w2, w3, eps, periodic, 1, vi, kv);
+            or_conv_lin(nx, ny, nth, r, w1, w2, w3, eps, dist, periodic, 1, vi, kv);
             for (size_t g = 0; g < V; ++g) wi[g] = mu_in[(size_t)i * V + g] / kv[g];
-            or_conv_lin(nx, ny, nth, r, w1, w2, w3, eps, periodic, 1, wi, kv);
+            or_conv_lin(nx, ny, nth, r, w1, w2, w3, eps, dist, periodic, 1, wi, kv);
             for (size_t g = 0; g < V; ++g) di[g] = vi[g] * kv[g];
             if (lam[i] != 0.0)
                 for (size_t g = 0; g < V; ++g) mu[g] *= pow(di[g], lam[i]);
@@ -306,7 +337,7 @@ void or_barycenter_lin(int nx, int ny, int nth, int r, double w1, double w2, dou
  * lw_i = log mu_i - log(K v_i), ld_i = lv_i + log(K w_i), L += lambda_i ld_i;
  * then lv_i += L - ld_i.  Returns exp(L) of the last iteration.  Optional outputs as in
  * or_barycenter_lin but as logarithms (lv, lw, ld), plus the final L. */
-void or_barycenter_log(int nx, int ny, int nth, int r, double w1, double w2, double w3, double eps,
+void or_barycenter_log(int nx, int ny, int nth, int r, double w1, double w2, double w3, double eps, int dist,
                        int periodic, int n, const double *mu_in, const double *lam, int iters,
                        double *bary, double *lv_out, double *lw_out, double *ld_out, double *L_out,
                        double *stats)
@@ -327,9 +358,9 @@ void or_barycenter_log(int nx, int ny, int nth, int r, double w1, double w2, dou
         for (size_t g = 0; g < V; ++g) L[g] = 0.0;
         for (int i = 0; i < n; ++i) {
             double *lvi = lv + (size_t)i * V, *lwi = lw + (size_t)i * V, *ldi = ld + (size_t)i * V;
-            or_conv_log(nx, ny, nth, r, w1, w2, w3, eps, periodic, 1, lvi, lkv);
+            or_conv_log(nx, ny, nth, r, w1, w2, w3, eps, dist, periodic, 1, lvi, lkv);
             for (size_t g = 0; g < V; ++g) lwi[g] = lmu[(size_t)i * V + g] - lkv[g];
-            or_conv_log(nx, ny, nth, r, w1, w2, w3, eps, periodic, 1, lwi, lkv);
+            or_conv_log(nx, ny, nth, r, w1, w2, w3, eps, dist, periodic, 1, lwi, lkv);
             for (size_t g = 0; g < V; ++g) ldi[g] = lvi[g] + lkv[g];
             if (lam[i] != 0.0)
                 for (size_t g = 0; g < V; ++g) L[g] += lam[i] * ldi[g];
@@ -354,7 +385,7 @@ void or_barycenter_log(int nx, int ny, int nth, int r, double w1, double w2, dou
 
 /* Cost-weighted tap table: lkc = log(c(h^-1 g) K(h^-1 g)) = log(rho_b^2) - rho_b^2 / eps in the
  * layout of or_taps; -inf where the cost vanishes (the identity tap). */
-void or_cost_taps(int nx, int ny, int nth, int r, double w1, double w2, double w3, double eps,
+void or_cost_taps(int nx, int ny, int nth, int r, double w1, double w2, double w3, double eps, int dist,
                   double *lkc)
 {
     int D = 2 * r + 1;
@@ -367,7 +398,7 @@ void or_cost_taps(int nx, int ny, int nth, int r, double w1, double w2, double w
                     double hi[3], u[3];
                     or_group_inv(h, hi);
                     or_group_mul(hi, g, u);
-                    double c = or_rho_b2(u[0], u[1], u[2], w1, w2, w3);
+                    double c = or_rho2(u[0], u[1], u[2], w1, w2, w3, dist);
                     lkc[((size_t)(o * nth + i) * D + (dy + r)) * D + (dx + r)] =
                         (c > 0.0 ? log(c) : -INFINITY) - c / eps;
                 }
@@ -394,7 +425,7 @@ static void or_conv_log_table(int nx, int ny, int nth, int r, const double *lk, 
  *   res[3] = ||a (K * b) - mu||_1 / ||mu||_1            first-marginal violation (the second
  *                                                       holds exactly after the b-step)
  * la_out / lb_out (may be NULL) receive log a and log b. */
-void or_w2_log(int nx, int ny, int nth, int r, double w1, double w2, double w3, double eps,
+void or_w2_log(int nx, int ny, int nth, int r, double w1, double w2, double w3, double eps, int dist,
                int periodic, const double *mu, const double *nu, int iters, double *res,
                double *la_out, double *lb_out)
 {
@@ -402,8 +433,8 @@ void or_w2_log(int nx, int ny, int nth, int r, double w1, double w2, double w3, 
     size_t V = (size_t)nx * ny * nth, ntap = (size_t)nth * nth * D * D;
     double *lk = (double *)malloc(sizeof(double) * ntap);
     double *lkc = (double *)malloc(sizeof(double) * ntap);
-    or_taps(nx, ny, nth, r, w1, w2, w3, eps, lk);
-    or_cost_taps(nx, ny, nth, r, w1, w2, w3, eps, lkc);
+    or_taps(nx, ny, nth, r, w1, w2, w3, eps, dist, lk);
+    or_cost_taps(nx, ny, nth, r, w1, w2, w3, eps, dist, lkc);
     double *la = (double *)malloc(sizeof(double) * V);
     double *lb = (double *)malloc(sizeof(double) * V);
     double *t = (double *)malloc(sizeof(double) * V);

@@ -404,3 +404,58 @@ def test_w2_converged_plan_is_symmetric_and_has_both_marginals():
     rev = oracle.w2_log(g, nu, mu, 300)
     np.testing.assert_allclose(rev["cost"], st["cost"], rtol=1e-10)
     np.testing.assert_allclose(rev["dual"], st["dual"], rtol=1e-10)
+
+
+# ------------------------------------------------------------- rho_c (Sec. 4.3, ||log g||)
+def test_rho_c_is_the_norm_of_the_logarithm():
+    """rho_c(exp(c1 A1 + c2 A2 + c3 A3))^2 = (w1 c1)^2 + (w2 c2)^2 + (w3 c3)^2 for |c3| < pi:
+    the oracle's logarithm inverts scipy's matrix exponential."""
+    for _ in range(300):
+        c1, c2 = RNG.uniform(-0.5, 0.5, size=2)
+        c3 = RNG.uniform(-3.1, 3.1)
+        w = RNG.uniform(0.3, 4.0, size=3)
+        g = refmath.coords(refmath.expm_algebra(c1, c2, c3))
+        want = (w[0] * c1) ** 2 + (w[1] * c2) ** 2 + (w[2] * c3) ** 2
+        assert abs(oracle.rho_c2(g[0], g[1], g[2], w) - want) <= 1e-12 * max(1.0, want)
+
+
+def test_rho_c_special_values_symmetries_and_bound():
+    """rho_c agrees with rho_b when theta = 0 or on the pure rotations, is symmetric under
+    inversion and the two reflections, and is never below rho_b (the chord factor
+    (theta/2) / sin(theta/2) >= 1)."""
+    assert oracle.rho_c2(0, 0, 0, W) == 0.0
+    for _ in range(200):
+        g = np.array([RNG.uniform(-1, 1), RNG.uniform(-1, 1), RNG.uniform(-math.pi, math.pi)])
+        w = RNG.uniform(0.3, 4.0, size=3)
+        base = oracle.rho_c2(*g, w)
+        assert abs(oracle.rho_c2(0, 0, g[2], w) - (w[2] * g[2]) ** 2) < 1e-13
+        assert abs(oracle.rho_c2(g[0], g[1], 0, w) - oracle.rho_b2(g[0], g[1], 0, w)) < 1e-14
+        assert abs(oracle.rho_c2(*oracle.group_inv(g), w) - base) < 1e-12 * max(1, base)
+        assert abs(oracle.rho_c2(g[0], -g[1], -g[2], w) - base) < 1e-12 * max(1, base)
+        assert abs(oracle.rho_c2(-g[0], g[1], -g[2], w) - base) < 1e-12 * max(1, base)
+        assert base >= oracle.rho_b2(*g, w) * (1 - 1e-13)
+
+
+@pytest.mark.parametrize("periodic", [False, True])
+def test_rho_c_conv_equals_dense_group_kernel(periodic):
+    g = oracle.Grid(6, 5, 8, 2, W, 0.05, periodic, dist="rho_c")
+    LK = refmath.dense_log_kernel(g.nx, g.ny, g.nth, g.r, lambda x, y, t: oracle.rho_c2(x, y, t, W), g.eps, periodic)
+    f = RNG.uniform(0.1, 1.0, size=g.shape)
+    np.testing.assert_allclose(oracle.conv_lin(g, f), (np.exp(LK) @ f.reshape(-1)).reshape(g.shape),
+                               rtol=1e-13, atol=0)
+    np.testing.assert_allclose(oracle.conv_log(g, np.log(f)), np.log(oracle.conv_lin(g, f)), rtol=0, atol=1e-14)
+
+
+def test_rho_c_barycenter_equivariance():
+    """Weak orientation penalty (w3 = 0.1) so that neighbouring orientations couple, where rho_c
+    and rho_b differ (by the chord factor on the spatial part)."""
+    w = (1.0, 3.0, 0.1)
+    g = oracle.Grid(12, 12, 8, 3, w, 2e-2, dist="rho_c")
+    mu = _inputs(g, 2, 8)
+    lam = [0.4, 0.6]
+    b = oracle.barycenter_log(g, mu, lam, 12)
+    np.testing.assert_allclose(oracle.barycenter_log(g, refmath.rot90(mu), lam, 12), refmath.rot90(b), rtol=1e-11)
+    np.testing.assert_allclose(oracle.barycenter_log(g, refmath.mirror_y(mu), lam, 12), refmath.mirror_y(b),
+                               rtol=1e-11)
+    other = oracle.barycenter_log(oracle.Grid(12, 12, 8, 3, w, 2e-2), mu, lam, 12)
+    assert np.abs(b - other).sum() / other.sum() > 1e-4
