@@ -73,12 +73,19 @@ typedef enum {
     SE2OT_BOUNDARY_PERIODIC = 1  /* spatial indices wrap (theta always wraps)               */
 } se2ot_boundary;
 
+/* The distance approximation rho in the Gibbs kernel K(g) = exp(-rho(g)^2 / eps) (Sec. 4.3). */
+typedef enum {
+    SE2OT_DIST_RHO_B = 0,        /* half-angle approximation rho_b (the paper's kernel)      */
+    SE2OT_DIST_RHO_C = 1         /* logarithmic approximation rho_c = ||log g||              */
+} se2ot_distance;
+
 /* Grid, metric and kernel.  Valid ranges: nx, ny >= 2*radius + 1; 0 <= radius <= 16;
  * 1 <= ntheta <= 64; w1, w2, w3 > 0; eps > 0. */
 typedef struct {
     int nx, ny, ntheta, radius;
     double w1, w2, w3, eps;
     int boundary;                /* se2ot_boundary */
+    int distance;                /* se2ot_distance */
 } se2ot_kernel_desc;
 
 typedef struct se2ot_kernel_s *se2ot_kernel;   /* opaque; owns tap tables and workspace */

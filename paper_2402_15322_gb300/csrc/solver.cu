@@ -164,6 +164,8 @@ se2ot_status validate_desc(const se2ot_kernel_desc *d)
     if (!(d->eps > 0) || !std::isfinite(d->eps)) return fail(SE2OT_EINVAL, "eps must be finite and > 0");
     if (d->boundary != SE2OT_BOUNDARY_ZERO && d->boundary != SE2OT_BOUNDARY_PERIODIC)
         return fail(SE2OT_EINVAL, "boundary=%d unknown", d->boundary);
+    if (d->distance != SE2OT_DIST_RHO_B && d->distance != SE2OT_DIST_RHO_C)
+        return fail(SE2OT_EINVAL, "distance=%d unknown", d->distance);
     if ((double)d->nx * d->ny * nt > 1.0e9) return fail(SE2OT_EINVAL, "grid too large");
     return SE2OT_OK;
 }

@@ -13,6 +13,10 @@
 // A theta difference of exactly pi is taken as -pi (small-angle convention); rho_b is the same
 // for +pi and -pi, so the choice does not matter.
 //
+// rho_c (the logarithmic approximation, ||log g|| in the same metric) differs only by the chord
+// factor of the SE(2) logarithm: log g = (f (b1, b2), b3) with f = (b3/2) / sin(b3/2) (f = 1 at
+// b3 = 0), so its spatial taps are those of rho_b times f^2 of the orientation pair.
+//
 // Cost-weighted table (the kernel c K with c = rho_b^2, whose convolution gives a plan's
 // transport cost, Eq. (L^{W_p}) with p = 2): the same ltheta, and log2(rho_b^2 / C0) added to
 // every spatial tap (-inf at the identity, where the cost vanishes).  C0 is a power of two no
@@ -39,7 +43,7 @@ __device__ double dtheta_pi(int o, int i, int nt)
 }
 
 __global__ void spatial_taps_kernel(int nx, int ny, int nt, int r, double w1, double w2, double w3, double eps,
-                                    bool cost, int log2_c0, float *ls, float *ls_lo)
+                                    int dist, bool cost, int log2_c0, float *ls, float *ls_lo)
 {
     const int D = 2 * r + 1;
     const long total = (long)nt * nt * D * D;
@@ -62,7 +66,12 @@ __global__ void spatial_taps_kernel(int nx, int ny, int nt, int r, double w1, do
         sincospi(0.5 * dtheta_pi(o, i, nt), &sh, &ch);
         const double b1 = ux * ch + uy * sh;
         const double b2 = -ux * sh + uy * ch;
-        const double sp = (w1 * b1) * (w1 * b1) + (w2 * b2) * (w2 * b2);
+        double sp = (w1 * b1) * (w1 * b1) + (w2 * b2) * (w2 * b2);
+        if (dist == SE2OT_DIST_RHO_C && o != i) {
+            const double half = 0.5 * dtheta_pi(o, i, nt);   // b3 / 2 in units of pi
+            const double f = half * 3.14159265358979323846 / sinpi(half);
+            sp *= f * f;
+        }
         double v = -sp / eps * LOG2E;
         if (cost) {
             const double b3 = dtheta_pi(o, i, nt) * 3.14159265358979323846;
@@ -95,7 +104,9 @@ __global__ void theta_taps_kernel(int nt, int r, double w3, double eps, const fl
 cudaError_t build_taps(const se2ot_kernel_desc &d, Taps &t, cudaStream_t s, bool cost, double *cost_scale)
 {
     // |(b1, b2)| = |(u_x, u_y)| <= r sqrt(1/nx^2 + 1/ny^2) and |b3| <= pi bound rho_b^2 on the window
-    const double ux = (double)d.radius / d.nx, uy = (double)d.radius / d.ny, wm = std::max(d.w1, d.w2);
+    // (rho_c: times the largest chord factor squared, (pi/2)^2)
+    const double ux = (double)d.radius / d.nx, uy = (double)d.radius / d.ny;
+    const double wm = std::max(d.w1, d.w2) * (d.distance == SE2OT_DIST_RHO_C ? 1.5707963267948966 : 1.0);
     const double bound = wm * wm * (ux * ux + uy * uy) + (d.w3 * 3.14159265358979323846) * (d.w3 * 3.14159265358979323846);
     const int log2_c0 = bound > 0.0 ? (int)std::ceil(std::log2(bound)) : 0;
     if (cost_scale) *cost_scale = std::ldexp(1.0, log2_c0);
@@ -103,8 +114,8 @@ cudaError_t build_taps(const se2ot_kernel_desc &d, Taps &t, cudaStream_t s, bool
     const long total = (long)d.ntheta * d.ntheta * D * D;
     int blocks = (int)((total + 255) / 256);
     if (blocks > 4096) blocks = 4096;
-    spatial_taps_kernel<<<blocks, 256, 0, s>>>(d.nx, d.ny, d.ntheta, d.radius, d.w1, d.w2, d.w3, d.eps, cost,
-                                               log2_c0, t.ls, t.ls_lo);
+    spatial_taps_kernel<<<blocks, 256, 0, s>>>(d.nx, d.ny, d.ntheta, d.radius, d.w1, d.w2, d.w3, d.eps,
+                                               d.distance, cost, log2_c0, t.ls, t.ls_lo);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int pairs = d.ntheta * d.ntheta;

@@ -26,13 +26,15 @@ STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENONFINITE", 
 SE2OT_FP32 = 0
 SE2OT_BOUNDARY_ZERO = 0
 SE2OT_BOUNDARY_PERIODIC = 1
+SE2OT_DIST_RHO_B, SE2OT_DIST_RHO_C = 0, 1
 SE2OT_FLAG_TIME_CONV = 1
 
 
 class se2ot_kernel_desc(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("ntheta", ctypes.c_int),
                 ("radius", ctypes.c_int), ("w1", ctypes.c_double), ("w2", ctypes.c_double),
-                ("w3", ctypes.c_double), ("eps", ctypes.c_double), ("boundary", ctypes.c_int)]
+                ("w3", ctypes.c_double), ("eps", ctypes.c_double), ("boundary", ctypes.c_int),
+                ("distance", ctypes.c_int)]
 
 
 class se2ot_solve_opts(ctypes.Structure):
@@ -170,10 +172,14 @@ class Kernel:
             pass
 
 
-def make_desc(nx, ny, ntheta, radius, w=(1.0, 3.0, 0.5), eps=1e-3, periodic=False):
+def make_desc(nx, ny, ntheta, radius, w=(1.0, 3.0, 0.5), eps=1e-3, periodic=False, distance="rho_b"):
+    """Kernel descriptor; distance "rho_b" (half-angle, the paper's) or "rho_c" (logarithmic)."""
+    if distance not in ("rho_b", "rho_c"):
+        raise ValueError("distance must be 'rho_b' or 'rho_c'")
     return se2ot_kernel_desc(int(nx), int(ny), int(ntheta), int(radius), float(w[0]), float(w[1]),
                              float(w[2]), float(eps),
-                             SE2OT_BOUNDARY_PERIODIC if periodic else SE2OT_BOUNDARY_ZERO)
+                             SE2OT_BOUNDARY_PERIODIC if periodic else SE2OT_BOUNDARY_ZERO,
+                             SE2OT_DIST_RHO_C if distance == "rho_c" else SE2OT_DIST_RHO_B)
 
 
 def se2ot_kernel_build(desc, stream=None):

@@ -63,8 +63,18 @@ def test_invalid_descriptor_is_rejected_on_the_host(lib, bad):
     assert se2ot.se2ot_last_error()
 
 
+def test_unknown_boundary_or_distance_is_rejected_on_the_host(lib):
+    for field, value in (("boundary", 5), ("distance", 3)):
+        desc = se2ot.make_desc(16, 16, 8, 3)
+        setattr(desc, field, value)
+        h = ctypes.c_void_p()
+        assert lib.se2ot_kernel_build(ctypes.byref(desc), None, ctypes.byref(h)) == se2ot.SE2OT_EINVAL
+        assert h.value is None and field in se2ot.se2ot_last_error()
+
+
 def test_null_arguments_are_rejected(lib):
     assert lib.se2ot_kernel_build(None, None, None) == se2ot.SE2OT_EINVAL
     assert lib.se2ot_apply(None, None, None, 1, None) == se2ot.SE2OT_EINVAL
     assert lib.se2ot_barycenter(None, 2, None, None, None, None, None, None) == se2ot.SE2OT_EINVAL
+    assert lib.se2ot_w2(None, None, None, None, None, None) == se2ot.SE2OT_EINVAL
     assert lib.se2ot_kernel_destroy(None) == se2ot.SE2OT_OK
