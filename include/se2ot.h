@@ -206,6 +206,40 @@ typedef struct {
 SE2OT_API se2ot_status se2ot_w2(se2ot_kernel k, const float *mu, const float *nu, const se2ot_solve_opts *opts,
                                 se2ot_w2_result *res, void *stream);
 
+/* Lifting / projection helpers of the paper's experiments (Sec. 2.4, 6.2, 6.3).  Device pointers
+ * only (EINVAL otherwise); arrays in the caller layout, orientation innermost; enqueued on
+ * `stream`, no synchronisation.
+ *
+ * se2ot_project: P[b][y][x] = sum_k U[b][y][x][k], the projection P(U) = integral of U over theta
+ * (Eq. proj) with unit weight per orientation bin (the bin width 2 pi / ntheta is a constant the
+ * paper's normalisation of every output removes).  U: batch * ny * nx * ntheta floats, P: batch *
+ * ny * nx floats (FP64 accumulation). */
+SE2OT_API se2ot_status se2ot_project(const float *U, float *P, int batch, int nx, int ny, int ntheta, void *stream);
+
+/* Lift of an orientation field v = |v| (cos psi, sin psi) onto SE(2) (Sec. 6.3, lifting of vector
+ * fields): U[y][x][k] = |v[y][x]| for the bin k whose centre 2 pi k / ntheta is within pi / ntheta
+ * of psi = atan2(v_y, v_x) (an angle exactly half-way goes to the upper bin), 0 elsewhere.
+ * v: ny * nx * 2 floats (x, y components), U: ny * nx * ntheta floats. */
+SE2OT_API se2ot_status se2ot_lift_field(const float *v, float *U, int nx, int ny, int ntheta, void *stream);
+
+/* Reconstruction of the field (Sec. 6.3): v = (sum_k U[y][x][k]) (cos psi*, sin psi*) with psi* the
+ * centre of the first largest bin; v = 0 where every bin is 0.  Inverse of se2ot_lift_field on
+ * bin-centred angles. */
+SE2OT_API se2ot_status se2ot_reconstruct_field(const float *U, float *v, int nx, int ny, int ntheta, void *stream);
+
+/* Interpolation of two signed orientation scores (Sec. 6.2, steps 2-4): the positive and negative
+ * parts U+- = max(+-U, 0) get a floor of 1e-6 of their maximum (exact zeros make the scaling
+ * update 0/0 wherever the barycenter vanishes too), are normalised to mass 1 and interpolated
+ * separately with the same kernel and options (se2ot_interpolate), then
+ *   b[y][x] = m+_t P(Phi_t(U0+, U1+)) - m-_t P(Phi_t(U0-, U1-)),   m_t = (1 - t) m_0 + t m_1,
+ * with m the parts' masses (FP64), so that b keeps the scale of the scores.  A part that is zero
+ * on both sides contributes nothing; zero on one side only is EINVAL (nothing to transport).
+ * U0, U1: V floats each (the kernel's grid), b: ny * nx floats, device memory; stats (may be NULL)
+ * receives 2 entries, the positive and the negative part's solve.  Synchronises the stream. */
+SE2OT_API se2ot_status se2ot_interpolate_signed(se2ot_kernel k, const float *U0, const float *U1, double t,
+                                                const se2ot_solve_opts *opts, float *b, se2ot_stats *stats,
+                                                void *stream);
+
 /* nprob independent interpolations Phi_t(mu0[p], mu1[p]) (weights (1 - t[p], t[p])) of uneven grid
  * sizes, radii, metrics and regularisations, iterated in lockstep for opts->max_iters Sinkhorn
  * iterations (Appendix A with n = 2 for every problem).  descs[p]: each problem's grid and kernel

@@ -16,10 +16,12 @@ Readings (the paper leaves them open):
     k = floor(psi N / (2 pi) + 1/2) mod N.
   * Reconstruction: psi* is the centre of the first largest bin (lowest index among ties);
     a voxel whose bins are all zero reconstructs to v = 0.
-  * Signed interpolation: each part is normalised to mass 1 for the transport and scaled back by
-    the interpolated mass m_t = (1 - t) m_0 + t m_1 before projecting, so that b_t keeps the
-    images' scale (at t = 0 and 1 up to the kernel's blur).  A part with zero mass on both sides
-    contributes nothing.
+  * Signed interpolation: each part gets a floor of 1e-6 of its maximum (the floor of every
+    input of the paper's configs: exact zeros make the scaling update 0/0 wherever the
+    barycenter vanishes too) and is normalised to mass 1 for the transport; the result is
+    scaled back by the interpolated mass m_t = (1 - t) m_0 + t m_1 of the unfloored parts before
+    projecting, so that b_t keeps the images' scale (at t = 0 and 1 up to the kernel's blur).  A
+    part with zero mass on both sides contributes nothing.
 """
 import math
 
@@ -74,10 +76,20 @@ def split(U):
     return up, um, up.sum(), um.sum()
 
 
+PART_FLOOR = 1e-6
+
+
+def part_measure(part):
+    """A split part as the measure that is transported: floored at PART_FLOOR of its maximum,
+    normalised to mass 1."""
+    f = part + PART_FLOOR * part.max()
+    return f / f.sum()
+
+
 def interpolate_signed(grid, U0, U1, t, iters):
-    """Interpolation of two signed scores (Sec. 6.2, steps 2-4): b_t = m+_t P(Phi_t(U0+/m0+,
-    U1+/m1+)) - m-_t P(Phi_t(U0-/m0-, U1-/m1-)) with m_t = (1 - t) m_0 + t m_1, both
-    interpolations with the same settings.  Returns b_t of shape [ny, nx]."""
+    """Interpolation of two signed scores (Sec. 6.2, steps 2-4): b_t = m+_t P(Phi_t(U0+, U1+))
+    - m-_t P(Phi_t(U0-, U1-)) with the parts as measures (part_measure) and m_t = (1 - t) m_0 + t m_1
+    their interpolated masses, both interpolations with the same settings.  Returns b_t [ny, nx]."""
     p0, n0, mp0, mn0 = split(U0)
     p1, n1, mp1, mn1 = split(U1)
     b = np.zeros(np.asarray(U0).shape[:2])
@@ -86,6 +98,6 @@ def interpolate_signed(grid, U0, U1, t, iters):
             continue
         if m0 == 0.0 or m1 == 0.0:
             raise ValueError("one side of a part has zero mass: no transport between them")
-        phi = interpolate_log(grid, a0 / m0, a1 / m1, t, iters)
+        phi = interpolate_log(grid, part_measure(a0), part_measure(a1), t, iters)
         b += sign * ((1.0 - t) * m0 + t * m1) * project(phi)
     return b

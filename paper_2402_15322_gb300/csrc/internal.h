@@ -82,6 +82,7 @@ cudaError_t launch_order_init(unsigned *order, unsigned *cost, unsigned *done, l
 size_t conv_smem_bytes(int r);           // dynamic shared memory of one convolution CTA
 
 // Host helpers of solver.cu shared with other entry points.
+const se2ot_kernel_desc &kernel_desc(se2ot_kernel k);            // the descriptor of a kernel handle
 se2ot_status validate_kernel_desc(const se2ot_kernel_desc *d);   // EINVAL + message, or OK
 void set_last_error(const char *msg);                            // se2ot_last_error() text
 

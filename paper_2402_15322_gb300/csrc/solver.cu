@@ -231,6 +231,8 @@ namespace se2ot {
 
 se2ot_status validate_kernel_desc(const se2ot_kernel_desc *d) { return validate_desc(d); }
 
+const se2ot_kernel_desc &kernel_desc(se2ot_kernel k) { return k->d; }
+
 void set_last_error(const char *msg) { g_last_error = msg; }
 
 }  // namespace se2ot

@@ -92,6 +92,11 @@ def lib():
                                     ctypes.POINTER(se2ot_stats), vp]
     L.se2ot_state_export.argtypes = [vp, i, vp, vp, vp, vp]
     L.se2ot_w2.argtypes = [vp, vp, vp, ctypes.POINTER(se2ot_solve_opts), ctypes.POINTER(se2ot_w2_result), vp]
+    L.se2ot_project.argtypes = [vp, vp, i, i, i, i, vp]
+    L.se2ot_lift_field.argtypes = [vp, vp, i, i, i, vp]
+    L.se2ot_reconstruct_field.argtypes = [vp, vp, i, i, i, vp]
+    L.se2ot_interpolate_signed.argtypes = [vp, vp, vp, d, ctypes.POINTER(se2ot_solve_opts), vp,
+                                           ctypes.POINTER(se2ot_stats), vp]
     L.se2ot_interpolate_batched.argtypes = [i, ctypes.POINTER(se2ot_kernel_desc), ctypes.POINTER(vp),
                                             ctypes.POINTER(vp), ctypes.POINTER(d),
                                             ctypes.POINTER(se2ot_solve_opts), ctypes.POINTER(vp),
@@ -263,6 +268,45 @@ def se2ot_w2(kernel, mu, nu, opts=None, stream=None, raise_on_error=True):
     if raise_on_error:
         _check(status)
     return res.as_dict(), status
+
+
+def se2ot_project(U, stream=None):
+    """P(U) = sum over the orientation bins: U [..., ny, nx, nt] (CUDA float32) -> [..., ny, nx]."""
+    ny, nx, nt = U.shape[-3:]
+    batch = U.numel() // (ny * nx * nt)
+    P = torch.empty(U.shape[:-1], dtype=torch.float32, device=U.device)
+    _check(lib().se2ot_project(_ptr(U, torch.float32), _ptr(P, torch.float32), batch, nx, ny, nt, _stream(stream)))
+    return P
+
+
+def se2ot_lift_field(v, ntheta, stream=None):
+    """Orientation-field lift: v [ny, nx, 2] (CUDA float32) -> U [ny, nx, ntheta]."""
+    ny, nx = v.shape[:2]
+    U = torch.empty((ny, nx, ntheta), dtype=torch.float32, device=v.device)
+    _check(lib().se2ot_lift_field(_ptr(v, torch.float32), _ptr(U, torch.float32), nx, ny, ntheta, _stream(stream)))
+    return U
+
+
+def se2ot_reconstruct_field(U, stream=None):
+    """Field reconstruction: U [ny, nx, nt] (CUDA float32) -> v [ny, nx, 2]."""
+    ny, nx, nt = U.shape
+    v = torch.empty((ny, nx, 2), dtype=torch.float32, device=U.device)
+    _check(lib().se2ot_reconstruct_field(_ptr(U, torch.float32), _ptr(v, torch.float32), nx, ny, nt, _stream(stream)))
+    return v
+
+
+def se2ot_interpolate_signed(kernel, U0, U1, t, opts=None, stream=None, raise_on_error=True):
+    """Signed-score interpolation b_t = m+_t P(Phi_t(U0+, U1+)) - m-_t P(Phi_t(U0-, U1-)).
+    Returns (b [ny, nx], [stats of the positive part, of the negative part], status)."""
+    ny, nx = U0.shape[:2]
+    b = torch.empty((ny, nx), dtype=torch.float32, device=U0.device)
+    st = (se2ot_stats * 2)()
+    status = lib().se2ot_interpolate_signed(kernel.handle, _ptr(U0, torch.float32), _ptr(U1, torch.float32), float(t),
+                                            ctypes.byref(opts if opts is not None else solve_opts()), _ptr(b, torch.float32),
+                                            st, _stream(stream))
+    if raise_on_error:
+        _check(status)
+    return b, [st[0].as_dict(), st[1].as_dict()], status
 
 
 def se2ot_interpolate(kernel, mu0, mu1, t, opts=None, out=None, stream=None, raise_on_error=True):

@@ -192,3 +192,13 @@ def curve_measures(n, nx, ny, nth, config_seed, max_shift, problem=0, nbumps=8, 
             f += bump(nx, ny, nth, cx + ox / nx, cy + oy / ny, phi, sa, sb, st, amp)
         out.append(_finish(f, floor))
     return np.stack(out)
+
+
+def dirac_measure(nx, ny, nt, voxel, floor=1e-6):
+    """A point mass at voxel (ix, iy, k) plus the floor on every voxel, normalised to mass 1
+    (the point masses of the geodesic-tracing experiments, with the configs' floor: an exact
+    zero makes the scaling update 0/0).  Shape [ny, nx, nt], float64."""
+    ix, iy, k = voxel
+    mu = np.full((ny, nx, nt), float(floor))
+    mu[iy, ix, k] += 1.0
+    return mu / mu.sum()
