@@ -46,6 +46,9 @@ def _lib():
                                           _P, _P, _P, _P, _P, _P]
         lib.or_cost_taps.argtypes = [_I, _I, _I, _I, _D, _D, _D, _D, _I, _P]
         lib.or_w2_log.argtypes = [_I, _I, _I, _I, _D, _D, _D, _D, _I, _I, _P, _P, _I, _P, _P, _P]
+        lib.or_prox_log.argtypes = [_D, _D, _D]
+        lib.or_prox_log.restype = _D
+        lib.or_jko_log.argtypes = [_I, _I, _I, _I, _D, _D, _D, _D, _I, _I, _P, _D, _D, _I, _I, _P, _P]
         _LIB = lib
     return _LIB
 
@@ -215,3 +218,19 @@ def w2_log(grid, mu, nu, iters, want_state=False):
     if want_state:
         out["la"], out["lb"] = la, lb
     return out
+
+
+def prox_log(lz, sigma, m):
+    """log of the KL-proximal map of sigma s^m / (m - 1) at z = exp(lz) (porous-medium energy)."""
+    return _lib().or_prox_log(float(lz), float(sigma), float(m))
+
+
+def jko_log(grid, mu0, tau, m, steps, iters):
+    """`steps` entropic JKO steps of F = sum mu^m / (m - 1) from mu0 (Sec. 2.2 Eq. (GF_JKO), Sec. 6.4),
+    each with `iters` scaling iterations.  Returns (mu, {mass, viol})."""
+    mu0 = _arr(mu0)
+    out = np.zeros_like(mu0)
+    st = np.zeros(2)
+    _lib().or_jko_log(*grid._args(), int(grid.periodic), _ptr(mu0), float(tau), float(m), int(steps), int(iters),
+                      _ptr(out), _ptr(st))
+    return out, {"mass": st[0], "viol": st[1]}

@@ -31,6 +31,11 @@
  *                                   its logarithm (same steps, same order).
  *   or_cost_taps                 -- log(c K) with c = rho_b^2: the kernel weighted by the cost,
  *                                   whose convolution gives the transport cost of a plan.
+ *   or_prox_log / or_jko_log     -- entropic JKO steps of the porous-medium energy
+ *                                   F = sum mu^m / (m - 1) (Sec. 2.2 Eq. (GF_JKO), Sec. 6.4):
+ *                                   the scaling iterations of Sec. 4.1 with the marginal
+ *                                   constraint on the first marginal and the KL-proximal map of
+ *                                   tau F on the second, derived in or_prox_log.
  *   or_w2_log                    -- entropic transport between two measures, Sec. 4.1: the
  *                                   scaling iterations with the marginal-constraint prox
  *                                   (a = mu / K b, b = nu / K a), in the log domain, and the
@@ -469,4 +474,82 @@ void or_w2_log(int nx, int ny, int nth, int r, double w1, double w2, double w3, 
     if (la_out) memcpy(la_out, la, sizeof(double) * V);
     if (lb_out) memcpy(lb_out, lb, sizeof(double) * V);
     free(lk); free(lkc); free(la); free(lb); free(t);
+}
+
+/* KL-proximal map of sigma F, F(s) = s^m / (m - 1) per voxel (unit Haar weight), at z = exp(lz):
+ * prox(z) = argmin_s sigma s^m / (m - 1) + s log(s / z) - s.  Setting the derivative to zero,
+ * u = log s solves u + c exp((m - 1) u) = lz with c = sigma m / (m - 1); the left side is increasing
+ * and convex in u, so Newton's method converges from any start (from the right monotonically).
+ * Returns u = log prox(z); lz = -inf gives -inf. */
+double or_prox_log(double lz, double sigma, double m)
+{
+    if (lz == -INFINITY) return -INFINITY;
+    double c = sigma * m / (m - 1.0), q = m - 1.0;
+    double u = lz;
+    /* a start no worse than lz when c exp(q lz) is large: the root has c exp(q u) <= |lz| + 1 */
+    double alt = log((fabs(lz) + 1.0) / c) / q;
+    if (alt < u) u = alt;
+    for (int it = 0; it < 200; ++it) {
+        double e = c * exp(q * u);
+        double f = u + e - lz, fp = 1.0 + q * e;
+        double step = f / fp;
+        u -= step;
+        if (fabs(step) <= 1e-15 * (1.0 + fabs(u))) break;
+    }
+    return u;
+}
+
+/* `steps` entropic JKO steps mu_{k+1} = argmin_nu W_eps(mu_k, nu) + tau F(nu) from mu_0 (Sec. 2.2
+ * Eq. (GF_JKO) with the entropic scheme of Sec. 4.1).  Each step runs `iters` scaling iterations
+ * from b = 1:
+ *   log a = log mu_k - log(K b)                       (prox of the constraint on the 1st marginal)
+ *   u = log prox_{(tau/eps) F}(K a),  log b = u - log(K a)     (prox of tau F on the 2nd marginal)
+ * and mu_{k+1} = exp(u) of the last iteration (= b (K a), the plan's second marginal).
+ * mu_out: V values; stats[0] = sum mu_out, stats[1] = ||a (K b) - mu_k||_1 / ||mu_k||_1 of the last
+ * step (its first-marginal violation). */
+void or_jko_log(int nx, int ny, int nth, int r, double w1, double w2, double w3, double eps, int dist,
+                int periodic, const double *mu0, double tau, double m, int steps, int iters, double *mu_out,
+                double *stats)
+{
+    int D = 2 * r + 1;
+    size_t V = (size_t)nx * ny * nth;
+    double *lk = (double *)malloc(sizeof(double) * (size_t)nth * nth * D * D);
+    or_taps(nx, ny, nth, r, w1, w2, w3, eps, dist, lk);
+    double *lmu = (double *)malloc(sizeof(double) * V);
+    double *la = (double *)malloc(sizeof(double) * V);
+    double *lb = (double *)malloc(sizeof(double) * V);
+    double *t = (double *)malloc(sizeof(double) * V);
+    double *u = (double *)malloc(sizeof(double) * V);
+    double sigma = tau / eps, viol = 0.0;
+    for (size_t g = 0; g < V; ++g) lmu[g] = log(mu0[g]);
+    for (int k = 0; k < steps; ++k) {
+        for (size_t g = 0; g < V; ++g) lb[g] = 0.0;
+        for (int j = 0; j < iters; ++j) {
+            or_conv_log_table(nx, ny, nth, r, lk, periodic, lb, t);
+            for (size_t g = 0; g < V; ++g) la[g] = lmu[g] - t[g];
+            or_conv_log_table(nx, ny, nth, r, lk, periodic, la, t);
+            for (size_t g = 0; g < V; ++g) {
+                u[g] = or_prox_log(t[g], sigma, m);
+                lb[g] = u[g] - t[g];
+            }
+        }
+        /* first-marginal violation of this step */
+        or_conv_log_table(nx, ny, nth, r, lk, periodic, lb, t);
+        double dev = 0.0, msum = 0.0;
+        for (size_t g = 0; g < V; ++g) {
+            double mk = exp(lmu[g]);
+            dev += fabs(exp(la[g] + t[g]) - mk);
+            msum += mk;
+        }
+        viol = dev / msum;
+        for (size_t g = 0; g < V; ++g) lmu[g] = u[g];
+    }
+    double mass = 0.0;
+    for (size_t g = 0; g < V; ++g) {
+        mu_out[g] = exp(lmu[g]);
+        mass += mu_out[g];
+    }
+    stats[0] = mass;
+    stats[1] = viol;
+    free(lk); free(lmu); free(la); free(lb); free(t); free(u);
 }

@@ -459,3 +459,79 @@ def test_rho_c_barycenter_equivariance():
                                rtol=1e-11)
     other = oracle.barycenter_log(oracle.Grid(12, 12, 8, 3, w, 2e-2), mu, lam, 12)
     assert np.abs(b - other).sum() / other.sum() > 1e-4
+
+
+# ------------------------------------------- entropic JKO, porous-medium energy (Sec. 2.2, 6.4)
+def test_prox_matches_lambert_w_for_m_2():
+    """m = 2: log s + 2 sigma s = log z, so s = W(2 sigma z) / (2 sigma) (scipy's Lambert W)."""
+    import scipy.special
+    for sigma in (1e-3, 0.1, 3.0, 50.0, 1e4):
+        for lz in (-300.0, -30.0, -2.0, 0.0, 3.0, 40.0, 300.0):
+            want = np.log(scipy.special.lambertw(2 * sigma * np.exp(min(lz, 700.0))).real / (2 * sigma)) \
+                if lz < 700 else None
+            got = oracle.prox_log(lz, sigma, 2.0)
+            assert abs(got - want) <= 1e-12 * max(1.0, abs(want))
+
+
+def test_prox_is_the_minimiser():
+    """m = 5: the objective sigma s^m / (m - 1) + s log(s / z) - s is smallest at the prox."""
+    m = 5.0
+    for sigma in (0.05, 2.0, 300.0):
+        for lz in (-8.0, -1.0, 0.5, 6.0):
+            s = math.exp(oracle.prox_log(lz, sigma, m))
+            obj = lambda q: sigma * q ** m / (m - 1) + q * (math.log(q) - lz) - q
+            for d in (1e-3, 1e-2):
+                assert obj(s) <= obj(s * (1 + d)) and obj(s) <= obj(s * (1 - d))
+            grad = sigma * m / (m - 1) * s ** (m - 1) + math.log(s) - lz
+            assert abs(grad) < 1e-12 * (1 + abs(lz))
+
+
+def _dense_jko_step(K, mu, sigma, m, iters):
+    """One JKO step with the explicit kernel matrix, the prox by a bracketing root finder."""
+    import scipy.optimize
+    c = sigma * m / (m - 1)
+    b = np.ones(K.shape[0])
+    for _ in range(iters):
+        a = mu / (K @ b)
+        z = K.T @ a
+        s = np.array([math.exp(scipy.optimize.brentq(lambda u: u + c * math.exp((m - 1) * u) - math.log(zi),
+                                                     math.log(zi) - 50.0, math.log(zi) + 1.0, xtol=1e-15,
+                                                     rtol=1e-15)) for zi in z])
+        b = s / z
+    return s, np.abs(a * (K @ b) - mu).sum() / mu.sum()
+
+
+@pytest.mark.parametrize("periodic", [False, True])
+def test_jko_matches_dense_scaling_with_an_independent_prox(periodic):
+    g = oracle.Grid(5, 6, 4, 2, (1.0, math.sqrt(10), math.sqrt(2)), 0.05, periodic)
+    K = _dense_K(g)
+    mu = _inputs(g, 1, 31)[0]
+    tau, m, iters = 0.02, 5.0, 15
+    s, viol = _dense_jko_step(K, mu.reshape(-1) * g.V, tau / g.eps, m, iters)   # density-scale values
+    got, st = oracle.jko_log(g, mu * g.V, tau, m, 1, iters)
+    np.testing.assert_allclose(got.reshape(-1), s, rtol=1e-11)
+    np.testing.assert_allclose(st["viol"], viol, rtol=1e-7, atol=1e-14)
+
+
+def test_jko_with_zero_time_step_is_one_blur():
+    """tau = 0: the prox is the identity, b = 1 and mu_1 = K(mu_0 / K 1) (as for identical inputs)."""
+    g = oracle.Grid(6, 5, 4, 2, W, 0.05)
+    K = _dense_K(g)
+    mu = _inputs(g, 1, 32)[0]
+    got, _ = oracle.jko_log(g, mu, 0.0, 5.0, 1, 4)
+    np.testing.assert_allclose(got.reshape(-1), K @ (mu.reshape(-1) / (K @ np.ones(g.V))), rtol=1e-12)
+
+
+def test_jko_conserves_mass_at_convergence_and_is_equivariant():
+    w = (1.0, math.sqrt(10), math.sqrt(2))
+    g = oracle.Grid(6, 6, 4, 2, w, 0.2)
+    mu = _inputs(g, 1, 33)[0] * g.V
+    out, st = oracle.jko_log(g, mu, 0.05, 5.0, 2, 300)
+    assert st["viol"] < 1e-12
+    np.testing.assert_allclose(out.sum(), mu.sum(), rtol=1e-11)
+    gp = oracle.Grid(8, 8, 8, 2, w, 0.05)
+    mu = _inputs(gp, 1, 34)[0] * gp.V
+    base, _ = oracle.jko_log(gp, mu, 0.05, 5.0, 2, 10)
+    np.testing.assert_allclose(oracle.jko_log(gp, refmath.rot90(mu), 0.05, 5.0, 2, 10)[0], refmath.rot90(base), rtol=1e-11)
+    np.testing.assert_allclose(oracle.jko_log(gp, refmath.mirror_y(mu), 0.05, 5.0, 2, 10)[0], refmath.mirror_y(base),
+                               rtol=1e-11)
