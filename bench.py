@@ -52,6 +52,10 @@ def inputs(problem=0):
 W2_WORKLOAD = ("entropic two-marginal transport (Sec. 4.1) between the first 2 of those measures, 128x128x16 "
                "SE(2) grid, kernel 21x21x16 (r=10), w=(1,3,0.5), eps=1e-4, 500 Sinkhorn iterations, then the "
                "plan cost <rho_b^2, pi> through the cost-weighted kernel, FP32 log-domain path")
+JKO = dict(tau=1e-3, m=5.0, steps=10, iters=50, eps=2e-3,
+           workload="10 entropic JKO steps (50 scaling iterations each) of the porous-medium energy (m=5), "
+                    "tau=1e-3, 128x128x16 SE(2) grid, kernel 21x21x16 (r=10), w=(1,sqrt(10),sqrt(2)), eps=2e-3, "
+                    "FP32 log-domain path")
 # Other workloads (parity cases and scale points; not the headline line): `--config large` is the
 # 512^2 x 32 single solve, `--config batched` the 64 uneven interpolations.
 LARGE = dict(nx=512, ny=512, nt=32, r=15, eps=2e-5, n=3, iters=1000,
@@ -328,6 +332,29 @@ def run_gpu(args):
         def solve(e2e=False):
             _, st, _ = se2ot.se2ot_interpolate_batched(descs, mu0, mu1, ts, se2ot.solve_opts(iters), outs)
             return st[0]
+    elif args.config == "jko":
+        nx, ny, nt, r, eps, n = NX, NY, NT, R, JKO["eps"], 1
+        wj = (1.0, math.sqrt(10.0), math.sqrt(2.0))
+        mu_h = torch.from_numpy(np.ascontiguousarray(inputs(problem=rank)[0] * (nx * ny * nt) * 0.5))
+        iters = JKO["steps"] * (args.iters or JKO["iters"])
+        workload = JKO["workload"]
+        vox = nx * ny * nt
+        cfg = {"grid": [nx, ny, nt], "radius": r, "steps": JKO["steps"], "iterations": iters, "eps": eps,
+               "w": list(wj), "tau": JKO["tau"], "m": JKO["m"]}
+        k = se2ot.se2ot_kernel_build(se2ot.make_desc(nx, ny, nt, r, wj, eps))
+        mu = mu_h.to(device)
+        out = torch.empty_like(mu)
+        mu_pin = mu_h.pin_memory()
+        out_pin = torch.empty(mu_h.shape, dtype=torch.float32).pin_memory()
+        timed_conv = False
+
+        def solve(e2e=False):
+            o = se2ot.solve_opts(iters // JKO["steps"])
+            if e2e:
+                _, st, _ = se2ot.se2ot_jko(k, mu_pin, JKO["tau"], JKO["m"], JKO["steps"], o, out_pin)
+            else:
+                _, st, _ = se2ot.se2ot_jko(k, mu, JKO["tau"], JKO["m"], JKO["steps"], o, out)
+            return st
     elif args.config == "w2":
         nx, ny, nt, r, eps, n = NX, NY, NT, R, EPS, 2
         mu_h = torch.from_numpy(np.ascontiguousarray(inputs(problem=rank)[:2]))
@@ -429,7 +456,10 @@ def run_gpu(args):
             "gpu_launches": int(launches),
             "solve": {"mass": mass, "viol": viol, "redo_outputs_timed": int(redo)},
         }
-        if args.config == "w2":
+        if args.config == "jko":
+            result["e2e"] = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(vox * 4),
+                             "d2h_bytes_per_step": int(vox * 4)}
+        elif args.config == "w2":
             result["solve"].update({"cost": st["cost"], "dual": st["dual"]})
             result["e2e"] = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(2 * vox * 4),
                              "d2h_bytes_per_step": 40}
@@ -516,7 +546,7 @@ def main(argv=None):
                     help="Sinkhorn iterations per solve (profiling runs only; default: the workload's)")
     ap.add_argument("--rate", type=float, default=0.0, help="serve: Poisson arrival rate (req/s)")
     ap.add_argument("--requests", type=int, default=0, help="serve: number of requests")
-    ap.add_argument("--config", default="barycenter", choices=["barycenter", "large", "batched", "serve", "w2"],
+    ap.add_argument("--config", default="barycenter", choices=["barycenter", "large", "batched", "serve", "w2", "jko"],
                     help="workload: the 128^2x16 barycenter (default, the headline), the 512^2x32 "
                          "large solve, or the 64-problem uneven batch")
     args = ap.parse_args(argv)

@@ -206,6 +206,22 @@ typedef struct {
 SE2OT_API se2ot_status se2ot_w2(se2ot_kernel k, const float *mu, const float *nu, const se2ot_solve_opts *opts,
                                 se2ot_w2_result *res, void *stream);
 
+/* Entropic JKO steps of the porous-medium energy F(mu) = sum_g mu(g)^m / (m - 1) (unit Haar weight
+ * per voxel; Sec. 2.2 Eq. (GF_JKO), Sec. 6.4): steps x
+ *   mu_{k+1} = argmin_nu W_eps(mu_k, nu) + tau F(nu)
+ * by the scaling iterations of Sec. 4.1 with the marginal constraint on the first marginal and
+ * the KL-proximal map of tau F on the second, opts->max_iters iterations per step from b = 1:
+ *   a = mu_k / (K * b),   b = prox_{(tau/eps) F}(K * a) / (K * a),   mu_{k+1} = prox(K * a).
+ * The prox solves log s + (tau/eps) m/(m-1) s^(m-1) = log z per voxel (Newton, FP64 result).
+ * mu0: V floats, caller layout, strictly positive (a zero density makes the b-update 0/0) and on
+ * the density scale F is meant for (no normalisation); mu_out: V floats; host or device memory.
+ * tau >= 0, m > 1, steps >= 1, opts->tol_viol must be 0.  stats: iters = steps * max_iters, mass =
+ * sum mu_out, viol = ||a (K * b) - mu_k||_1 / ||mu_k||_1 of the last step (FP64).  Workspace as for
+ * a 2-measure barycenter.  Synchronises the stream.  EINVAL for invalid arguments, ENONFINITE for a
+ * non-finite iterate. */
+SE2OT_API se2ot_status se2ot_jko(se2ot_kernel k, const float *mu0, double tau, double m, int steps,
+                                 const se2ot_solve_opts *opts, float *mu_out, se2ot_stats *stats, void *stream);
+
 /* Lifting / projection helpers of the paper's experiments (Sec. 2.4, 6.2, 6.3).  Device pointers
  * only (EINVAL otherwise); arrays in the caller layout, orientation innermost; enqueued on
  * `stream`, no synchronisation.

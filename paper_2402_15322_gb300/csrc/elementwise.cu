@@ -136,6 +136,70 @@ __global__ void __launch_bounds__(256) update_kernel(float2 *lv, const float2 *l
     }
 }
 
+// log prox_{sigma F}(exp(lz)) for F = s^m / (m - 1), natural logs: u solves u + c e^{q u} = lz with
+// c = sigma m / (m - 1), q = m - 1 (the stationarity condition of sigma F(s) + KL(s | z)); the left
+// side is increasing and convex in u.  Newton in FP32, safeguarded by bisection on the bracket
+// [min(lz, alt) - 1 - |lz|, lz] (alt = log((|lz| + 1) / c) / q bounds c e^{q u} by |lz| + 1 at the
+// start; an overflowing exponential counts as f > 0), then three FP64 Newton steps from the FP32
+// root (quadratic convergence to the double root).  -inf (a zero density) stays -inf.
+__device__ double prox_log(double lz, double c, double q)
+{
+    if (!(lz > -INFINITY) || !(c > 0.0)) return lz;
+    const double alt = log((fabs(lz) + 1.0) / c) / q;
+    float uf = (float)fmin(lz, alt), lof = (float)(fmin(lz, alt) - 1.0 - fabs(lz)), hif = (float)lz;
+    const float cf = (float)c, qf = (float)q, lzf = (float)lz;
+    for (int it = 0; it < 80; ++it) {
+        const float e = cf * __expf(qf * uf);
+        const float f = uf + e - lzf;
+        if (f > 0.f) hif = uf;
+        else lof = uf;
+        float un = uf - f / (1.f + qf * e);
+        if (!(un > lof && un < hif)) un = 0.5f * (lof + hif);
+        const bool done = fabsf(un - uf) <= 1e-6f * (1.f + fabsf(un));
+        uf = un;
+        if (done) break;
+    }
+    double u = uf;
+    for (int it = 0; it < 3; ++it) {
+        const double e = c * exp(q * u);
+        u -= (u + e - lz) / (1.0 + q * e);
+    }
+    return u;
+}
+
+// One CTA per (convolution tile, orientation slice), 2 voxels per thread (as update_kernel).
+__global__ void __launch_bounds__(256) prox_kernel(const float2 *lq, float2 *lb, float2 *lu, double c, double q,
+                                                   int nx, int ny, float *tmax_b)
+{
+    constexpr int TX = TILE_X, TY = TILE_Y;
+    const long plane = (long)nx * ny;
+    const int t = blockIdx.z;
+    __shared__ float red[8];
+    float m = -INFINITY;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int e = threadIdx.x + 256 * k;
+        const int y = blockIdx.y * TY + e / TX, x = blockIdx.x * TX + e % TX;
+        if (y >= ny || x >= nx) continue;
+        const long g = (long)t * plane + (long)y * nx + x;
+        const double q2 = df_to_double(lq[g]);                    // -log2 K a
+        const double u = prox_log(-q2 * 0.69314718055994530942, c, q) * 1.44269504088896340736;
+        const float2 b = df_from_double(u + q2);
+        lb[g] = b;
+        lu[g] = df_from_double(u);
+        m = fmaxf(m, b.x);
+    }
+    if (!tmax_b) return;   // uniform
+#pragma unroll
+    for (int off = 16; off; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < 8; ++w) m = fmaxf(m, red[w]);
+        tmax_b[(long)t * gridDim.x * gridDim.y + blockIdx.y * gridDim.x + blockIdx.x] = m;
+    }
+}
+
 __global__ void finalize_kernel(const float2 *L, float *bary, long V, int nx, int ny, int nt)
 {
     for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < V; g += (long)gridDim.x * blockDim.x)
@@ -243,6 +307,14 @@ cudaError_t launch_update(float2 *lv, const float2 *ld, float2 *L, const Lambdas
 {
     dim3 g((nx + TILE_X - 1) / TILE_X, (ny + TILE_Y - 1) / TILE_Y, nt);
     update_kernel<<<g, 256, 0, s>>>(lv, ld, L, lam, n, nx, ny, nt, tmax_v);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prox(const float2 *lq, float2 *lb, float2 *lu, double sigma, double m, int nx, int ny, int nt,
+                        float *tmax_b, cudaStream_t s)
+{
+    dim3 g((nx + TILE_X - 1) / TILE_X, (ny + TILE_Y - 1) / TILE_Y, nt);
+    prox_kernel<<<g, 256, 0, s>>>(lq, lb, lu, sigma * m / (m - 1.0), m - 1.0, nx, ny, tmax_b);
     return cudaGetLastError();
 }
 

@@ -102,6 +102,12 @@ cudaError_t launch_finalize(const float2 *L, float *bary, int nx, int ny, int nt
 constexpr int STATS_BLOCKS = 256;
 cudaError_t launch_stats(const float2 *L, const float2 *ld, const Lambdas &lam, int n, long V, double *partial,
                          double *scal, cudaStream_t s);
+// JKO scaling step of the porous-medium energy (slice-major, one field): with lq = -log2(K a) (the
+// EPI_W output for a zero aux), u = log2 prox_{sigma F}(K a) for F = s^m / (m - 1) per voxel,
+// lb = u + lq (log2 b) and lu = u (log2 of the plan's second marginal); tmax_b (if not NULL) =
+// inner-tile maxima of lb (hi), as the update kernel writes them for lv.
+cudaError_t launch_prox(const float2 *lq, float2 *lb, float2 *lu, double sigma, double m, int nx, int ny, int nt,
+                        float *tmax_b, cudaStream_t s);
 // Two-marginal transport (slice-major base-2 logarithms, V voxels): lm = log2(a K b),
 // lc = log2(a cK b), lmu / lnu the marginals.  FP64, fixed order:
 //   scal[0] = sum 2^lc (transport cost), scal[1] = sum 2^lmu la + sum 2^lnu lb (log2 units, zero

@@ -143,6 +143,8 @@ struct se2ot_kernel_s {
     Taps ctaps;                                // cost-weighted taps (se2ot_w2), built on first use
     double cost_scale = 1.0;                   // their scale C0
     double *w2p = nullptr;                     // se2ot_w2 reductions: 5 * STATS_BLOCKS partials + 5 sums
+    float2 *zero = nullptr;                    // V zeros (se2ot_jko: the aux of the K a convolution)
+    size_t c_zero = 0;
     std::vector<cudaEvent_t> ev;
 };
 
@@ -285,7 +287,7 @@ se2ot_status se2ot_kernel_destroy(se2ot_kernel k)
     cudaDeviceSynchronize();
     void *ptrs[] = {k->taps.ltheta, k->taps.ls, k->taps.ls_lo, k->taps.lsrow, k->tmax, k->tmax2, k->lmu, k->lv, k->lw, k->ld, k->L, k->lf, k->h1, k->h2, k->hint_ws,
                     k->mu_stage, k->bary_stage, k->redo, k->counters, k->redo_total, k->partial, k->scal, k->ord, k->ctaps.ltheta, k->ctaps.ls,
-                    k->ctaps.ls_lo, k->ctaps.lsrow, k->w2p};
+                    k->ctaps.ls_lo, k->ctaps.lsrow, k->w2p, k->zero};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : k->ev) cudaEventDestroy(e);
@@ -674,6 +676,132 @@ se2ot_status se2ot_w2(se2ot_kernel k, const float *mu, const float *nu, const se
         return fail(SE2OT_ENONFINITE, "non-finite result (cost=%g, mass=%g, viol=%g)", res->cost, res->mass, res->viol);
     if (o.tol_viol > 0 && !converged && !(res->viol <= o.tol_viol))
         return fail(SE2OT_ENOTCONV, "viol=%g > tol=%g after %d iterations", res->viol, o.tol_viol, it);
+    return SE2OT_OK;
+}
+
+se2ot_status se2ot_jko(se2ot_kernel k, const float *mu0, double tau, double m, int steps, const se2ot_solve_opts *opts,
+                       float *mu_out, se2ot_stats *stats, void *stream)
+{
+    const auto wall0 = std::chrono::steady_clock::now();
+    if (!k || !mu0 || !mu_out) return fail(SE2OT_EINVAL, "NULL argument");
+    if (!(tau >= 0.0) || !std::isfinite(tau)) return fail(SE2OT_EINVAL, "tau=%g invalid", tau);
+    if (!(m > 1.0) || !std::isfinite(m)) return fail(SE2OT_EINVAL, "m=%g not > 1", m);
+    if (steps < 1) return fail(SE2OT_EINVAL, "steps=%d < 1", steps);
+    se2ot_solve_opts o = {100, 0, 0.0, SE2OT_FP32, 0};
+    if (opts) o = *opts;
+    if (o.max_iters < 1) return fail(SE2OT_EINVAL, "max_iters=%d < 1", o.max_iters);
+    if (o.precision != SE2OT_FP32) return fail(SE2OT_EINVAL, "precision=%d unsupported", o.precision);
+    if (o.tol_viol != 0.0) return fail(SE2OT_EINVAL, "tol_viol is not supported by se2ot_jko");
+    if (2.0 * k->V >= 2147483647.0) return fail(SE2OT_EINVAL, "V too large");
+    cudaStream_t s = (cudaStream_t)stream;
+    const long V = k->V;
+    se2ot_status st = ensure_solver_ws(k, 2);
+    if (st != SE2OT_OK) return st;
+    long long launches = 0;
+    if (!k->w2p) CK(cudaMalloc((void **)&k->w2p, (5 * STATS_BLOCKS + 5) * sizeof(double)), "cudaMalloc(sums)");
+    if (k->c_zero < (size_t)V) {
+        CK(grow(k->zero, k->c_zero, (size_t)V), "cudaMalloc(zeros)");
+        CK(cudaMemset(k->zero, 0, (size_t)V * sizeof(float2)), "cudaMemset(zeros)");
+    }
+    const float *mu_dev = mu0;
+    if (!is_device_ptr(mu0)) {
+        CK(grow(k->mu_stage, k->c_mus, (size_t)V), "cudaMalloc(mu stage)");
+        CK(cudaMemcpyAsync(k->mu_stage, mu0, (size_t)V * sizeof(float), cudaMemcpyHostToDevice, s), "cudaMemcpyAsync(mu0)");
+        mu_dev = k->mu_stage;
+    }
+    float *out_dev = mu_out;
+    const bool out_host = !is_device_ptr(mu_out);
+    if (out_host) {
+        CK(grow(k->bary_stage, k->c_bs, (size_t)V), "cudaMalloc(out stage)");
+        out_dev = k->bary_stage;
+    }
+    // workspace of a 2-measure solve: lmu[0] log2 mu_k, lmu[1] the next mu; lv[0] = lb, lv[1] = la;
+    // lw[0] = -log2 K a, lw[1] = log2 a K b (statistics); h1 / h2 the two convolutions' shifts
+    CK(launch_init(mu_dev, k->lmu, k->lv, k->h1, k->h2, 1, k->d.nx, k->d.ny, k->d.ntheta, s), "init launch");
+    ++launches;
+    float2 *lmu = k->lmu, *lnext = k->lmu + V, *lb = k->lv, *la = k->lv + V, *lq = k->lw, *lm = k->lw + V;
+    const bool fused_max = k->d.boundary == SE2OT_BOUNDARY_ZERO;
+    const long ntile = (long)k->d.ntheta * conv_tiles(k->d.nx, k->d.ny);
+    CK(cudaMemsetAsync(k->redo_total, 0, 2 * sizeof(unsigned long long), s), "cudaMemsetAsync");
+    // a = mu_k / (K b)
+    ConvArgs A = conv_args(k, 1, EPI_W);
+    A.in = lb;
+    A.hint = k->h1;
+    A.out2 = la;
+    A.tmax_ready = fused_max;
+    A.tmax_out = fused_max ? k->tmax2 : nullptr;
+    A.order = k->ord;
+    A.cost = k->ord + ntile;
+    A.done = k->ord + 4 * ntile;
+    // lq = 0 - log2 (K a)
+    ConvArgs B = conv_args(k, 1, EPI_W);
+    B.in = la;
+    B.hint = k->h2;
+    B.aux = k->zero;
+    B.out2 = lq;
+    B.tmax = k->tmax2;
+    B.tmax_w = k->tmax2;
+    B.tmax_ready = fused_max;
+    B.order = k->ord + 2 * ntile;
+    B.cost = k->ord + 3 * ntile;
+    B.done = k->ord + 4 * ntile + 1;
+    CK(launch_order_init(A.order, A.cost, A.done, ntile, s), "order init");
+    CK(launch_order_init(B.order, B.cost, B.done, ntile, s), "order init");
+    launches += 2;
+    double h[5] = {0, 0, 0, 0, 0};
+    for (int step = 0; step < steps; ++step) {
+        // b = 1 at the start of every step: lb = 0, its tile maxima 0, the shift of K 1 near 0
+        CK(cudaMemsetAsync(lb, 0, (size_t)V * sizeof(float2), s), "cudaMemsetAsync(lb)");
+        CK(cudaMemsetAsync(k->h1, 0, (size_t)V * sizeof(float), s), "cudaMemsetAsync(hint)");
+        if (fused_max) CK(cudaMemsetAsync(k->tmax, 0, ntile * sizeof(float), s), "cudaMemsetAsync(tmax)");
+        A.aux = lmu;
+        for (int it = 0; it < o.max_iters; ++it) {
+            st = run_conv(k, A, s, &launches);
+            if (st == SE2OT_OK) st = run_conv(k, B, s, &launches);
+            if (st != SE2OT_OK) return st;
+            CK(launch_prox(lq, lb, lnext, tau / k->d.eps, m, k->d.nx, k->d.ny, k->d.ntheta,
+                           fused_max ? k->tmax : nullptr, s), "prox launch");
+            ++launches;
+        }
+        if (step == steps - 1) {
+            // first-marginal violation of the last step, and the mass of the result
+            ConvArgs M = conv_args(k, 1, EPI_D);
+            M.in = lb;
+            M.hint = k->h1;
+            M.aux = la;
+            M.out2 = lm;
+            M.tmax_ready = fused_max;
+            st = run_conv(k, M, s, &launches);
+            if (st != SE2OT_OK) return st;
+            CK(launch_w2_stats(la, lb, lm, lnext, lmu, lmu, V, k->w2p, k->w2p + 5 * STATS_BLOCKS, s), "stats launch");
+            launches += 2;
+        }
+        std::swap(lmu, lnext);
+    }
+    CK(launch_finalize(lmu, out_dev, k->d.nx, k->d.ny, k->d.ntheta, s), "finalize launch");
+    ++launches;
+    if (out_host)
+        CK(cudaMemcpyAsync(mu_out, out_dev, (size_t)V * sizeof(float), cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync(out)");
+    unsigned long long counts[2] = {0, 0};
+    CK(cudaMemcpyAsync(h, k->w2p + 5 * STATS_BLOCKS, sizeof h, cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync(stats)");
+    CK(cudaMemcpyAsync(counts, k->redo_total, sizeof counts, cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync(counters)");
+    CK(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    k->last_n = 0;
+    const double mass = h[0], viol = h[3] / h[4];
+    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - wall0).count();
+    if (stats) {
+        std::memset(stats, 0, sizeof *stats);
+        stats->iters = steps * o.max_iters;
+        stats->mass = mass;
+        stats->viol = viol;
+        stats->ms = ms;
+        stats->voxel_iters_per_s = ms > 0 ? (double)V * steps * o.max_iters / (ms * 1e-3) : 0.0;
+        stats->kernel_launches = launches;
+        stats->redo_outputs = (long long)counts[0];
+        stats->evaluated_terms = (long long)counts[1];
+    }
+    if (!std::isfinite(mass) || !std::isfinite(viol))
+        return fail(SE2OT_ENONFINITE, "non-finite iterate (mass=%g, viol=%g)", mass, viol);
     return SE2OT_OK;
 }
 

@@ -93,6 +93,7 @@ def lib():
     L.se2ot_state_export.argtypes = [vp, i, vp, vp, vp, vp]
     L.se2ot_w2.argtypes = [vp, vp, vp, ctypes.POINTER(se2ot_solve_opts), ctypes.POINTER(se2ot_w2_result), vp]
     L.se2ot_project.argtypes = [vp, vp, i, i, i, i, vp]
+    L.se2ot_jko.argtypes = [vp, vp, d, d, i, ctypes.POINTER(se2ot_solve_opts), vp, ctypes.POINTER(se2ot_stats), vp]
     L.se2ot_lift_field.argtypes = [vp, vp, i, i, i, vp]
     L.se2ot_reconstruct_field.argtypes = [vp, vp, i, i, i, vp]
     L.se2ot_interpolate_signed.argtypes = [vp, vp, vp, d, ctypes.POINTER(se2ot_solve_opts), vp,
@@ -268,6 +269,20 @@ def se2ot_w2(kernel, mu, nu, opts=None, stream=None, raise_on_error=True):
     if raise_on_error:
         _check(status)
     return res.as_dict(), status
+
+
+def se2ot_jko(kernel, mu0, tau, m, steps, opts=None, out=None, stream=None, raise_on_error=True):
+    """`steps` entropic JKO steps of the porous-medium energy sum mu^m / (m - 1) from mu0 [ny, nx, nt]
+    (opts.max_iters scaling iterations per step).  Returns (mu, stats dict, status)."""
+    if out is None:
+        out = torch.empty_like(mu0)
+    st = se2ot_stats()
+    status = lib().se2ot_jko(kernel.handle, _ptr(mu0, torch.float32), float(tau), float(m), int(steps),
+                             ctypes.byref(opts if opts is not None else solve_opts()), _ptr(out, torch.float32),
+                             ctypes.byref(st), _stream(stream))
+    if raise_on_error:
+        _check(status)
+    return out, st.as_dict(), status
 
 
 def se2ot_project(U, stream=None):

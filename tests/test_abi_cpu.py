@@ -78,6 +78,7 @@ def test_null_arguments_are_rejected(lib):
     assert lib.se2ot_barycenter(None, 2, None, None, None, None, None, None) == se2ot.SE2OT_EINVAL
     assert lib.se2ot_w2(None, None, None, None, None, None) == se2ot.SE2OT_EINVAL
     assert lib.se2ot_project(None, None, 1, 4, 4, 4, None) == se2ot.SE2OT_EINVAL
+    assert lib.se2ot_jko(None, None, 0.1, 5.0, 1, None, None, None, None) == se2ot.SE2OT_EINVAL
     assert lib.se2ot_lift_field(None, None, 4, 4, 4, None) == se2ot.SE2OT_EINVAL
     assert lib.se2ot_reconstruct_field(None, None, 4, 4, 4, None) == se2ot.SE2OT_EINVAL
     assert lib.se2ot_interpolate_signed(None, None, None, 0.5, None, None, None, None) == se2ot.SE2OT_EINVAL
