@@ -63,6 +63,7 @@ __global__ void __launch_bounds__(256) tile_max_kernel(ConvArgs a)
 __global__ void redo_kernel(ConvArgs a0, const ConvArgs *probs)
 {
     const unsigned n = *a0.redo_count;
+    if (a0.redo_clear && blockIdx.x == 0 && threadIdx.x == 0) *a0.redo_clear = 0;
     const int lane = threadIdx.x & 31;
     const int wpb = blockDim.x >> 5;
     const long nwarps = (long)gridDim.x * wpb;

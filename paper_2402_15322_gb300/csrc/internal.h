@@ -42,6 +42,7 @@ struct ConvArgs {
     double out_scale;        // EPI_LOG_OUT: ln 2 for natural-log output
     int2 *redo_list;         // outputs to recompute exactly: (problem, slice-major flat index)
     unsigned *redo_count;    // entries in redo_list
+    unsigned *redo_clear;    // if not NULL: set to 0 by the recompute pass (the counter of the next launch)
     unsigned long long *redo_total;  // running total for statistics
     unsigned long long *eval_count;  // kernel terms evaluated (not skipped)
     // Launch order of the tiles (single-problem launches, optional): CTA k computes tile order[k]

@@ -130,7 +130,8 @@ struct se2ot_kernel_s {
     size_t c_h1 = 0, c_h2 = 0, c_mus = 0, c_bs = 0;
     int2 *redo = nullptr;
     size_t c_redo = 0;
-    unsigned *counters = nullptr;           // [0] redo count
+    unsigned *counters = nullptr;           // [0], [1] redo counts, used alternately (see run_conv)
+    int phase = 0;                          // the counter the next convolution appends to
     unsigned long long *redo_total = nullptr;   // [0] redo outputs, [1] evaluated warp-slices
     float *hint_ws = nullptr;
     size_t c_hint_ws = 0;
@@ -214,11 +215,25 @@ ConvArgs conv_args(se2ot_kernel k, int batch, int epi)
     return a;
 }
 
-// One convolution plus its exact-recompute pass; 3 stream operations (memset, conv, redo).
-se2ot_status run_conv(se2ot_kernel k, const ConvArgs &a, cudaStream_t s, long long *launches,
+// Both recompute counters to 0 and the first one next: once per call of an entry point, so that a
+// failed earlier call leaves nothing behind.
+se2ot_status reset_counters(se2ot_kernel k, cudaStream_t s)
+{
+    CK(cudaMemsetAsync(k->counters, 0, 2 * sizeof(unsigned), s), "cudaMemsetAsync(redo counts)");
+    k->phase = 0;
+    return SE2OT_OK;
+}
+
+// One convolution plus its exact-recompute pass.  The recompute counters alternate: this launch
+// appends to counters[phase] (0 since reset_counters or the previous recompute pass) and its
+// recompute pass clears the other one for the next launch, so no memset runs between launches.
+se2ot_status run_conv(se2ot_kernel k, const ConvArgs &a0, cudaStream_t s, long long *launches,
                       cudaEvent_t t0 = nullptr, cudaEvent_t t1 = nullptr)
 {
-    CK(cudaMemsetAsync(k->counters, 0, sizeof(unsigned), s), "cudaMemsetAsync(redo count)");
+    ConvArgs a = a0;
+    a.redo_count = k->counters + k->phase;
+    a.redo_clear = k->counters + (1 - k->phase);
+    k->phase = 1 - k->phase;
     if (t0) CK(cudaEventRecord(t0, s), "cudaEventRecord");
     CK(launch_conv(a, s), "conv launch");
     if (t1) CK(cudaEventRecord(t1, s), "cudaEventRecord");
@@ -333,7 +348,8 @@ se2ot_status se2ot_apply(se2ot_kernel k, const float *f, float *out, int batch, 
     a.hint = k->hint_ws;
     a.out32 = out;
     CK(launch_conv_max(a, s), "conv max-pass launch");
-    return run_conv(k, a, s, nullptr);
+    se2ot_status rs = reset_counters(k, s);
+    return rs == SE2OT_OK ? run_conv(k, a, s, nullptr) : rs;
 }
 
 se2ot_status se2ot_apply_log(se2ot_kernel k, const double *lf, double *lout, int batch, void *stream)
@@ -356,7 +372,8 @@ se2ot_status se2ot_apply_log(se2ot_kernel k, const double *lf, double *lout, int
     a.out64 = lout;
     a.out_scale = LN2;
     CK(launch_conv_max(a, s), "conv max-pass launch");
-    return run_conv(k, a, s, nullptr);
+    se2ot_status rs = reset_counters(k, s);
+    return rs == SE2OT_OK ? run_conv(k, a, s, nullptr) : rs;
 }
 
 se2ot_status se2ot_barycenter(se2ot_kernel k, int n, const float *mu, const double *lambda,
@@ -388,6 +405,8 @@ se2ot_status se2ot_barycenter(se2ot_kernel k, int n, const float *mu, const doub
     const long V = k->V;
     const size_t nV = (size_t)n * V;
     se2ot_status st = ensure_solver_ws(k, n);
+    if (st != SE2OT_OK) return st;
+    st = reset_counters(k, s);
     if (st != SE2OT_OK) return st;
 
     // inputs: host or device
@@ -555,6 +574,8 @@ se2ot_status se2ot_w2(se2ot_kernel k, const float *mu, const float *nu, const se
     const long V = k->V;
     se2ot_status st = ensure_solver_ws(k, 2);
     if (st != SE2OT_OK) return st;
+    st = reset_counters(k, s);
+    if (st != SE2OT_OK) return st;
     long long launches = 0;
     if (!k->ctaps.ls) {
         const int D = 2 * k->d.radius + 1;
@@ -696,6 +717,8 @@ se2ot_status se2ot_jko(se2ot_kernel k, const float *mu0, double tau, double m, i
     cudaStream_t s = (cudaStream_t)stream;
     const long V = k->V;
     se2ot_status st = ensure_solver_ws(k, 2);
+    if (st != SE2OT_OK) return st;
+    st = reset_counters(k, s);
     if (st != SE2OT_OK) return st;
     long long launches = 0;
     if (!k->w2p) CK(cudaMalloc((void **)&k->w2p, (5 * STATS_BLOCKS + 5) * sizeof(double)), "cudaMalloc(sums)");
