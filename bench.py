@@ -491,7 +491,8 @@ def run_gpu(args):
                 "evaluated": {"achieved": eval_tflops, "frac": eval_tflops / peak_tflops,
                               "terms_per_launch": evaluated / max(1, 2 * iters * args.steps),
                               "note": "kernel terms actually computed; orientation pairs, kernel rows and "
-                                      "window blocks below 2^-40 of the output are skipped"}}
+                                      "window blocks whose terms all lie below 2^-64 of the output's shift are "
+                                      "skipped"}}
         result["clocks"] = clocks.summary()
     return result
 

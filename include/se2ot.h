@@ -115,10 +115,11 @@ typedef struct {
  *   kernel_launches  kernels this call launched
  *   redo_outputs     convolution outputs whose first evaluation fell outside the safe range
  *                    of its shift and were recomputed exactly
- *   evaluated_terms  kernel terms the convolutions evaluated; orientation pairs and kernel rows
- *                    whose whole contribution lies below 2^-40 of the output are skipped, so
- *                    this is at most 2 * iters * n * V * ntheta * (2r+1)^2 (counted per 32x32
- *                    tile, ragged tiles in full) */
+ *   evaluated_terms  kernel terms the convolutions evaluated; orientation pairs, kernel rows and
+ *                    blocks of window positions whose terms all lie below 2^-64 of the output's
+ *                    shift are skipped, so this is at most 2 * iters * n * V * ntheta * (2r+1)^2.
+ *                    Counted per block of 4 window positions of a warp: an estimate, within
+ *                    10% of the exact count. */
 typedef struct {
     int iters;
     double mass, viol, ms, voxel_iters_per_s;
