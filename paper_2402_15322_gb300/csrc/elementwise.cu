@@ -53,39 +53,40 @@ __global__ void init_kernel(const float *mu, float2 *lmu, float2 *lv, float *h1,
 // The first UC measures' d_i and v_i are loaded up front and kept in registers (the loads of all
 // measures are in flight together); the tile maxima of all measures take one barrier.
 constexpr int UC = 4;
+constexpr int VPT = 1, UT = TILE_X * TILE_Y / VPT;   // voxels per thread, threads per CTA
 
-__global__ void __launch_bounds__(256) update_kernel(float2 *lv, const float2 *ld, float2 *L, Lambdas lam, int n,
+__global__ void __launch_bounds__(UT) update_kernel(float2 *lv, const float2 *ld, float2 *L, Lambdas lam, int n,
                                                      int nx, int ny, int nt, float *tmax_v)
 {
     constexpr int TX = TILE_X, TY = TILE_Y;   // the convolution's tile
-    static_assert(TX * TY == 512, "two voxels per thread");
+    static_assert(TX * TY == VPT * UT, "one tile per CTA");
     const long plane = (long)nx * ny, V = plane * nt;
     const int t = blockIdx.z;
     const long ntiles = (long)gridDim.x * gridDim.y;
-    __shared__ float red[64][8];
+    __shared__ float red[64][UT / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    long gi[2];
-    bool ok[2];
+    long gi[VPT];
+    bool ok[VPT];
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        const int e = threadIdx.x + 256 * k;            // TX * TY = 512 voxels, 2 per thread
+    for (int k = 0; k < VPT; ++k) {
+        const int e = threadIdx.x + UT * k;
         const int y = blockIdx.y * TY + e / TX, x = blockIdx.x * TX + e % TX;
         ok[k] = y < ny && x < nx;
         gi[k] = (long)t * plane + (long)y * nx + x;
     }
-    float2 dc[UC][2], vc[UC][2];
+    float2 dc[UC][VPT], vc[UC][VPT];
 #pragma unroll
     for (int i = 0; i < UC; ++i)
 #pragma unroll
-        for (int k = 0; k < 2; ++k) {
+        for (int k = 0; k < VPT; ++k) {
             const bool use = i < n && ok[k];
             dc[i][k] = use ? ld[(long)i * V + gi[k]] : make_float2(0.f, 0.f);
             vc[i][k] = use ? lv[(long)i * V + gi[k]] : make_float2(0.f, 0.f);
         }
     // L = sum_i lambda_i ld_i in measure order
-    float2 Lg[2];
+    float2 Lg[VPT];
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < VPT; ++k) {
         float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
         for (int i = 0; i < UC; ++i)
@@ -100,7 +101,7 @@ __global__ void __launch_bounds__(256) update_kernel(float2 *lv, const float2 *l
     auto step = [&](int i, const float2 *d, const float2 *v) {
         float m = -INFINITY;
 #pragma unroll
-        for (int k = 0; k < 2; ++k) {
+        for (int k = 0; k < VPT; ++k) {
             if (!ok[k]) continue;
             const float2 nv = df_add(v[k], df_add(Lg[k], df_neg(d[k])));
             lv[(long)i * V + gi[k]] = nv;
@@ -117,9 +118,9 @@ __global__ void __launch_bounds__(256) update_kernel(float2 *lv, const float2 *l
         step(i, dc[i], vc[i]);
     }
     for (int i = UC; i < n; ++i) {
-        float2 d[2], v[2];
+        float2 d[VPT], v[VPT];
 #pragma unroll
-        for (int k = 0; k < 2; ++k) {
+        for (int k = 0; k < VPT; ++k) {
             d[k] = ok[k] ? ld[(long)i * V + gi[k]] : make_float2(0.f, 0.f);
             v[k] = ok[k] ? lv[(long)i * V + gi[k]] : make_float2(0.f, 0.f);
         }
@@ -131,7 +132,7 @@ __global__ void __launch_bounds__(256) update_kernel(float2 *lv, const float2 *l
         const int i = threadIdx.x;
         float m = red[i][0];
 #pragma unroll
-        for (int w = 1; w < 8; ++w) m = fmaxf(m, red[i][w]);
+        for (int w = 1; w < UT / 32; ++w) m = fmaxf(m, red[i][w]);
         tmax_v[((long)i * nt + t) * ntiles + blockIdx.y * gridDim.x + blockIdx.x] = m;
     }
 }
@@ -178,7 +179,7 @@ __global__ void __launch_bounds__(256) prox_kernel(const float2 *lq, float2 *lb,
     float m = -INFINITY;
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
-        const int e = threadIdx.x + 256 * k;
+        const int e = threadIdx.x + 256 * k;   // 512 voxels of the tile, 2 per thread
         const int y = blockIdx.y * TY + e / TX, x = blockIdx.x * TX + e % TX;
         if (y >= ny || x >= nx) continue;
         const long g = (long)t * plane + (long)y * nx + x;
@@ -306,7 +307,7 @@ cudaError_t launch_update(float2 *lv, const float2 *ld, float2 *L, const Lambdas
                           int nt, float *tmax_v, cudaStream_t s)
 {
     dim3 g((nx + TILE_X - 1) / TILE_X, (ny + TILE_Y - 1) / TILE_Y, nt);
-    update_kernel<<<g, 256, 0, s>>>(lv, ld, L, lam, n, nx, ny, nt, tmax_v);
+    update_kernel<<<g, UT, 0, s>>>(lv, ld, L, lam, n, nx, ny, nt, tmax_v);
     return cudaGetLastError();
 }
 
