@@ -58,7 +58,12 @@ __global__ void __launch_bounds__(256) tile_max_kernel(ConvArgs a)
     }
 }
 
-// Exact recomputation of queued outputs: one warp per output, FP64 terms, shift = largest term.
+// Recomputation of queued outputs: one warp per output, with the shift that keeps every term in
+// range, the largest term.  Pass 1 finds it (FP32 sums of the hi parts, good to ~1e-4 log2 units,
+// plenty for a shift); pass 2 evaluates every term as the tile kernel does, relative to the shift
+// folded with the orientation factor as a double-float, t = ((in_hi - S'_hi) + ls) + ((in_lo -
+// S'_lo) + ls_lo), with FP32 ex2 and an FP64 sum.  The largest term is ~2^0, so the sum needs no
+// window and the result c = S + log2(sum) is as precise as an output whose shift was right.
 // Entries are (problem, flat index); probs == NULL means every entry belongs to a0.
 __global__ void redo_kernel(ConvArgs a0, const ConvArgs *probs)
 {
@@ -70,42 +75,65 @@ __global__ void redo_kernel(ConvArgs a0, const ConvArgs *probs)
     for (long k = blockIdx.x * (long)wpb + (threadIdx.x >> 5); k < n; k += nwarps) {
         const int2 ent = a0.redo_list[k];
         const ConvArgs &a = probs ? probs[ent.x] : a0;
-        const int r = a.r, D = 2 * r + 1, nx = a.nx, ny = a.ny, nt = a.nt;
+        const int r = a.r, D = 2 * r + 1, DD = D * D, nx = a.nx, ny = a.ny, nt = a.nt;
         const long plane = (long)nx * ny;
-        const long T = (long)nt * D * D;
         const long flat = ent.y;
         const long bo = flat / plane, p = flat - bo * plane;
         const int b = (int)(bo / nt), o = (int)(bo - (long)b * nt);
         const int y = (int)(p / nx), x = (int)(p - (long)y * nx);
         const float2 *in_b = a.in + (long)b * nt * plane;
-        auto term = [&](long t) -> double {
-            const int i = (int)(t / (D * D));
-            const int rem = (int)(t - (long)i * D * D);
+        // input voxel of tap rem (dy, dx) of slice i, or -1 outside a zero-boundary grid
+        auto src = [&](int i, int rem) -> long {
             const int dyi = rem / D, dxi = rem - dyi * D;
             int sy = y - (dyi - r), sx = x - (dxi - r);
             if (a.periodic) {
                 sy = tile::wrapi(sy, ny);
                 sx = tile::wrapi(sx, nx);
             } else if (sy < 0 || sy >= ny || sx < 0 || sx >= nx) {
-                return -INFINITY;
+                return -1;
             }
-            const long ti = ((long)o * nt + i) * D * D + rem;
-            return df_to_double(in_b[(long)i * plane + (long)sy * nx + sx]) + df_to_double(a.ltheta[o * nt + i]) +
-                   ((double)a.ls[ti] + (double)a.ls_lo[ti]);
+            return (long)i * plane + (long)sy * nx + sx;
         };
-        double m = -INFINITY;
-        for (long t = lane; t < T; t += 32) m = fmax(m, term(t));
+        float m = -INFINITY;
+        bool bad = false;   // a +inf or NaN input
+        for (int i = 0; i < nt; ++i) {
+            const float lt = a.ltheta[o * nt + i].x;
+            const float *ls = a.ls + ((long)o * nt + i) * DD;
+            for (int rem = lane; rem < DD; rem += 32) {
+                const long g = src(i, rem);
+                if (g < 0) continue;
+                const float h = in_b[g].x;
+                bad |= !(h <= INFINITY) || h == INFINITY;
+                m = fmaxf(m, (h + lt) + ls[rem]);
+            }
+        }
 #pragma unroll
-        for (int off = 16; off; off >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
-        double s = 0.0;
-        if (isfinite(m))
-            for (long t = lane; t < T; t += 32) s += exp2(term(t) - m);
+        for (int off = 16; off; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+        bad = __any_sync(0xffffffffu, bad);
+        double sum = 0.0;
+        if (!bad && m > -INFINITY) {
+            for (int i = 0; i < nt; ++i) {
+                const float2 lt = a.ltheta[o * nt + i];
+                float shi, e;
+                two_sum(m, -lt.x, shi, e);
+                const float slo = e - lt.y;
+                const float *ls = a.ls + ((long)o * nt + i) * DD;
+                const float *ls_lo = a.ls_lo + ((long)o * nt + i) * DD;
+                for (int rem = lane; rem < DD; rem += 32) {
+                    const long g = src(i, rem);
+                    if (g < 0) continue;
+                    const float2 v = in_b[g];
+                    const float t = ((v.x - shi) + ls[rem]) + ((v.y - slo) + ls_lo[rem]);
+                    if (t > -160.f) sum += (double)tile::ex2(t);
+                }
+            }
+        }
 #pragma unroll
-        for (int off = 16; off; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+        for (int off = 16; off; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
         double c;
-        if (m == -INFINITY) c = -INFINITY;   // empty window: zero density
-        else if (!isfinite(m)) c = NAN;      // +inf or NaN input
-        else c = m + log2(s);
+        if (bad) c = NAN;                       // +inf or NaN input
+        else if (m == -INFINITY) c = -INFINITY;  // empty window: zero density
+        else c = (double)m + log2(sum);
         if (lane == 0) {
             const float2 cd = df_from_double(c);   // c as an exact-enough hi + lo pair
             tile::write_out(a, flat, b, o, y, x, make_float2(cd.x, 0.f), cd.y);
