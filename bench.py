@@ -17,6 +17,7 @@ import math
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -224,7 +225,9 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%d.csv" % os.getpid())
+        # the raw samples go to SE2OT_CLOCKS_DIR (default: the system's temporary directory)
+        out_dir = os.environ.get("SE2OT_CLOCKS_DIR", tempfile.gettempdir())
+        self.path = os.path.join(out_dir, "clocks_bench_%d.csv" % os.getpid())
 
     def __enter__(self):
         try:
