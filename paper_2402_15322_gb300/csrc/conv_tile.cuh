@@ -10,9 +10,10 @@
 // contribute (see skipping), the CTA stages slice i of the input halo ((TY + 2R) x (TX + 2R)
 // double-floats, split into an FP32 hi and a lo plane) and the (2R+1)^2 spatial taps of the pair
 // in shared memory, then each thread walks the rows of the window; the (2R+1)-tap row is fully
-// unrolled (R is a template parameter).  Staging is asynchronous (cp.async) and double-buffered:
-// the next contributing slice is copied while the current one is summed.  Halo cells outside the
-// grid (zero boundary) are set to 2^-inf once per CTA; the copies only write cells inside it.
+// unrolled (R is a template parameter).  Staging is asynchronous (cp.async) and, where shared
+// memory allows (stage_buffers), double-buffered: the next contributing slice is copied while the
+// current one is summed.  Halo cells outside the grid (zero boundary) are set to 2^-inf once per
+// CTA; the copies only write cells inside it.
 //
 // Shift and precision: output j of a thread is evaluated as
 //   S_j + log2 sum 2^t,  t = ((in_hi - S'_j,hi) + ls) + (in_lo - S'_j,lo),   S'_j = S_j - lt(o, i)
@@ -80,9 +81,19 @@ __host__ __device__ constexpr int stage_floats(int r)
     return 2 * (TY + 2 * r) * halo_pitch(TX + 2 * r) + (2 * r + 1) * tap_pitch(2 * r + 1);
 }
 
+// Staging buffers: two (the next slice is copied while the current one is summed) where six CTAs
+// with two buffers still fit in an SM's 228 KB of shared memory (1 KB reserved per CTA), one
+// otherwise: six resident CTAs (the register limit) hide more latency than the prefetch does
+// (at r = 15 two buffers would leave 4 CTAs per SM; measured 11% slower).
+__host__ __device__ constexpr size_t other_floats(int r) { return (size_t)(TY + 2 * r) + 8 + 4 * MAX_NT + 8; }
+__host__ __device__ constexpr int stage_buffers(int r)
+{
+    return 6 * ((2 * (size_t)stage_floats(r) + other_floats(r)) * 4 + 1024) <= 228 * 1024 ? 2 : 1;
+}
+
 __host__ __device__ constexpr size_t smem_floats(int r)
 {
-    return (size_t)2 * stage_floats(r) + (size_t)(TY + 2 * r) + 8 + 4 * MAX_NT + 8;
+    return (size_t)stage_buffers(r) * stage_floats(r) + other_floats(r);
 }
 
 __device__ __forceinline__ void cp_async4(float *dst, const float *src)
@@ -187,10 +198,10 @@ __global__ void __launch_bounds__(THREADS, 6) conv_tile_kernel(const ConvArgs a0
     constexpr int HX = TX + 2 * R, HY = TY + 2 * R, HXP = halo_pitch(HX), TP = tap_pitch(D);
     constexpr int WIN = XQ + 2 * R;        // window of one thread row: x' in [xl, xl + WIN)
     constexpr int WIN4 = (WIN + 3) / 4;
-    constexpr int SF = stage_floats(R);
+    constexpr int SF = stage_floats(R), NBUF = stage_buffers(R);
     // two staging buffers, each [HY][HXP] hi, [HY][HXP] lo, [D][TP] spatial taps of the pair
     extern __shared__ __align__(16) float smem[];
-    float *rowmax = smem + 2 * SF;         // [HY]
+    float *rowmax = smem + NBUF * SF;      // [HY]
     float *red = rowmax + HY;              // [THREADS / 32]
     float2 *lts = (float2 *)(red + 8);     // [nt] orientation factors lt(o, i)
     int *need = (int *)(lts + MAX_NT);     // [nt] slice i contributes
@@ -280,8 +291,8 @@ __global__ void __launch_bounds__(THREADS, 6) conv_tile_kernel(const ConvArgs a0
     // outside the grid, in both buffers
     for (int idx = tid; idx < D * (TP - D); idx += THREADS) {
         const int dy = idx / (TP - D), dx = D + idx - dy * (TP - D);
-        smem[2 * HY * HXP + dy * TP + dx] = -INFINITY;
-        smem[SF + 2 * HY * HXP + dy * TP + dx] = -INFINITY;
+#pragma unroll
+        for (int q = 0; q < NBUF; ++q) smem[q * SF + 2 * HY * HXP + dy * TP + dx] = -INFINITY;
     }
     if (!a.periodic && (x0 < R || y0 < R || x0 + TX + R > nx || y0 + TY + R > ny)) {
         for (int idx = tid; idx < HY * HX; idx += THREADS) {
@@ -289,7 +300,7 @@ __global__ void __launch_bounds__(THREADS, 6) conv_tile_kernel(const ConvArgs a0
             const int sy = y0 - R + hy, sx = x0 - R + hx;
             if (sy >= 0 && sy < ny && sx >= 0 && sx < nx) continue;
 #pragma unroll
-            for (int q = 0; q < 2; ++q) {
+            for (int q = 0; q < NBUF; ++q) {
                 smem[q * SF + hy * HXP + hx] = -INFINITY;
                 smem[q * SF + HY * HXP + hy * HXP + hx] = 0.f;
             }
@@ -332,16 +343,20 @@ __global__ void __launch_bounds__(THREADS, 6) conv_tile_kernel(const ConvArgs a0
         }
         cp_async_commit();
     };
-    if (nn > 0) stage(nlist[0], 0);
+    if (NBUF == 2 && nn > 0) stage(nlist[0], 0);
 
     unsigned rows_eval = 0;
     for (int qi = 0; qi < nn; ++qi) {
         const int i = nlist[qi];
         const float2 lt = lts[i];
-        const float *hhi = smem + (qi & 1) * SF, *hlo = hhi + HY * HXP, *ts = hlo + HY * HXP;
+        const float *hhi = smem + (NBUF == 2 ? (qi & 1) * SF : 0), *hlo = hhi + HY * HXP, *ts = hlo + HY * HXP;
+        if (NBUF == 1) {
+            __syncthreads();   // nobody reads slice qi - 1 any more
+            stage(i, 0);
+        }
         cp_async_wait_all();
         __syncthreads();   // slice qi has landed; nobody reads the other buffer (slice qi - 1) any more
-        if (qi + 1 < nn) stage(nlist[qi + 1], (qi + 1) & 1);
+        if (NBUF == 2 && qi + 1 < nn) stage(nlist[qi + 1], (qi + 1) & 1);
         if (!MAXPASS) {
             // row maxima of the staged halo: one warp per row, lanes across the row
             for (int hy = warp; hy < HY; hy += THREADS / 32) {
