@@ -178,9 +178,10 @@ __global__ void __launch_bounds__(THREADS, 6) conv_tile_kernel(const ConvArgs a0
                                                                const int4 *items)
 {
     int p = 0, bo, tx, ty;
-    unsigned tile_id = 0;   // single problem: (bo * tiles y + ty) * tiles x + tx
+    unsigned tile_id = 0;   // single problem: (bo * tiles y + ty) * tiles x + tx; batch: the item index
     if (BATCHED) {
-        const int4 it = items[blockIdx.x];
+        tile_id = a0.order ? a0.order[blockIdx.x] : blockIdx.x;
+        const int4 it = items[tile_id];
         p = it.x;
         bo = it.y;
         tx = it.z;
@@ -509,20 +510,20 @@ __global__ void __launch_bounds__(THREADS, 6) conv_tile_kernel(const ConvArgs a0
             a.tmax_out[((long)b * nt + o) * ntiles + ty * ntx + tx] = omax;
         }
     }
-    if (!BATCHED && a.order) {   // uniform over the CTA
+    if (a0.order) {   // uniform over the CTA (the launch order lives in a0 for a batch too)
         __shared__ int s_last;
         const unsigned total = gridDim.x * gridDim.y * gridDim.z;
         __syncthreads();
         if (tid == 0) {
-            a.cost[tile_id] = (unsigned)min(clock64() - t_start, 0xffffffffLL);
+            a0.cost[tile_id] = (unsigned)min(clock64() - t_start, 0xffffffffLL);
             __threadfence();
-            s_last = atomicAdd(a.done, 1u) == total - 1;
+            s_last = atomicAdd(a0.done, 1u) == total - 1;
         }
         __syncthreads();
         if (s_last) {
             __threadfence();
-            lpt_order(a.order, a.cost, total, nlist, need);
-            if (tid == 0) *a.done = 0;
+            lpt_order(a0.order, a0.cost, total, nlist, need);
+            if (tid == 0) *a0.done = 0;
         }
     }
 }

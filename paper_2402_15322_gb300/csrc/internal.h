@@ -45,10 +45,11 @@ struct ConvArgs {
     unsigned *redo_clear;    // if not NULL: set to 0 by the recompute pass (the counter of the next launch)
     unsigned long long *redo_total;  // running total for statistics
     unsigned long long *eval_count;  // kernel terms evaluated (not skipped)
-    // Launch order of the tiles (single-problem launches, optional): CTA k computes tile order[k]
-    // and records its duration in cost[tile]; the last CTA to finish (counted in *done, 0 between
-    // launches) writes into order the tiles by decreasing cost for the next launch with these
-    // arguments.  Any permutation gives the same results; heavy tiles first shortens the tail.
+    // Launch order (optional): CTA k computes tile (single problem) or work item (batch, taken from
+    // the shared arguments) order[k] and records its duration in cost[tile]; the last CTA to
+    // finish (counted in *done, 0 between launches) writes into order the tiles by decreasing
+    // cost for the next launch with these arguments.  Any permutation gives the same results;
+    // heavy tiles first shortens the tail.
     unsigned *order, *cost, *done;
     int nx, ny, nt, r, periodic, batch, epi;
 };
@@ -78,6 +79,9 @@ cudaError_t launch_conv_batch(int r, const ConvArgs &shared, const ConvArgs *pro
                               cudaStream_t s);
 cudaError_t launch_redo_batch(const ConvArgs &shared, const ConvArgs *probs, int max_blocks, cudaStream_t s);
 int conv_tiles(int nx, int ny);          // spatial tiles of one slice (size of tmax per slice)
+// Whether a convolution of `tiles` CTAs gets a heaviest-first launch order: only when the launch
+// has few waves (the one-CTA sort at its end would cost more than the shorter tail saves).
+inline bool conv_order_pays(long tiles) { return tiles <= 16L * 6 * 152; }
 // order[k] = k for k < count, cost = 0, *done = 0 (the identity launch order).
 cudaError_t launch_order_init(unsigned *order, unsigned *cost, unsigned *done, long count, cudaStream_t s);
 size_t conv_smem_bytes(int r);           // dynamic shared memory of one convolution CTA

@@ -235,6 +235,7 @@ extern "C" se2ot_status se2ot_barycenter_noalloc(const se2ot_kernel_desc *desc, 
     ad.done = ord + 4 * ntmax + 1;
     NCK(launch_order_init(aw.order, aw.cost, aw.done, (long)ntmax, s), "order init");
     NCK(launch_order_init(ad.order, ad.cost, ad.done, (long)ntmax, s), "order init");
+    if (!conv_order_pays((long)ntmax)) aw.order = ad.order = nullptr;
 
     int it = 0;
     bool converged = false;

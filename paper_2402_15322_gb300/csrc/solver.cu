@@ -464,6 +464,7 @@ se2ot_status se2ot_barycenter(se2ot_kernel k, int n, const float *mu, const doub
     ad.done = k->ord + 4 * ntile + 1;
     CK(launch_order_init(ad.order, ad.cost, ad.done, ntile, s), "order init");
     launches += 2;
+    if (!conv_order_pays(ntile)) aw.order = ad.order = nullptr;
     ad.in = k->lw;
     ad.hint = k->h2;
     ad.aux = k->lv;
@@ -631,6 +632,7 @@ se2ot_status se2ot_w2(se2ot_kernel k, const float *mu, const float *nu, const se
     CK(launch_order_init(A.order, A.cost, A.done, ntile, s), "order init");
     CK(launch_order_init(B.order, B.cost, B.done, ntile, s), "order init");
     launches += 2;
+    if (!conv_order_pays(ntile)) A.order = B.order = nullptr;
     // statistics: lm = log2(a (K * b)), lc = log2(a ((c / C0) K * b)) with its own max-pass shift
     ConvArgs M = conv_args(k, 1, EPI_D);
     M.in = lb;
@@ -771,6 +773,7 @@ se2ot_status se2ot_jko(se2ot_kernel k, const float *mu0, double tau, double m, i
     CK(launch_order_init(A.order, A.cost, A.done, ntile, s), "order init");
     CK(launch_order_init(B.order, B.cost, B.done, ntile, s), "order init");
     launches += 2;
+    if (!conv_order_pays(ntile)) A.order = B.order = nullptr;
     double h[5] = {0, 0, 0, 0, 0};
     for (int step = 0; step < steps; ++step) {
         // b = 1 at the start of every step: lb = 0, its tile maxima 0, the shift of K 1 near 0

@@ -119,6 +119,7 @@ void state_bind(SolveState &st, const se2ot_kernel_desc &d, int n, const double 
     st.ad.order = st.ord + 2 * ntile;
     st.ad.cost = st.ord + 3 * ntile;
     st.ad.done = st.ord + 4 * ntile + 1;
+    if (!conv_order_pays(ntile)) st.aw.order = st.ad.order = nullptr;
 }
 
 cudaError_t state_begin(SolveState &st, cudaStream_t s)
