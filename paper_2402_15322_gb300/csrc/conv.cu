@@ -67,6 +67,8 @@ __global__ void __launch_bounds__(256) tile_max_kernel(ConvArgs a)
 // Entries are (problem, flat index); probs == NULL means every entry belongs to a0.
 __global__ void redo_kernel(ConvArgs a0, const ConvArgs *probs)
 {
+    pdl_launch_dependents();
+    pdl_wait();
     const unsigned n = *a0.redo_count;
     if (a0.redo_clear && blockIdx.x == 0 && threadIdx.x == 0) *a0.redo_clear = 0;
     const int lane = threadIdx.x & 31;
@@ -192,8 +194,8 @@ cudaError_t launch_conv_max(const ConvArgs &a, cudaStream_t s) { return dispatch
 
 cudaError_t launch_redo(const ConvArgs &a, int max_blocks, cudaStream_t s)
 {
-    redo_kernel<<<max_blocks, 256, 0, s>>>(a, nullptr);
-    return cudaGetLastError();
+    PdlLaunch L(dim3(max_blocks), dim3(256), 0, s);
+    return cudaLaunchKernelEx(&L.cfg, redo_kernel, a, (const ConvArgs *)nullptr);
 }
 
 cudaError_t launch_conv_batch(int r, const ConvArgs &shared, const ConvArgs *probs, const int4 *items, int nitems,

@@ -177,6 +177,8 @@ template <int R, bool MAXPASS, bool BATCHED>
 __global__ void __launch_bounds__(THREADS, 6) conv_tile_kernel(const ConvArgs a0, const ConvArgs *probs,
                                                                const int4 *items)
 {
+    pdl_launch_dependents();
+    pdl_wait();   // everything below may read the previous kernel's results
     int p = 0, bo, tx, ty;
     unsigned tile_id = 0;   // single problem: (bo * tiles y + ty) * tiles x + tx; batch: the item index
     if (BATCHED) {
@@ -547,7 +549,9 @@ cudaError_t launch_tile(const ConvArgs &a, const ConvArgs *probs, const int4 *it
         if (nitems > 0) conv_tile_kernel<R, false, true><<<nitems, THREADS, smem, s>>>(a, probs, items);
     } else {
         dim3 grid((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY, a.batch * a.nt);
-        conv_tile_kernel<R, MAXPASS, false><<<grid, THREADS, smem, s>>>(a, nullptr, nullptr);
+        PdlLaunch L(grid, dim3(THREADS), smem, s);
+        return cudaLaunchKernelEx(&L.cfg, conv_tile_kernel<R, MAXPASS, false>, a, (const ConvArgs *)nullptr,
+                                  (const int4 *)nullptr);
     }
     return cudaGetLastError();
 }

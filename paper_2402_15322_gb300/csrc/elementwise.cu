@@ -60,6 +60,8 @@ __global__ void __launch_bounds__(UT) update_kernel(float2 *lv, const float2 *ld
 {
     constexpr int TX = TILE_X, TY = TILE_Y;   // the convolution's tile
     static_assert(TX * TY == VPT * UT, "one tile per CTA");
+    pdl_launch_dependents();
+    pdl_wait();
     const long plane = (long)nx * ny, V = plane * nt;
     const int t = blockIdx.z;
     const long ntiles = (long)gridDim.x * gridDim.y;
@@ -307,8 +309,8 @@ cudaError_t launch_update(float2 *lv, const float2 *ld, float2 *L, const Lambdas
                           int nt, float *tmax_v, cudaStream_t s)
 {
     dim3 g((nx + TILE_X - 1) / TILE_X, (ny + TILE_Y - 1) / TILE_Y, nt);
-    update_kernel<<<g, UT, 0, s>>>(lv, ld, L, lam, n, nx, ny, nt, tmax_v);
-    return cudaGetLastError();
+    PdlLaunch Lc(g, dim3(UT), 0, s);
+    return cudaLaunchKernelEx(&Lc.cfg, update_kernel, lv, ld, L, lam, n, nx, ny, nt, tmax_v);
 }
 
 cudaError_t launch_prox(const float2 *lq, float2 *lb, float2 *lu, double sigma, double m, int nx, int ny, int nt,

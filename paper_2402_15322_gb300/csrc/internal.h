@@ -62,6 +62,31 @@ struct Taps {
     float *lsrow = nullptr;    // [nt][nt][D]
 };
 
+// Programmatic dependent launch: a kernel of the solve loop lets the next one be scheduled while
+// it runs (launch_dependents, early) and waits for the previous grid's memory before touching
+// anything (wait).  Both are no-ops for a kernel launched without the attribute.
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// Launch configuration with programmatic stream serialisation (the next kernel of the stream may
+// start while this one finishes; it waits in pdl_wait).
+struct PdlLaunch {
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute attr[1];
+    PdlLaunch(dim3 grid, dim3 block, size_t smem, cudaStream_t s)
+    {
+        cfg = cudaLaunchConfig_t{};
+        cfg.gridDim = grid;
+        cfg.blockDim = block;
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = s;
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+    }
+};
+
 // Launchers (conv.cu / taps.cu).
 // cost = false: the Gibbs kernel K; true: the cost-weighted kernel (c / C0) K, c = rho_b^2, with
 // *cost_scale = C0 (a power of two >= every rho_b^2 of the window, so that every tap is <= 0)
