@@ -38,6 +38,8 @@ struct UpdArgs {
 // Batched form of the update kernel (elementwise.cu): item = (problem, tile x, tile y, slice).
 __global__ void __launch_bounds__(256) batch_update_kernel(const UpdArgs *args, const int4 *items)
 {
+    pdl_launch_dependents();
+    pdl_wait();
     const int4 it = items[blockIdx.x];
     const UpdArgs &u = args[it.x];
     const int nx = u.nx, ny = u.ny, nt = u.nt, t = it.w;
@@ -319,8 +321,8 @@ se2ot_status setup(BatchCtx &B, int nprob, const se2ot_kernel_desc *descs)
         ++launches;
     }
     if (e == cudaSuccess) {
-        batch_update_kernel<<<B.nuitems, 256, 0, B.cs>>>(B.dU, B.uitems);
-        e = cudaGetLastError();
+        PdlLaunch L(dim3(B.nuitems), dim3(256), 0, B.cs);
+        e = cudaLaunchKernelEx(&L.cfg, batch_update_kernel, (const UpdArgs *)B.dU, (const int4 *)B.uitems);
         ++launches;
     }
     cudaError_t e2 = cudaStreamEndCapture(B.cs, &g);

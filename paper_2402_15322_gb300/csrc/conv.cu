@@ -206,8 +206,8 @@ cudaError_t launch_conv_batch(int r, const ConvArgs &shared, const ConvArgs *pro
 
 cudaError_t launch_redo_batch(const ConvArgs &shared, const ConvArgs *probs, int max_blocks, cudaStream_t s)
 {
-    redo_kernel<<<max_blocks, 256, 0, s>>>(shared, probs);
-    return cudaGetLastError();
+    PdlLaunch L(dim3(max_blocks), dim3(256), 0, s);
+    return cudaLaunchKernelEx(&L.cfg, redo_kernel, shared, probs);
 }
 
 }  // namespace se2ot

@@ -546,7 +546,10 @@ cudaError_t launch_tile(const ConvArgs &a, const ConvArgs *probs, const int4 *it
     }
     if (items) {
         if (MAXPASS) return cudaErrorInvalidValue;   // batches never need the max pass
-        if (nitems > 0) conv_tile_kernel<R, false, true><<<nitems, THREADS, smem, s>>>(a, probs, items);
+        if (nitems > 0) {
+            PdlLaunch L(dim3(nitems), dim3(THREADS), smem, s);
+            return cudaLaunchKernelEx(&L.cfg, conv_tile_kernel<R, false, true>, a, probs, items);
+        }
     } else {
         dim3 grid((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY, a.batch * a.nt);
         PdlLaunch L(grid, dim3(THREADS), smem, s);
