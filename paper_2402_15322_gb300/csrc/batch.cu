@@ -304,6 +304,8 @@ se2ot_status setup(BatchCtx &B, int nprob, const se2ot_kernel_desc *descs)
     // record one Sinkhorn iteration of the whole batch as a graph (kernel attributes are set
     // before the capture: a zero-item launch only configures the kernel)
     ConvArgs shared = hW[0];
+    // the recompute pass of the w-line is followed by the first class's convolution of the d-line
+    shared.release_early = pdl_release_early(B.classes.empty() ? 0 : B.classes[0].second.second, B.sms);
     for (auto &c : B.classes) BCK(launch_conv_batch(c.first, shared, B.dW, B.items, 0, B.cs), "conv attributes");
     cudaGraph_t g = nullptr;
     BCK(cudaStreamBeginCapture(B.cs, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");

@@ -67,8 +67,10 @@ __global__ void __launch_bounds__(256) tile_max_kernel(ConvArgs a)
 // Entries are (problem, flat index); probs == NULL means every entry belongs to a0.
 __global__ void redo_kernel(ConvArgs a0, const ConvArgs *probs)
 {
-    pdl_launch_dependents();
+    // The next kernel is released before or after the wait for the convolution (pdl_release_early).
+    if (a0.release_early) pdl_launch_dependents();
     pdl_wait();
+    if (!a0.release_early) pdl_launch_dependents();
     const unsigned n = *a0.redo_count;
     if (a0.redo_clear && blockIdx.x == 0 && threadIdx.x == 0) *a0.redo_clear = 0;
     const int lane = threadIdx.x & 31;

@@ -56,12 +56,13 @@ constexpr int UC = 4;
 constexpr int VPT = 1, UT = TILE_X * TILE_Y / VPT;   // voxels per thread, threads per CTA
 
 __global__ void __launch_bounds__(UT) update_kernel(float2 *lv, const float2 *ld, float2 *L, Lambdas lam, int n,
-                                                     int nx, int ny, int nt, float *tmax_v)
+                                                     int nx, int ny, int nt, float *tmax_v, int release_early)
 {
     constexpr int TX = TILE_X, TY = TILE_Y;   // the convolution's tile
     static_assert(TX * TY == VPT * UT, "one tile per CTA");
-    pdl_launch_dependents();
+    if (release_early) pdl_launch_dependents();   // the next convolution (pdl_release_early)
     pdl_wait();
+    if (!release_early) pdl_launch_dependents();
     const long plane = (long)nx * ny, V = plane * nt;
     const int t = blockIdx.z;
     const long ntiles = (long)gridDim.x * gridDim.y;
@@ -306,11 +307,11 @@ cudaError_t launch_init(const float *mu, float2 *lmu, float2 *lv, float *h1, flo
 }
 
 cudaError_t launch_update(float2 *lv, const float2 *ld, float2 *L, const Lambdas &lam, int n, int nx, int ny,
-                          int nt, float *tmax_v, cudaStream_t s)
+                          int nt, float *tmax_v, bool release_early, cudaStream_t s)
 {
     dim3 g((nx + TILE_X - 1) / TILE_X, (ny + TILE_Y - 1) / TILE_Y, nt);
     PdlLaunch Lc(g, dim3(UT), 0, s);
-    return cudaLaunchKernelEx(&Lc.cfg, update_kernel, lv, ld, L, lam, n, nx, ny, nt, tmax_v);
+    return cudaLaunchKernelEx(&Lc.cfg, update_kernel, lv, ld, L, lam, n, nx, ny, nt, tmax_v, (int)release_early);
 }
 
 cudaError_t launch_prox(const float2 *lq, float2 *lb, float2 *lu, double sigma, double m, int nx, int ny, int nt,

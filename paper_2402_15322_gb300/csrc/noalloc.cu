@@ -211,6 +211,7 @@ extern "C" se2ot_status se2ot_barycenter_noalloc(const se2ot_kernel_desc *desc, 
     aw.r = desc->radius;
     aw.periodic = desc->boundary == SE2OT_BOUNDARY_PERIODIC;
     aw.batch = n;
+    aw.release_early = pdl_release_early((long)ntmax, sms);
     ConvArgs ad = aw;
     aw.epi = EPI_W;
     aw.in = lv;
@@ -246,7 +247,8 @@ extern "C" se2ot_status se2ot_barycenter_noalloc(const se2ot_kernel_desc *desc, 
             NCK(launch_redo(*a, 2 * sms, s), "redo launch");
             launches += fused_max ? 2 : 3;
         }
-        NCK(launch_update(lv, ld, L, lam, n, desc->nx, desc->ny, nt, fused_max ? tmax : nullptr, s), "update launch");
+        NCK(launch_update(lv, ld, L, lam, n, desc->nx, desc->ny, nt, fused_max ? tmax : nullptr, aw.release_early, s),
+            "update launch");
         ++launches;
         ++it;
         if (o.tol_viol > 0 && o.check_every > 0 && it % o.check_every == 0 && it < o.max_iters) {

@@ -212,6 +212,7 @@ ConvArgs conv_args(se2ot_kernel k, int batch, int epi)
     a.periodic = k->d.boundary == SE2OT_BOUNDARY_PERIODIC;
     a.batch = batch;
     a.epi = epi;
+    a.release_early = pdl_release_early((long)batch * k->d.ntheta * conv_tiles(k->d.nx, k->d.ny), k->sms);
     return a;
 }
 
@@ -482,7 +483,8 @@ se2ot_status se2ot_barycenter(se2ot_kernel k, int n, const float *mu, const doub
         if (st != SE2OT_OK) return st;
         st = run_conv(k, ad, s, &launches, e ? e[2] : nullptr, e ? e[3] : nullptr);
         if (st != SE2OT_OK) return st;
-        CK(launch_update(k->lv, k->ld, k->L, lam, n, k->d.nx, k->d.ny, k->d.ntheta, fused_max ? k->tmax : nullptr, s),
+        CK(launch_update(k->lv, k->ld, k->L, lam, n, k->d.nx, k->d.ny, k->d.ntheta, fused_max ? k->tmax : nullptr,
+                         aw.release_early, s),
            "update launch");
         ++launches;
         ++it;

@@ -93,6 +93,7 @@ void state_bind(SolveState &st, const se2ot_kernel_desc &d, int n, const double 
     a.r = d.radius;
     a.periodic = d.boundary == SE2OT_BOUNDARY_PERIODIC;
     a.batch = n;
+    a.release_early = pdl_release_early((long)n * d.ntheta * conv_tiles(d.nx, d.ny), sms);
     st.aw = a;
     st.ad = a;
     st.aw.epi = EPI_W;
@@ -144,7 +145,7 @@ cudaError_t state_iterate(SolveState &st, int iters, cudaStream_t s)
             if (e != cudaSuccess) return e;
         }
         cudaError_t e = launch_update(st.lv, st.ld, st.L, st.lam, st.n, st.d.nx, st.d.ny, st.d.ntheta,
-                                      st.fused_max ? st.tmax : nullptr, s);
+                                      st.fused_max ? st.tmax : nullptr, st.aw.release_early, s);
         if (e != cudaSuccess) return e;
         ++st.iters_done;
     }
