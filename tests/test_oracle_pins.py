@@ -219,6 +219,26 @@ def test_homogeneity_and_invariants():
         np.testing.assert_allclose(vKw, b.reshape(-1), rtol=1e-11)
 
 
+@pytest.mark.parametrize("iters", [1, 6])
+def test_haar_normalisation_of_the_kernel_leaves_the_barycenter_unchanged(iters):
+    """The oracle leaves out the voxel volume of the Haar measure (uniform dx dy dtheta weights).
+    Scaling K by any c > 0 sends w_i to w_i / c and leaves K w_i, d_i and mu unchanged, so the
+    oracle must equal the literal scaling iterations (Algorithm, Appendix A) run with the
+    Haar-weighted dense kernel c K, c = the voxel volume (1/nx)(1/ny)(2 pi/ntheta)."""
+    g = oracle.Grid(7, 6, 4, 2, W, 0.03)
+    mu = _inputs(g, 2, 21).reshape(2, -1)
+    lam = [0.35, 0.65]
+    K = _dense_K(g) * (1.0 / g.nx) * (1.0 / g.ny) * (2 * math.pi / g.nth)
+    v = np.ones_like(mu)
+    for _ in range(iters):
+        w = mu / (v @ K.T)                      # w_i = mu_i / (K v_i)
+        d = v * (w @ K.T)                       # d_i = v_i (K w_i)
+        bary = np.exp(sum(l * np.log(d[i]) for i, l in enumerate(lam)))
+        v = v * bary / d
+    np.testing.assert_allclose(oracle.barycenter_log(g, mu.reshape((2,) + g.shape), lam, iters).reshape(-1),
+                               bary, rtol=1e-11)
+
+
 def test_barycenter_equivariance():
     g = oracle.Grid(12, 12, 8, 3, W, 6e-3)
     mu = _inputs(g, 3, 5)
