@@ -47,9 +47,10 @@ struct ConvArgs {
     unsigned long long *eval_count;  // kernel terms evaluated (not skipped)
     // Launch order (optional): CTA k computes tile (single problem) or work item (batch, taken from
     // the shared arguments) order[k] and records its duration in cost[tile]; the last CTA to
-    // finish (counted in *done, 0 between launches) writes into order the tiles by decreasing
-    // cost for the next launch with these arguments.  Any permutation gives the same results;
-    // heavy tiles first shortens the tail.
+    // finish (counted in done[0], 0 between launches) writes into order the tiles by decreasing
+    // cost, on every LPT_EVERY-th launch with these arguments (counted in done[1]), for the
+    // launches that follow.  Any permutation gives the same results; heavy tiles first shortens
+    // the tail.
     unsigned *order, *cost, *done;
     int nx, ny, nt, r, periodic, batch, epi;
     int release_early;       // the recompute pass releases the next kernel before its wait (pdl_release_early)
@@ -116,7 +117,7 @@ inline bool conv_order_pays(long tiles) { return tiles <= 16L * 6 * 152; }
 // the 512-CTA launches of two-marginal transport, 128^2 x 16: 95 ms per 500 iterations with early
 // release, 69 ms without).
 inline bool pdl_release_early(long ctas, int sms) { return ctas > 6L * sms; }
-// order[k] = k for k < count, cost = 0, *done = 0 (the identity launch order).
+// order[k] = k for k < count, cost = 0, done[0] = done[1] = 0 (the identity launch order).
 cudaError_t launch_order_init(unsigned *order, unsigned *cost, unsigned *done, long count, cudaStream_t s);
 size_t conv_smem_bytes(int r);           // dynamic shared memory of one convolution CTA
 

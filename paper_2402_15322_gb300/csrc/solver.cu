@@ -139,7 +139,7 @@ struct se2ot_kernel_s {
     float *tmax = nullptr, *tmax2 = nullptr;   // tile maxima of lv (and apply inputs), of lw
     int last_n = 0;                            // measures of the last completed solve
     size_t c_tmax = 0, c_tmax2 = 0;
-    unsigned *ord = nullptr;                   // tile launch orders and costs of the two convolutions, 2 counters
+    unsigned *ord = nullptr;                   // tile launch orders and costs of the two convolutions, 2 counter pairs
     size_t c_ord = 0;
     Taps ctaps;                                // cost-weighted taps (se2ot_w2), built on first use
     double cost_scale = 1.0;                   // their scale C0
@@ -186,7 +186,7 @@ se2ot_status ensure_solver_ws(se2ot_kernel k, int n)
     CK(grow(k->redo, k->c_redo, nV), "cudaMalloc(redo)");
     CK(grow(k->tmax, k->c_tmax, (size_t)n * k->d.ntheta * conv_tiles(k->d.nx, k->d.ny)), "cudaMalloc(tmax)");
     CK(grow(k->tmax2, k->c_tmax2, (size_t)n * k->d.ntheta * conv_tiles(k->d.nx, k->d.ny)), "cudaMalloc(tmax)");
-    CK(grow(k->ord, k->c_ord, 4 * (size_t)n * k->d.ntheta * conv_tiles(k->d.nx, k->d.ny) + 2), "cudaMalloc(order)");
+    CK(grow(k->ord, k->c_ord, 4 * (size_t)n * k->d.ntheta * conv_tiles(k->d.nx, k->d.ny) + 4), "cudaMalloc(order)");
     return SE2OT_OK;
 }
 
@@ -462,7 +462,7 @@ se2ot_status se2ot_barycenter(se2ot_kernel k, int n, const float *mu, const doub
     ConvArgs ad = conv_args(k, n, EPI_D);
     ad.order = k->ord + 2 * ntile;
     ad.cost = k->ord + 3 * ntile;
-    ad.done = k->ord + 4 * ntile + 1;
+    ad.done = k->ord + 4 * ntile + 2;
     CK(launch_order_init(ad.order, ad.cost, ad.done, ntile, s), "order init");
     launches += 2;
     if (!conv_order_pays(ntile)) aw.order = ad.order = nullptr;
@@ -630,7 +630,7 @@ se2ot_status se2ot_w2(se2ot_kernel k, const float *mu, const float *nu, const se
     B.tmax_out = fused_max ? k->tmax : nullptr;
     B.order = k->ord + 2 * ntile;
     B.cost = k->ord + 3 * ntile;
-    B.done = k->ord + 4 * ntile + 1;
+    B.done = k->ord + 4 * ntile + 2;
     CK(launch_order_init(A.order, A.cost, A.done, ntile, s), "order init");
     CK(launch_order_init(B.order, B.cost, B.done, ntile, s), "order init");
     launches += 2;
@@ -771,7 +771,7 @@ se2ot_status se2ot_jko(se2ot_kernel k, const float *mu0, double tau, double m, i
     B.tmax_ready = fused_max;
     B.order = k->ord + 2 * ntile;
     B.cost = k->ord + 3 * ntile;
-    B.done = k->ord + 4 * ntile + 1;
+    B.done = k->ord + 4 * ntile + 2;
     CK(launch_order_init(A.order, A.cost, A.done, ntile, s), "order init");
     CK(launch_order_init(B.order, B.cost, B.done, ntile, s), "order init");
     launches += 2;

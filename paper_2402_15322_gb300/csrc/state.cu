@@ -41,7 +41,7 @@ void layout(SolveState &st, Carve &c)
     st.tmax = c.take<float>(ntm);
     st.tmax2 = c.take<float>(ntm);
     st.redo = c.take<int2>(nV);
-    st.ord = c.take<unsigned>(4 * ntm + 2);
+    st.ord = c.take<unsigned>(4 * ntm + 4);
     st.count = c.take<unsigned>(4);
     st.totals = c.take<unsigned long long>(2);
     st.partial = c.take<double>(2 * STATS_BLOCKS);
@@ -119,7 +119,7 @@ void state_bind(SolveState &st, const se2ot_kernel_desc &d, int n, const double 
     st.aw.done = st.ord + 4 * ntile;
     st.ad.order = st.ord + 2 * ntile;
     st.ad.cost = st.ord + 3 * ntile;
-    st.ad.done = st.ord + 4 * ntile + 1;
+    st.ad.done = st.ord + 4 * ntile + 2;
     if (!conv_order_pays(ntile)) st.aw.order = st.ad.order = nullptr;
 }
 
