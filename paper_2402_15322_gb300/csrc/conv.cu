@@ -174,7 +174,7 @@ cudaError_t launch_order_init(unsigned *order, unsigned *cost, unsigned *done, l
 {
     if (count > 0) order_init_kernel<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(order, cost, count);
     cudaError_t e = cudaGetLastError();
-    return e == cudaSuccess ? cudaMemsetAsync(done, 0, 2 * sizeof(unsigned), s) : e;
+    return e == cudaSuccess ? cudaMemsetAsync(done, 0, sizeof(unsigned), s) : e;
 }
 
 int conv_tiles(int nx, int ny) { return ((nx + tile::TX - 1) / tile::TX) * ((ny + tile::TY - 1) / tile::TY); }

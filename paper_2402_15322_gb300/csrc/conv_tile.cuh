@@ -141,11 +141,6 @@ __device__ __forceinline__ void write_out(const ConvArgs &a, long flat, int b, i
 // The tiles by decreasing cost (bucketed: NB buckets of equal width up to the largest cost,
 // arbitrary order within a bucket), by one CTA.  hist and cur hold NB ints of shared memory.
 constexpr int NB = 64;
-// The launch order is rebuilt on every LPT_EVERY-th launch with the same arguments, from that
-// launch's tile costs, and reused in between: the sort runs in the last CTA, on the launch's
-// critical path (about 10 us of a 100 us launch at 2048 tiles), while the tile costs of
-// consecutive Sinkhorn iterations differ little.
-constexpr unsigned LPT_EVERY = 8;
 __device__ __forceinline__ void lpt_order(unsigned *order, const unsigned *cost, unsigned total, int *hist, int *cur)
 {
     const int tid = threadIdx.x;
@@ -517,9 +512,8 @@ __global__ void __launch_bounds__(THREADS, 6) conv_tile_kernel(const ConvArgs a0
             a.tmax_out[((long)b * nt + o) * ntiles + ty * ntx + tx] = omax;
         }
     }
-    if (a0.order) {   // uniform over the CTA (the launch order lives in a0 for a batch too)
+    if (a0.order && a0.sort_order) {   // uniform over the CTA (the launch order lives in a0 for a batch too)
         __shared__ int s_last;
-        __shared__ unsigned s_epoch;
         const unsigned total = gridDim.x * gridDim.y * gridDim.z;
         __syncthreads();
         if (tid == 0) {
@@ -530,14 +524,8 @@ __global__ void __launch_bounds__(THREADS, 6) conv_tile_kernel(const ConvArgs a0
         __syncthreads();
         if (s_last) {
             __threadfence();
-            if (tid == 0) s_epoch = a0.done[1];
-            __syncthreads();
-            const unsigned epoch = s_epoch;   // the same in every thread: the sort's barriers are uniform
-            if (epoch % LPT_EVERY == 0) lpt_order(a0.order, a0.cost, total, nlist, need);
-            if (tid == 0) {
-                a0.done[1] = epoch + 1;
-                a0.done[0] = 0;
-            }
+            lpt_order(a0.order, a0.cost, total, nlist, need);
+            if (tid == 0) *a0.done = 0;
         }
     }
 }

@@ -46,12 +46,12 @@ struct ConvArgs {
     unsigned long long *redo_total;  // running total for statistics
     unsigned long long *eval_count;  // kernel terms evaluated (not skipped)
     // Launch order (optional): CTA k computes tile (single problem) or work item (batch, taken from
-    // the shared arguments) order[k] and records its duration in cost[tile]; the last CTA to
-    // finish (counted in done[0], 0 between launches) writes into order the tiles by decreasing
-    // cost, on every LPT_EVERY-th launch with these arguments (counted in done[1]), for the
-    // launches that follow.  Any permutation gives the same results; heavy tiles first shortens
-    // the tail.
+    // the shared arguments) order[k].  On a launch with sort_order set (order_sort_launch), every
+    // CTA also records its duration in cost[tile] and the last CTA to finish (counted in *done, 0
+    // between launches) writes into order the tiles by decreasing cost, for the launches that
+    // follow.  Any permutation gives the same results; heavy tiles first shortens the tail.
     unsigned *order, *cost, *done;
+    int sort_order;
     int nx, ny, nt, r, periodic, batch, epi;
     int release_early;       // the recompute pass releases the next kernel before its wait (pdl_release_early)
 };
@@ -109,6 +109,12 @@ int conv_tiles(int nx, int ny);          // spatial tiles of one slice (size of 
 // Whether a convolution of `tiles` CTAs gets a heaviest-first launch order: only when the launch
 // has few waves (the one-CTA sort at its end would cost more than the shorter tail saves).
 inline bool conv_order_pays(long tiles) { return tiles <= 16L * 6 * 152; }
+// Whether launch number `launch` (0, 1, ... with one set of arguments) rebuilds the launch order:
+// every 8th, from the first.  The sort runs in the last CTA, on the launch's critical path (about
+// 10 us of a 100 us launch at 2048 tiles), while the tile costs of consecutive Sinkhorn iterations
+// differ little (128^2 x 16 barycenter: 103.9 ms per solve sorting every launch, 96.4 every 8th,
+// 96.1 every 16th, 100.2 every 32nd).
+inline int order_sort_launch(long launch) { return launch % 8 == 0; }
 // Whether the kernels between two convolutions of `ctas` CTAs release their successor before
 // waiting for their predecessor (programmatic dependent launch).  Released early, the next
 // convolution's CTAs are placed while the current one still runs, onto whichever SMs have free
@@ -117,7 +123,7 @@ inline bool conv_order_pays(long tiles) { return tiles <= 16L * 6 * 152; }
 // the 512-CTA launches of two-marginal transport, 128^2 x 16: 95 ms per 500 iterations with early
 // release, 69 ms without).
 inline bool pdl_release_early(long ctas, int sms) { return ctas > 6L * sms; }
-// order[k] = k for k < count, cost = 0, done[0] = done[1] = 0 (the identity launch order).
+// order[k] = k for k < count, cost = 0, *done = 0 (the identity launch order).
 cudaError_t launch_order_init(unsigned *order, unsigned *cost, unsigned *done, long count, cudaStream_t s);
 size_t conv_smem_bytes(int r);           // dynamic shared memory of one convolution CTA
 

@@ -149,7 +149,7 @@ extern "C" se2ot_status se2ot_barycenter_noalloc(const se2ot_kernel_desc *desc, 
     dry.take<float>(nV);
     dry.take<float>(nV);
     dry.take<int2>(nV);
-    dry.take<unsigned>(4 * ntmax + 4);
+    dry.take<unsigned>(4 * ntmax + 2);
     dry.take<unsigned>(4);
     dry.take<unsigned long long>(2);
     dry.take<double>(2 * STATS_BLOCKS);
@@ -173,7 +173,7 @@ extern "C" se2ot_status se2ot_barycenter_noalloc(const se2ot_kernel_desc *desc, 
     float2 *L = c.take<float2>((size_t)V);
     float *h1 = c.take<float>(nV), *h2 = c.take<float>(nV);
     int2 *redo = c.take<int2>(nV);
-    unsigned *ord = c.take<unsigned>(4 * ntmax + 4);
+    unsigned *ord = c.take<unsigned>(4 * ntmax + 2);
     unsigned *count = c.take<unsigned>(4);
     unsigned long long *totals = c.take<unsigned long long>(2);
     double *partial = c.take<double>(2 * STATS_BLOCKS);
@@ -233,7 +233,7 @@ extern "C" se2ot_status se2ot_barycenter_noalloc(const se2ot_kernel_desc *desc, 
     aw.done = ord + 4 * ntmax;
     ad.order = ord + 2 * ntmax;
     ad.cost = ord + 3 * ntmax;
-    ad.done = ord + 4 * ntmax + 2;
+    ad.done = ord + 4 * ntmax + 1;
     NCK(launch_order_init(aw.order, aw.cost, aw.done, (long)ntmax, s), "order init");
     NCK(launch_order_init(ad.order, ad.cost, ad.done, (long)ntmax, s), "order init");
     if (!conv_order_pays((long)ntmax)) aw.order = ad.order = nullptr;
@@ -241,6 +241,7 @@ extern "C" se2ot_status se2ot_barycenter_noalloc(const se2ot_kernel_desc *desc, 
     int it = 0;
     bool converged = false;
     for (it = 0; it < o.max_iters;) {
+        aw.sort_order = ad.sort_order = order_sort_launch(it);
         for (const ConvArgs *a : {&aw, &ad}) {
             NCK(cudaMemsetAsync(count, 0, sizeof(unsigned), s), "cudaMemsetAsync");
             NCK(launch_conv(*a, s), "conv launch");

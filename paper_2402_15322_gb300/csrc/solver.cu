@@ -139,7 +139,7 @@ struct se2ot_kernel_s {
     float *tmax = nullptr, *tmax2 = nullptr;   // tile maxima of lv (and apply inputs), of lw
     int last_n = 0;                            // measures of the last completed solve
     size_t c_tmax = 0, c_tmax2 = 0;
-    unsigned *ord = nullptr;                   // tile launch orders and costs of the two convolutions, 2 counter pairs
+    unsigned *ord = nullptr;                   // tile launch orders and costs of the two convolutions, 2 counters
     size_t c_ord = 0;
     Taps ctaps;                                // cost-weighted taps (se2ot_w2), built on first use
     double cost_scale = 1.0;                   // their scale C0
@@ -186,7 +186,7 @@ se2ot_status ensure_solver_ws(se2ot_kernel k, int n)
     CK(grow(k->redo, k->c_redo, nV), "cudaMalloc(redo)");
     CK(grow(k->tmax, k->c_tmax, (size_t)n * k->d.ntheta * conv_tiles(k->d.nx, k->d.ny)), "cudaMalloc(tmax)");
     CK(grow(k->tmax2, k->c_tmax2, (size_t)n * k->d.ntheta * conv_tiles(k->d.nx, k->d.ny)), "cudaMalloc(tmax)");
-    CK(grow(k->ord, k->c_ord, 4 * (size_t)n * k->d.ntheta * conv_tiles(k->d.nx, k->d.ny) + 4), "cudaMalloc(order)");
+    CK(grow(k->ord, k->c_ord, 4 * (size_t)n * k->d.ntheta * conv_tiles(k->d.nx, k->d.ny) + 2), "cudaMalloc(order)");
     return SE2OT_OK;
 }
 
@@ -462,7 +462,7 @@ se2ot_status se2ot_barycenter(se2ot_kernel k, int n, const float *mu, const doub
     ConvArgs ad = conv_args(k, n, EPI_D);
     ad.order = k->ord + 2 * ntile;
     ad.cost = k->ord + 3 * ntile;
-    ad.done = k->ord + 4 * ntile + 2;
+    ad.done = k->ord + 4 * ntile + 1;
     CK(launch_order_init(ad.order, ad.cost, ad.done, ntile, s), "order init");
     launches += 2;
     if (!conv_order_pays(ntile)) aw.order = ad.order = nullptr;
@@ -479,6 +479,7 @@ se2ot_status se2ot_barycenter(se2ot_kernel k, int n, const float *mu, const doub
     bool converged = false;
     for (it = 0; it < max_it;) {
         cudaEvent_t *e = timing ? &k->ev[(size_t)4 * it] : nullptr;
+        aw.sort_order = ad.sort_order = order_sort_launch(it);
         st = run_conv(k, aw, s, &launches, e ? e[0] : nullptr, e ? e[1] : nullptr);
         if (st != SE2OT_OK) return st;
         st = run_conv(k, ad, s, &launches, e ? e[2] : nullptr, e ? e[3] : nullptr);
@@ -630,7 +631,7 @@ se2ot_status se2ot_w2(se2ot_kernel k, const float *mu, const float *nu, const se
     B.tmax_out = fused_max ? k->tmax : nullptr;
     B.order = k->ord + 2 * ntile;
     B.cost = k->ord + 3 * ntile;
-    B.done = k->ord + 4 * ntile + 2;
+    B.done = k->ord + 4 * ntile + 1;
     CK(launch_order_init(A.order, A.cost, A.done, ntile, s), "order init");
     CK(launch_order_init(B.order, B.cost, B.done, ntile, s), "order init");
     launches += 2;
@@ -670,6 +671,7 @@ se2ot_status se2ot_w2(se2ot_kernel k, const float *mu, const float *nu, const se
     int it = 0;
     bool converged = false;
     while (it < o.max_iters) {
+        A.sort_order = B.sort_order = order_sort_launch(it);
         st = run_conv(k, A, s, &launches);
         if (st == SE2OT_OK) st = run_conv(k, B, s, &launches);
         if (st != SE2OT_OK) return st;
@@ -771,7 +773,7 @@ se2ot_status se2ot_jko(se2ot_kernel k, const float *mu0, double tau, double m, i
     B.tmax_ready = fused_max;
     B.order = k->ord + 2 * ntile;
     B.cost = k->ord + 3 * ntile;
-    B.done = k->ord + 4 * ntile + 2;
+    B.done = k->ord + 4 * ntile + 1;
     CK(launch_order_init(A.order, A.cost, A.done, ntile, s), "order init");
     CK(launch_order_init(B.order, B.cost, B.done, ntile, s), "order init");
     launches += 2;
@@ -784,6 +786,7 @@ se2ot_status se2ot_jko(se2ot_kernel k, const float *mu0, double tau, double m, i
         if (fused_max) CK(cudaMemsetAsync(k->tmax, 0, ntile * sizeof(float), s), "cudaMemsetAsync(tmax)");
         A.aux = lmu;
         for (int it = 0; it < o.max_iters; ++it) {
+            A.sort_order = B.sort_order = order_sort_launch(it);   // each step starts from b = 1
             st = run_conv(k, A, s, &launches);
             if (st == SE2OT_OK) st = run_conv(k, B, s, &launches);
             if (st != SE2OT_OK) return st;

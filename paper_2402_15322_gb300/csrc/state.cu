@@ -41,7 +41,7 @@ void layout(SolveState &st, Carve &c)
     st.tmax = c.take<float>(ntm);
     st.tmax2 = c.take<float>(ntm);
     st.redo = c.take<int2>(nV);
-    st.ord = c.take<unsigned>(4 * ntm + 4);
+    st.ord = c.take<unsigned>(4 * ntm + 2);
     st.count = c.take<unsigned>(4);
     st.totals = c.take<unsigned long long>(2);
     st.partial = c.take<double>(2 * STATS_BLOCKS);
@@ -119,7 +119,7 @@ void state_bind(SolveState &st, const se2ot_kernel_desc &d, int n, const double 
     st.aw.done = st.ord + 4 * ntile;
     st.ad.order = st.ord + 2 * ntile;
     st.ad.cost = st.ord + 3 * ntile;
-    st.ad.done = st.ord + 4 * ntile + 2;
+    st.ad.done = st.ord + 4 * ntile + 1;
     if (!conv_order_pays(ntile)) st.aw.order = st.ad.order = nullptr;
 }
 
@@ -138,6 +138,7 @@ cudaError_t state_begin(SolveState &st, cudaStream_t s)
 cudaError_t state_iterate(SolveState &st, int iters, cudaStream_t s)
 {
     for (int it = 0; it < iters; ++it) {
+        st.aw.sort_order = st.ad.sort_order = order_sort_launch(st.iters_done);
         for (const ConvArgs *a : {&st.aw, &st.ad}) {
             cudaError_t e = cudaMemsetAsync(st.count, 0, sizeof(unsigned), s);
             if (e == cudaSuccess) e = launch_conv(*a, s);

@@ -21,7 +21,7 @@ struct SolveState {
     float2 *lmu = nullptr, *lv = nullptr, *lw = nullptr, *ld = nullptr, *L = nullptr;
     float *h1 = nullptr, *h2 = nullptr, *tmax = nullptr, *tmax2 = nullptr;
     int2 *redo = nullptr;
-    unsigned *ord = nullptr;        // tile launch orders and costs of the two convolutions, 2 counter pairs
+    unsigned *ord = nullptr;        // tile launch orders and costs of the two convolutions, 2 counters
     unsigned *count = nullptr;
     unsigned long long *totals = nullptr;
     double *partial = nullptr, *scal = nullptr;
