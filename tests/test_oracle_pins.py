@@ -8,6 +8,7 @@ import pytest
 import scipy.ndimage
 
 import oracle
+from paper_2402_15322_gb300 import synth
 from tests import refmath
 
 W = (1.0, 3.0, 0.5)
@@ -237,6 +238,31 @@ def test_haar_normalisation_of_the_kernel_leaves_the_barycenter_unchanged(iters)
         v = v * bary / d
     np.testing.assert_allclose(oracle.barycenter_log(g, mu.reshape((2,) + g.shape), lam, iters).reshape(-1),
                                bary, rtol=1e-11)
+
+
+@pytest.mark.parametrize("coupled,share", [(False, 0.5), (True, 0.01)])
+def test_max_scaled_reduced_precision_would_flush_outputs(coupled, share):
+    """At the regularisation of the 32^2 x 8 interpolation workload (r = 3, eps = 5e-4,
+    w = (1, 3, 0.5)) the log-potentials after 100 scaling updates (Appendix A) vary by more than
+    the whole exponent range of FP32 and BF16 inside one kernel window.  For a share of the
+    outputs of K v, every term lies below 2^-149 (FP32's smallest subnormal) times the largest
+    input in the output's window: a mantissa scaled by any per-slice, per-tile or per-window
+    maximum, in FP32 or BF16, flushes those outputs to zero.  (The log-domain result itself is
+    finite: out >= the largest term.)"""
+    g = oracle.Grid(32, 32, 8, 3, (1.0, 3.0, 0.5), 5e-4)
+    if coupled:
+        mu = synth.coupled_measures(2, 32, 32, 8, config_seed=1, max_shift=1, nbumps=4)
+    else:
+        mu = synth.measures(2, 32, 32, 8, config_seed=1, nbumps=4)
+    _, st = oracle.barycenter_log(g, mu, [0.5, 0.5], 100, want_state=True)
+    lv = st["lv"][0]
+    assert lv.max() - lv.min() > 88.72 + 87.34        # wider than FP32's normal range
+    out = oracle.conv_log(g, lv[None])[0]
+    assert np.isfinite(out).all()
+    D = 2 * g.r + 1
+    window_max = scipy.ndimage.maximum_filter(lv.max(axis=-1), size=(D, D), mode="constant",
+                                              cval=-np.inf)[..., None]
+    assert ((out - window_max) < -149 * math.log(2)).mean() > share
 
 
 def test_barycenter_equivariance():
