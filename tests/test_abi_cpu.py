@@ -83,3 +83,13 @@ def test_null_arguments_are_rejected(lib):
     assert lib.se2ot_reconstruct_field(None, None, 4, 4, 4, None) == se2ot.SE2OT_EINVAL
     assert lib.se2ot_interpolate_signed(None, None, None, 0.5, None, None, None, None) == se2ot.SE2OT_EINVAL
     assert lib.se2ot_kernel_destroy(None) == se2ot.SE2OT_OK
+
+
+def test_missing_library_fails_loudly(monkeypatch):
+    """No CPU fallback: without libse2ot.so every entry point raises instead of computing."""
+    monkeypatch.setattr(se2ot, "_LIB", None)
+    monkeypatch.setattr(se2ot, "LIB_PATH", os.path.join(build.ROOT, "no_such_dir", "libse2ot.so"))
+    with pytest.raises(ImportError):
+        se2ot.lib()
+    with pytest.raises(ImportError):
+        se2ot.se2ot_kernel_build(se2ot.make_desc(16, 16, 4, 2, (1.0, 3.0, 0.5), 1e-2))
