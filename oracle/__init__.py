@@ -23,7 +23,9 @@ _P = ctypes.POINTER(ctypes.c_double)
 def _lib():
     global _LIB
     if _LIB is None:
-        path = _build.build()
+        # SE2OT_ORACLE_LIB: a library built from a planted-mistake copy of the source, for the
+        # test that checks the pins catch such mistakes
+        path = os.environ.get("SE2OT_ORACLE_LIB") or _build.build()
         lib = ctypes.CDLL(path)
         lib.or_threads.restype = _I
         lib.or_group_mul.argtypes = [_P, _P, _P]

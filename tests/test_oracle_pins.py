@@ -122,6 +122,10 @@ def test_taps_identity_and_symmetry():
     # F[o][i](d) = F[i][o](-d)  <=>  k(u^-1) = k(u)
     np.testing.assert_allclose(lk, np.flip(np.transpose(lk, (1, 0, 2, 3)), axis=(2, 3)),
                                rtol=1e-12)
+    # rho_b^2 is even in the spatial offset (b1, b2 change sign with (x, y)), so F[o][i](d) =
+    # F[o][i](-d), and with the line above the tap table is symmetric in (o, i)
+    np.testing.assert_allclose(lk, np.flip(lk, axis=(2, 3)), rtol=1e-12)
+    np.testing.assert_allclose(lk, np.transpose(lk, (1, 0, 2, 3)), rtol=1e-12)
 
 
 @pytest.mark.parametrize("periodic", [False, True])
