@@ -1,5 +1,5 @@
 """The oracle's pins catch plausible mistakes: each case plants one mistake in a copy of the C
-oracle (a wrong sign, a dropped term, a swapped operand or index), builds it, and runs the pin
+oracle (a wrong sign, a dropped term or factor, a swapped operand or index), builds it, and runs the pin
 suites against it in a separate process, which must fail.  CPU only.
 
 Transposing the orientation pair (o, i) of a tap is not among them: it is not a mistake for
@@ -41,6 +41,13 @@ MUTANTS = [
     ("sign of the v-update", "lv[(size_t)i * V + g] += L[g] - ld[(size_t)i * V + g];",
      "lv[(size_t)i * V + g] += ld[(size_t)i * V + g] - L[g];"),
     ("uniform weights instead of lambda", "L[g] += lam[i] * ldi[g];", "L[g] += ldi[g] / n;"),
+    ("sign in the logarithm of rho_c", "double c1 = (p * x + q * y) / det;", "double c1 = (p * x - q * y) / det;"),
+    ("cost taps without 1/eps", "(c > 0.0 ? log(c) : -INFINITY) - c / eps;", "(c > 0.0 ? log(c) : -INFINITY) - c;"),
+    ("second marginal of W2 from mu", "lb[g] = log(nu[g]) - t[g];", "lb[g] = log(mu[g]) - t[g];"),
+    ("W2 dual without eps", "res[1] = eps * dual;", "res[1] = dual;"),
+    ("prox constant without m", "double c = sigma * m / (m - 1.0), q = m - 1.0;",
+     "double c = sigma / (m - 1.0), q = m - 1.0;"),
+    ("sign of the JKO b-update", "lb[g] = u[g] - t[g];", "lb[g] = u[g] + t[g];"),
 ]
 
 
