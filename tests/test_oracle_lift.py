@@ -3,14 +3,24 @@ mathematics fix: the field lift conserves |v| under the projection, the reconstr
 lift on bin-centred angles and quantises other angles to within half a bin, the lift commutes with
 a quarter turn of the plane, and the signed interpolation is odd in its inputs and reduces to a
 closed form for identical inputs (dense kernel matrix from the group law)."""
+import importlib.util
 import math
+import os
 
 import numpy as np
 import pytest
 
 import oracle
-from oracle import lift
 from tests import refmath
+
+if os.environ.get("SE2OT_ORACLE_LIFT"):
+    # a planted-mistake copy of oracle/lift.py, loaded in the oracle package (the mutation test)
+    _spec = importlib.util.spec_from_file_location("oracle._lift_under_test", os.environ["SE2OT_ORACLE_LIFT"])
+    lift = importlib.util.module_from_spec(_spec)
+    lift.__package__ = "oracle"
+    _spec.loader.exec_module(lift)
+else:
+    from oracle import lift
 
 RNG = np.random.default_rng(4242)
 W = (1.0, 3.0, 0.5)
@@ -81,3 +91,20 @@ def test_signed_interpolation_is_odd_and_has_the_identical_input_closed_form():
         phi = (K @ (nu.reshape(-1) / k1)).reshape(g.shape)
         want += sign * m * phi.sum(axis=-1)
     np.testing.assert_allclose(lift.interpolate_signed(g, U, U, 0.7, 5), want, rtol=1e-11, atol=1e-13)
+
+
+def test_signed_interpolation_at_t0_uses_the_first_inputs_masses():
+    """t = 0: the weights are (1, 0), so every barycenter iterate of a part is K(nu0 / K 1) (the
+    one-hot closed form of the scaling iterations), and the result is m0+ P(K(nu0+ / K 1)) -
+    m0- P(K(nu0- / K 1)) with the first input's part masses, whatever the second input is."""
+    g = oracle.Grid(6, 6, 4, 2, W, 0.05)
+    U = RNG.normal(size=g.shape)
+    V = 3.0 * RNG.normal(size=g.shape) + 0.5        # other part masses on the second side
+    K = _dense_K(g)
+    k1 = K @ np.ones(g.V)
+    want = np.zeros(g.shape[:2])
+    for part, sign in ((np.maximum(U, 0), 1.0), (-np.minimum(U, 0), -1.0)):
+        nu = part + 1e-6 * part.max()
+        nu = nu / nu.sum()
+        want += sign * part.sum() * (K @ (nu.reshape(-1) / k1)).reshape(g.shape).sum(axis=-1)
+    np.testing.assert_allclose(lift.interpolate_signed(g, U, V, 0.0, 6), want, rtol=1e-11, atol=1e-13)

@@ -12,6 +12,7 @@ import sys
 import pytest
 
 from oracle import build as oracle_build
+from oracle import lift as oracle_lift
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 PINS = [os.path.join(ROOT, "tests", "test_oracle_pins.py"), os.path.join(ROOT, "tests", "test_oracle_lift.py")]
@@ -62,6 +63,30 @@ def test_pins_catch_a_planted_mistake(tmp_path, name, old, new):
                     "-shared", str(mutant), "-o", str(lib), "-lm"], check=True)
     env = dict(os.environ, SE2OT_ORACLE_LIB=str(lib))
     run = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider"] + PINS,
+                         cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert run.returncode != 0, "no pin failed with the planted mistake: " + name
+    assert "failed" in run.stdout, run.stdout[-2000:]
+
+
+# the same for the lifting / projection oracle (Python): (name, exact text, planted replacement)
+LIFT_MUTANTS = [
+    ("lift bin by floor instead of rounding", "(2.0 * math.pi) + 0.5)) % nt", "(2.0 * math.pi))) % nt"),
+    ("half the reconstruction angle", "th = 2.0 * math.pi * k / nt", "th = math.pi * k / nt"),
+    ("negative part not negated", "up, um = np.maximum(U, 0.0), -np.minimum(U, 0.0)",
+     "up, um = np.maximum(U, 0.0), np.minimum(U, 0.0)"),
+    ("interpolated masses swapped", "b += sign * ((1.0 - t) * m0 + t * m1) * project(phi)",
+     "b += sign * (t * m0 + (1.0 - t) * m1) * project(phi)"),
+]
+
+
+@pytest.mark.parametrize("name,old,new", LIFT_MUTANTS, ids=[m[0] for m in LIFT_MUTANTS])
+def test_lift_pins_catch_a_planted_mistake(tmp_path, name, old, new):
+    src = open(oracle_lift.__file__).read()
+    assert src.count(old) == 1, "the planted line no longer matches the oracle source: " + name
+    mutant = tmp_path / "lift_mutant.py"
+    mutant.write_text(src.replace(old, new))
+    env = dict(os.environ, SE2OT_ORACLE_LIFT=str(mutant))
+    run = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", PINS[1]],
                          cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert run.returncode != 0, "no pin failed with the planted mistake: " + name
     assert "failed" in run.stdout, run.stdout[-2000:]
