@@ -49,6 +49,8 @@ MUTANTS = [
     ("prox constant without m", "double c = sigma * m / (m - 1.0), q = m - 1.0;",
      "double c = sigma / (m - 1.0), q = m - 1.0;"),
     ("sign of the JKO b-update", "lb[g] = u[g] - t[g];", "lb[g] = u[g] + t[g];"),
+    ("marginal violation without the weights", "viol += lam[i] * s;", "viol += s;"),
+    ("marginal violation not relative", "stats[1] = viol / mass;", "stats[1] = viol;"),
 ]
 
 

@@ -190,8 +190,11 @@ def test_one_hot_weights_closed_form(iters):
     mu = _inputs(g, 3, 7)
     want = K @ (mu[0].reshape(-1) / (K @ np.ones(g.V)))
     for fn in (oracle.barycenter_lin, oracle.barycenter_log):
-        got = fn(g, mu, [1.0, 0.0, 0.0], iters)
+        got, st = fn(g, mu, [1.0, 0.0, 0.0], iters, want_state=True)
         np.testing.assert_allclose(got.reshape(-1), want, rtol=1e-12)
+        # mu = d_1 exactly, so the lambda-weighted marginal violation is 0 (the weight-0 inputs
+        # have d_i != mu and must not count)
+        assert st["viol"] < 1e-14
 
 
 def test_identical_inputs_closed_form():
@@ -208,8 +211,12 @@ def test_homogeneity_and_invariants():
     mu = _inputs(g, 3, 11)
     lam = [0.5, 0.3, 0.2]
     b, st = oracle.barycenter_log(g, mu, lam, 12, want_state=True)
-    b3 = oracle.barycenter_log(g, 3.7 * mu, lam, 12)
+    b3, st3 = oracle.barycenter_log(g, 3.7 * mu, lam, 12, want_state=True)
     np.testing.assert_allclose(b3, 3.7 * b, rtol=1e-11)
+    # the marginal violation is relative: unchanged by the common scale, the mass scales with it
+    np.testing.assert_allclose(st3["viol"], st["viol"], rtol=1e-10)
+    np.testing.assert_allclose(st3["mass"], 3.7 * st["mass"], rtol=1e-12)
+    assert st["viol"] > 1e-3                         # not converged: a nontrivial value
     # sum_g d_i = sum_g mu_i = 1 (K symmetric), every iteration
     for i in range(3):
         assert abs(np.exp(st["ld"][i]).sum() - 1.0) < 1e-12
