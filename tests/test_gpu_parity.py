@@ -50,6 +50,8 @@ GRIDS = [  # nx, ny, nt, r, eps, periodic
     (20, 20, 2, 2, 1e-2, False),
     (33, 17, 32, 4, 4e-3, False),    # 32 orientations
     (64, 64, 16, 10, 1e-4, False),   # the 128^2 x 16 workload's kernel on a 64^2 grid
+    (9, 7, 8, 0, 5e-3, False),       # radius 0: orientations mix, no spatial spread; grid < one tile
+    (35, 34, 4, 16, 2e-2, True),     # the largest radius (33-tap rows), periodic
 ]
 
 
