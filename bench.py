@@ -288,7 +288,7 @@ def peak_terms_per_s():
 
 def conv_traffic():
     """DRAM bytes per launch of the convolution from the committed ncu summary, if it was taken
-    on the current source of conv.cu (else None)."""
+    on the current source of the kernel, conv_tile.cuh (else None)."""
     import hashlib
     p = os.path.join(ROOT, "profiles", "conv_kernel_traffic.json")
     src = os.path.join(ROOT, "paper_2402_15322_gb300", "csrc", "conv_tile.cuh")

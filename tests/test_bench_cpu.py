@@ -1,5 +1,6 @@
 """Host logic of bench.py without a GPU: the per-rank problem seeding of the replica mode and
-the max-over-ranks timing reduction, run as two gloo ranks on the CPU."""
+the max-over-ranks timing reduction, run as two gloo ranks on the CPU; the clock summary; the
+reference arm's JSON line."""
 import os
 import socket
 
@@ -60,3 +61,33 @@ def test_replicas_draw_distinct_problems():
 def test_single_rank_needs_no_process_group():
     assert bench.max_over_ranks(3.5, 1) == 3.5
     bench.barrier(1)
+
+
+def test_clock_summary_reads_nvidia_smi_rows(tmp_path):
+    """The clocks object of the JSON line: median SM clock under load, the largest maximum clock
+    and every throttle reason seen Active (rows as nvidia-smi prints them, csv,noheader,nounits)."""
+    s = bench.ClockSampler(0)
+    s.path = str(tmp_path / "clocks.csv")
+    s.proc = object()   # as if the sampler had run
+    with open(s.path, "w") as f:
+        f.write("0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active\n")
+        f.write("0, 1980, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active\n")
+        f.write("0, 2055, 2070, 1200.5, 0x0, Not Active, Not Active, Not Active, Not Active\n")
+        f.write("[N/A], garbage\n")
+    got = s.summary()
+    assert got == {"sm_mhz": 2055.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+
+
+def test_reference_arm_prints_the_contract_keys():
+    """`bench.py --impl reference`: the oracle timed on the host cores, one JSON object with the
+    keys the contract asks of the reference arm."""
+    line = bench.run_reference(type("A", (), {"steps": 1, "warmup": 0})())
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["value"] > 0
+    assert line["config"]["workload"] == bench.WORKLOAD
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"] and cb["sample"]
+    assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
