@@ -51,6 +51,11 @@ MUTANTS = [
     ("sign of the JKO b-update", "lb[g] = u[g] - t[g];", "lb[g] = u[g] + t[g];"),
     ("marginal violation without the weights", "viol += lam[i] * s;", "viol += s;"),
     ("marginal violation not relative", "stats[1] = viol / mass;", "stats[1] = viol;"),
+    ("log convolution without its shift", "    return M + log(acc);\n}", "    return log(acc);\n}"),
+    ("log convolution skipping terms above double resolution", "if (t < -746.0) continue;",
+     "if (t < -7.46) continue;"),
+    ("log convolution shift over the first orientation only",
+     "double M = -INFINITY;\n    for (int i = 0; i < nth; ++i)", "double M = -INFINITY;\n    for (int i = 0; i < 1; ++i)"),
 ]
 
 

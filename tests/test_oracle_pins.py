@@ -169,6 +169,19 @@ def test_log_conv_matches_linear_and_is_shift_covariant():
     np.testing.assert_allclose(np.exp(oracle.conv_log(g, lf)), oracle.conv_lin(g, f0), rtol=1e-13)
 
 
+@pytest.mark.parametrize("periodic", [False, True])
+def test_log_conv_matches_dense_logsumexp_over_a_wide_range(periodic):
+    """log(K * exp(lf)) against scipy's logsumexp over the dense group-law kernel matrix, for a
+    field whose orientation slices sit hundreds of nats apart (exp() of it overflows and
+    underflows double precision; the scaling vectors of the workloads look like this)."""
+    import scipy.special
+    g = oracle.Grid(7, 6, 8, 2, W, 0.03, periodic)
+    LK = refmath.dense_log_kernel(g.nx, g.ny, g.nth, g.r, _rho2, g.eps, periodic)
+    lf = RNG.normal(size=g.shape) * 3.0 + 800.0 * np.sin(np.arange(g.nth))[None, None, :]
+    want = scipy.special.logsumexp(LK + lf.reshape(-1)[None, :], axis=1).reshape(g.shape)
+    np.testing.assert_allclose(oracle.conv_log(g, lf), want, rtol=0, atol=1e-10)
+
+
 # -------------------------------------------------------- barycenter (Appendix A)
 def _dense_K(g):
     return np.exp(refmath.dense_log_kernel(g.nx, g.ny, g.nth, g.r,
