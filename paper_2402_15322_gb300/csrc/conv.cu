@@ -1,6 +1,6 @@
 // conv.cu -- launchers of the log-domain SE(2) group convolution (Sec. 4.2): the tile-max
 // pre-pass that drives orientation-pair skipping, the tiled kernel (conv_tile.cuh, instantiated
-// per radius in conv_r_*.cu) and the exact FP64 recompute of the outputs whose shift was poor.
+// per radius in conv_r_*.cu) and the exact recompute of the outputs whose shift was poor.
 //
 // Arrays are slice-major, in[b][i][y][x] (FP64 base-2 logarithms); see conv_tile.cuh for the
 // arithmetic of a term.

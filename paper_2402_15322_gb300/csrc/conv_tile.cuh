@@ -22,8 +22,8 @@
 // once per slice.  The big common magnitudes (the scaling vectors are hundreds to thousands of
 // log2 units, the orientation factor hundreds) cancel exactly before anything is rounded.  No
 // FP64 instruction runs per staged element or per output (GB300's FP64 rate is a small fraction
-// of FP32's).  Outputs that leave [S_j - 24, S_j + 16] are queued for the exact FP64 recompute of
-// conv.cu.
+// of FP32's).  Outputs that leave [S_j - 24, S_j + 16] are queued for the exact recompute of
+// conv.cu (the largest term as the shift, an FP64 sum).
 //
 // Affine shift (the common case): the scaling vectors are smooth on the grid, so the XQ shifts of
 // a thread usually lie close to a line, S_j ~ T_j = S_0 + g j (g on a 2^-6 grid, |g| <= 32).  With
