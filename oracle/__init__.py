@@ -91,6 +91,7 @@ class Grid:
 
 
 def threads():
+    """OpenMP threads the C oracle runs on (reported with the CPU timings; no arithmetic)."""
     return _lib().or_threads()
 
 
@@ -126,7 +127,9 @@ def log_kernel(g, h, w, eps, dist="rho_b"):
 
 
 def taps(grid):
-    """Log-kernel table lk[o, i, dy + r, dx + r] (output orientation o, input i)."""
+    """Log-kernel table lk[o, i, dy + r, dx + r] = log K(h^-1 g) for output orientation o and
+    input orientation i at spatial offset (dx, dy) (Sec. 4.2 kernel, Sec. 4.3 Eq. rho_b; by left
+    invariance only the offset and the two orientations matter)."""
     D = 2 * grid.r + 1
     lk = np.zeros((grid.nth, grid.nth, D, D))
     _lib().or_taps(*grid._args(), _ptr(lk))
@@ -152,7 +155,8 @@ def conv_log(grid, lf):
 
 
 def conv_log_points(grid, lf, idx):
-    """log(K * exp(lf)) at the flat output indices idx (layout [b, y, x, k]) only."""
+    """log(K * exp(lf)) (Sec. 4.2, log domain) at the flat output indices idx (layout
+    [b, y, x, k]) only: the same sum as conv_log, for grids too large to convolve whole."""
     lf = _arr(lf)
     idx = np.ascontiguousarray(idx, dtype=np.int64)
     out = np.zeros(idx.size)
@@ -199,7 +203,8 @@ def interpolate_log(grid, mu0, mu1, t, iters, want_state=False):
 
 
 def cost_taps(grid):
-    """log(c K) per tap, c = rho_b^2 (layout of taps()): the kernel of the plan's transport cost."""
+    """log(c K) per tap, c = rho_b^2 (layout of taps()): the kernel of the plan's transport cost
+    <c, pi> with pi = a K b (Sec. 4.1, the entropic plan)."""
     D = 2 * grid.r + 1
     out = np.zeros((grid.nth, grid.nth, D, D))
     _lib().or_cost_taps(*grid._args(), _ptr(out))
@@ -223,7 +228,9 @@ def w2_log(grid, mu, nu, iters, want_state=False):
 
 
 def prox_log(lz, sigma, m):
-    """log of the KL-proximal map of sigma s^m / (m - 1) at z = exp(lz) (porous-medium energy)."""
+    """log of the KL-proximal map of sigma s^m / (m - 1) at z = exp(lz): the porous-medium
+    energy's step in the entropic JKO scheme (Sec. 2.2 Eq. GF_JKO, Sec. 6.4; derivation in the C
+    source, or_prox_log)."""
     return _lib().or_prox_log(float(lz), float(sigma), float(m))
 
 

@@ -80,8 +80,8 @@ PART_FLOOR = 1e-6
 
 
 def part_measure(part):
-    """A split part as the measure that is transported: floored at PART_FLOOR of its maximum,
-    normalised to mass 1."""
+    """A split part (Sec. 6.2, step 2) as the measure that is transported: floored at PART_FLOOR
+    of its maximum, normalised to mass 1."""
     f = part + PART_FLOOR * part.max()
     return f / f.sum()
 
