@@ -79,7 +79,8 @@ int or_threads(void)
 #endif
 }
 
-/* (x,y,th)(x',y',th') = (x + x' cos th - y' sin th, y + x' sin th + y' cos th, th + th'). */
+/* The group law of Sec. 2.3:
+ * (x,y,th)(x',y',th') = (x + x' cos th - y' sin th, y + x' sin th + y' cos th, th + th'). */
 void or_group_mul(const double *a, const double *b, double *c)
 {
     double ca = cos(a[2]), sa = sin(a[2]);
@@ -89,7 +90,7 @@ void or_group_mul(const double *a, const double *b, double *c)
     c[0] = x; c[1] = y; c[2] = t;
 }
 
-/* g^-1 = (-R^-1 x, R^-1). */
+/* The inverse of Sec. 2.3: g^-1 = (-R^-1 x, R^-1). */
 void or_group_inv(const double *a, double *c)
 {
     double ca = cos(a[2]), sa = sin(a[2]);
@@ -99,7 +100,7 @@ void or_group_inv(const double *a, double *c)
     c[0] = x; c[1] = y; c[2] = or_wrap(-a[2]);
 }
 
-/* rho_b(g)^2 = (w1 b1)^2 + (w2 b2)^2 + (w3 b3)^2 with the half-angle coordinates
+/* Sec. 4.3 Eq. (rho_b): rho_b(g)^2 = (w1 b1)^2 + (w2 b2)^2 + (w3 b3)^2 with the half-angle coordinates
  * b1 = x cos(th/2) + y sin(th/2), b2 = -x sin(th/2) + y cos(th/2), b3 = th, th in [-pi, pi). */
 double or_rho_b2(double x, double y, double th, double w1, double w2, double w3)
 {
@@ -139,7 +140,8 @@ double or_rho2(double x, double y, double th, double w1, double w2, double w3, i
     return dist == 1 ? or_rho_c2(x, y, th, w1, w2, w3) : or_rho_b2(x, y, th, w1, w2, w3);
 }
 
-/* log K(h^-1 g) = -rho_b(h^-1 g)^2 / eps, with h^-1 g formed by the group law. */
+/* The Gibbs kernel of Sec. 4.2: log K(h^-1 g) = -rho(h^-1 g)^2 / eps, with h^-1 g formed by the
+ * group law. */
 double or_log_kernel(const double *g, const double *h, double w1, double w2, double w3, double eps, int dist)
 {
     double hi[3], u[3];
@@ -148,7 +150,8 @@ double or_log_kernel(const double *g, const double *h, double w1, double w2, dou
     return -or_rho2(u[0], u[1], u[2], w1, w2, w3, dist) / eps;
 }
 
-/* Tabulated log-kernel: lk[((o*nth + i)*D + (dy+r))*D + (dx+r)], D = 2r+1, is log K(h^-1 g)
+/* Tabulated log-kernel (the Gibbs kernel of Sec. 4.2 on the grid):
+ * lk[((o*nth + i)*D + (dy+r))*D + (dx+r)], D = 2r+1, is log K(h^-1 g)
  * for an output voxel g = (dx/nx, dy/ny, theta_o) and an input voxel h = (0, 0, theta_i).
  * By left invariance only the spatial offset g - h and the two orientations matter. */
 void or_taps(int nx, int ny, int nth, int r, double w1, double w2, double w3, double eps, int dist,
@@ -180,7 +183,8 @@ static long or_src(int y, int x, int dy, int dx, int nx, int ny, int periodic)
     return (long)sy * nx + sx;
 }
 
-/* out[b][y][x][o] = sum_{i, dy, dx} K_o,i(dx, dy) f[b][y-dy][x-dx][i]. */
+/* The group convolution of Sec. 4.2, (K * f)(g) = sum_h K(h^-1 g) f(h) with unit Haar weights:
+ * out[b][y][x][o] = sum_{i, dy, dx} K_o,i(dx, dy) f[b][y-dy][x-dx][i]. */
 void or_conv_lin(int nx, int ny, int nth, int r, double w1, double w2, double w3, double eps, int dist,
                  int periodic, int batch, const double *f, double *out)
 {
@@ -388,7 +392,8 @@ void or_barycenter_log(int nx, int ny, int nth, int r, double w1, double w2, dou
     free(lmu); free(lv); free(lw); free(ld); free(lkv); free(L);
 }
 
-/* Cost-weighted tap table: lkc = log(c(h^-1 g) K(h^-1 g)) = log(rho_b^2) - rho_b^2 / eps in the
+/* Cost-weighted tap table for the plan's cost <c, pi> of Sec. 4.1:
+ * lkc = log(c(h^-1 g) K(h^-1 g)) = log(rho_b^2) - rho_b^2 / eps in the
  * layout of or_taps; -inf where the cost vanishes (the identity tap). */
 void or_cost_taps(int nx, int ny, int nth, int r, double w1, double w2, double w3, double eps, int dist,
                   double *lkc)
@@ -476,7 +481,8 @@ void or_w2_log(int nx, int ny, int nth, int r, double w1, double w2, double w3, 
     free(lk); free(lkc); free(la); free(lb); free(t);
 }
 
-/* KL-proximal map of sigma F, F(s) = s^m / (m - 1) per voxel (unit Haar weight), at z = exp(lz):
+/* The JKO step's KL-proximal map (Sec. 2.2 Eq. (GF_JKO), Sec. 6.4, which only cites it; derived here):
+ * prox of sigma F, F(s) = s^m / (m - 1) per voxel (unit Haar weight), at z = exp(lz):
  * prox(z) = argmin_s sigma s^m / (m - 1) + s log(s / z) - s.  Setting the derivative to zero,
  * u = log s solves u + c exp((m - 1) u) = lz with c = sigma m / (m - 1); the left side is increasing
  * and convex in u, so Newton's method converges from any start (from the right monotonically).
