@@ -1,4 +1,4 @@
-// conv_r_b.cu -- instantiations of the tiled log-domain convolution for radii 6..11
+// conv_r_b.cu -- instantiations of the tiled log-domain group convolution (Sec. 4.2) for radii 6..11
 // (split across files so that they compile in parallel).
 #include "conv_tile.cuh"
 

@@ -1,4 +1,4 @@
-// conv_r_c.cu -- instantiations of the tiled log-domain convolution for radii 12..16
+// conv_r_c.cu -- instantiations of the tiled log-domain group convolution (Sec. 4.2) for radii 12..16
 // (split across files so that they compile in parallel).
 #include "conv_tile.cuh"
 

@@ -1,6 +1,7 @@
 // dfloat.cuh -- double-float arithmetic (an unevaluated sum hi + lo of two FP32 numbers, ~48
-// significant bits) built from error-free transformations: Knuth's TwoSum, Dekker's Fast2Sum and
-// the FMA-based exact product.  GB300 runs FP64 at a small fraction of its FP32 rate, so the
+// significant bits) for the log-domain scaling vectors of the Sinkhorn iterations (Appendix A),
+// built from error-free transformations: Knuth's TwoSum, Dekker's Fast2Sum and the FMA-based
+// exact product.  GB300 runs FP64 at a small fraction of its FP32 rate, so the
 // scaling vectors (base-2 logarithms of hundreds to thousands, needed to ~1e-12 absolute) are held
 // and updated as double-floats with FP32 instructions only.  Compiled without fast-math; the
 // transformations rely on round-to-nearest FP32 additions not being reassociated.

@@ -1,5 +1,5 @@
-// noalloc.cu -- se2ot_barycenter_noalloc: the barycenter solve for callers that must not
-// allocate device memory.
+// noalloc.cu -- se2ot_barycenter_noalloc: the barycenter solve (Appendix A, the same kernel
+// sequence as se2ot_barycenter) for callers that must not allocate device memory.
 //
 // Who needs it: code that runs where a device allocation is not allowed or not safe -- inside a
 // host application or framework that owns the whole device-memory budget through its own

@@ -1,4 +1,5 @@
-// server.cu -- se2ot_serve_*: a request loop for barycenter solves with continuous batching.
+// server.cu -- se2ot_serve_*: a request loop for barycenter solves (Appendix A) with continuous
+// batching.  The paper has no serving counterpart; each request runs se2ot_barycenter's kernels.
 //
 // Requests are queued by se2ot_serve_submit (inputs copied into the server, so the caller may
 // free them).  One worker thread owns the device work:

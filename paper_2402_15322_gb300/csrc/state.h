@@ -1,4 +1,4 @@
-// state.h -- one barycenter solve laid out in a caller-provided block of device memory, advanced
+// state.h -- one barycenter solve (Appendix A) laid out in a caller-provided block of device memory, advanced
 // in chunks of iterations on one stream.  The serving loop keeps many of these resident and
 // interleaves them; every step is the same kernel sequence as se2ot_barycenter.
 #pragma once
