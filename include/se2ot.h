@@ -119,7 +119,12 @@ typedef struct {
  *                    blocks of window positions whose terms all lie below 2^-64 of the output's
  *                    shift are skipped, so this is at most 2 * iters * n * V * ntheta * (2r+1)^2.
  *                    Counted per block of 4 window positions of a warp: an estimate, within
- *                    10% of the exact count. */
+ *                    10% of the exact count.
+ *   logscale_min, logscale_max   smallest and largest natural logarithm of the scaling vectors
+ *                    v_i over all measures and voxels after the last iteration (FP64, finite entries
+ *                    only): the dynamic range the solve needed, the reason the library keeps the
+ *                    scaling vectors as logarithms (FP32 holds e^-87 .. e^88, FP64 e^-708 .. e^709).
+ *                    Not measured by se2ot_jko (0). */
 typedef struct {
     int iters;
     double mass, viol, ms, voxel_iters_per_s;
@@ -128,6 +133,7 @@ typedef struct {
     long long kernel_launches;
     long long redo_outputs;
     long long evaluated_terms;
+    double logscale_min, logscale_max;
 } se2ot_stats;
 
 /* Build the kernel for a grid: validates desc, evaluates the taps
@@ -158,16 +164,19 @@ SE2OT_API se2ot_status se2ot_apply_log(se2ot_kernel k, const double *lf, double 
                              void *stream);
 
 /* Barycenter of n >= 1 measures with weights lambda (Appendix A; Eq. barywass with the
- * entropic kernel of Sec. 4.2).  mu: n*V floats, host or device memory (detected), each
- * measure >= 0 and not all zero; the caller makes the n masses equal (the iteration assumes it
- * and does not check or renormalise; the barycenter is homogeneous of degree one in a common
- * scale).  lambda: n <= 64 host doubles, >= 0, summing to 1 within 1e-12.  bary: V floats, host
- * or device memory.  opts may be NULL (100 iterations, no checks).  stats may be NULL.  Host
- * memory is copied on the stream; the call synchronises the stream before returning (stats
- * need it).  Workspace: 4 n V + V double-floats, 3 n V words, owned by the kernel handle and
- * reused.
- * Returns EINVAL for invalid arguments, ENONFINITE if an iterate became non-finite (a NaN input
- * does that), ENOTCONV if tol_viol > 0 was not reached (the result is still written). */
+ * entropic kernel of Sec. 4.2).  mu: n*V floats, host or device memory (detected).  The inputs
+ * must be measures of equal mass, which the Appendix A iteration assumes: every entry finite and
+ * >= 0, every measure with positive mass, and the n masses equal to 1e-6 relative to the largest.
+ * This is checked on the device in FP64 before the first iteration (one stream synchronisation);
+ * a violation returns EINVAL with a message naming the measure.  The library does not
+ * renormalise; a common scale of all inputs is allowed (the barycenter is homogeneous of degree
+ * one in it).  lambda: n <= 64 host doubles, >= 0, summing to 1 within 1e-12.  bary: V floats,
+ * host or device memory.  opts may be NULL (100 iterations, no checks).  stats may be NULL.
+ * Host memory is copied on the stream; the call synchronises the stream before returning (stats
+ * need it).  Workspace: 4 n V + V double-floats, 2 n V floats and n V int pairs, owned by the
+ * kernel handle and reused.
+ * Returns EINVAL for invalid arguments (inputs included), ENONFINITE if an iterate became
+ * non-finite, ENOTCONV if tol_viol > 0 was not reached (the result is still written). */
 SE2OT_API se2ot_status se2ot_barycenter(se2ot_kernel k, int n, const float *mu, const double *lambda,
                               const se2ot_solve_opts *opts, float *bary, se2ot_stats *stats,
                               void *stream);
@@ -190,7 +199,7 @@ SE2OT_API se2ot_status se2ot_interpolate(se2ot_kernel k, const float *mu0, const
  *   viol  = ||a (K * b) - mu||_1 / ||mu||_1         (the nu-marginal holds exactly after each b-step)
  * all reduced in FP64 in a fixed order.  mu, nu: V floats each, caller layout [y][x][theta],
  * nonnegative and finite, host or device memory; their masses need not be 1 but must agree to
- * 1e-6 relative.  opts as in se2ot_barycenter (tol_viol > 0 with check_every > 0 stops once viol
+ * 1e-6 relative (checked on the device before the first iteration: EINVAL otherwise).  opts as in se2ot_barycenter (tol_viol > 0 with check_every > 0 stops once viol
  * <= tol_viol; each check costs two convolutions).  The first call on a kernel handle builds the
  * cost-weighted tap table (same size as the kernel's); workspace is the handle's, as for a
  * 2-measure barycenter.  The call synchronises the stream before returning.
@@ -214,8 +223,9 @@ SE2OT_API se2ot_status se2ot_w2(se2ot_kernel k, const float *mu, const float *nu
  * the KL-proximal map of tau F on the second, opts->max_iters iterations per step from b = 1:
  *   a = mu_k / (K * b),   b = prox_{(tau/eps) F}(K * a) / (K * a),   mu_{k+1} = prox(K * a).
  * The prox solves log s + (tau/eps) m/(m-1) s^(m-1) = log z per voxel (Newton, FP64 result).
- * mu0: V floats, caller layout, strictly positive (a zero density makes the b-update 0/0) and on
- * the density scale F is meant for (no normalisation); mu_out: V floats; host or device memory.
+ * mu0: V floats, caller layout, strictly positive and finite (a zero density makes the b-update
+ * 0/0; checked on the device before the first step: EINVAL otherwise) and on the density scale F
+ * is meant for (no normalisation); mu_out: V floats; host or device memory.
  * tau >= 0, m > 1, steps >= 1, opts->tol_viol must be 0.  stats: iters = steps * max_iters, mass =
  * sum mu_out, viol = ||a (K * b) - mu_k||_1 / ||mu_k||_1 of the last step (FP64).  Workspace as for
  * a 2-measure barycenter.  Synchronises the stream.  EINVAL for invalid arguments, ENONFINITE for a
@@ -260,8 +270,9 @@ SE2OT_API se2ot_status se2ot_interpolate_signed(se2ot_kernel k, const float *U0,
 /* nprob independent interpolations Phi_t(mu0[p], mu1[p]) (weights (1 - t[p], t[p])) of uneven grid
  * sizes, radii, metrics and regularisations, iterated in lockstep for opts->max_iters Sinkhorn
  * iterations (Appendix A with n = 2 for every problem).  descs[p]: each problem's grid and kernel
- * (zero boundary only).  mu0[p], mu1[p]: device arrays of V_p floats (caller layout), out[p]: V_p
- * floats, device.  opts: max_iters >= 1, tol_viol must be 0 (no early stop in a batch), NULL =
+ * (zero boundary only).  mu0[p], mu1[p]: device arrays of V_p floats (caller layout), measures of
+ * equal mass as for se2ot_barycenter (checked on the device before the first iteration: EINVAL
+ * naming the problem otherwise), out[p]: V_p floats, device.  opts: max_iters >= 1, tol_viol must be 0 (no early stop in a batch), NULL =
  * 100 iterations.  stats: NULL or an array of nprob entries (ms and kernel_launches are for the
  * whole batch).
  * One iteration of the batch is one convolution launch per distinct radius for each of the two
@@ -290,7 +301,8 @@ typedef struct se2ot_server_s *se2ot_server;
 SE2OT_API se2ot_status se2ot_serve_create(size_t device_budget_bytes, int max_slots, int device, se2ot_server *out);
 
 /* Queue a barycenter of n measures (arguments as in se2ot_barycenter; mu host or device memory,
- * copied before return so the caller may free it).  ticket receives the request's id.  ENOMEM if
+ * copied before return so the caller may free it; the input check of se2ot_barycenter runs on that
+ * host copy, EINVAL on failure).  ticket receives the request's id.  ENOMEM if
  * the request can never fit the budget, EINVAL for invalid arguments, ESHUTDOWN after destroy
  * began. */
 SE2OT_API se2ot_status se2ot_serve_submit(se2ot_server sv, const se2ot_kernel_desc *desc, int n, const float *mu,
@@ -336,11 +348,16 @@ SE2OT_API se2ot_status se2ot_state_export(se2ot_kernel k, int n, double *log_v, 
  *
  * Arguments as in se2ot_barycenter, except: desc replaces the kernel handle; mu (n*V floats) and
  * bary (V floats) must be device memory (EINVAL otherwise: nothing is staged); stats->conv_ms is
- * not measured (0).  A problem whose tap table and workspace need more than the array
- * (ntheta^2 (2 (2r+1)^2 + (2r+1) + 2) floats of taps, 4 n V + V double-floats and 3 n V words of
- * workspace, n ntheta ceil(nx/32) ceil(ny/32) floats of tile maxima, plus 4 KiB) is
- * rejected with EINVAL and a message giving the size; e.g. n = 4 measures on 64 x 64 x 16 fit,
- * 128 x 128 x 16 does not.
+ * not measured (0).  The inputs are checked as in se2ot_barycenter.  A problem whose tap table
+ * and workspace need more than the array is rejected with EINVAL and a message giving the size.
+ * The array holds, in this order, each part starting on a 256-byte boundary (P = ntheta^2 orientation
+ * pairs, D = 2 radius + 1, T = n ntheta ceil(nx/32) ceil(ny/16) tiles):
+ *   taps: 8 P, 4 P D^2, 4 P D^2 and 4 P D bytes;  tile maxima: 4 T and 4 T bytes;
+ *   logs of mu_i, v_i, w_i, d_i: four arrays of 8 n V bytes;  log of the barycenter: 8 V;
+ *   shifts: two arrays of 4 n V;  recompute list: 8 n V;  launch order: 16 T + 8;
+ *   counters and sums: 16, 16, 8192 and 32 bytes;  input check: 2080 n bytes.
+ * E.g. n = 4 measures on 64 x 64 x 16 with radius 10 fit (14.1 MB); n = 5 there (17.2 MB) and
+ * 128 x 128 x 16 do not.
  *
  * The first call on each device looks up the array's device address (cudaGetSymbolAddress) and
  * caches it; make that first call before any stream capture.  Every call shares the one array
@@ -349,6 +366,13 @@ SE2OT_API se2ot_status se2ot_state_export(se2ot_kernel k, int n, double *log_v, 
 SE2OT_API se2ot_status se2ot_barycenter_noalloc(const se2ot_kernel_desc *desc, int n, const float *mu,
                                                 const double *lambda, const se2ot_solve_opts *opts,
                                                 float *bary, se2ot_stats *stats, void *stream);
+
+/* Measured throughput of the SFU's ex2.approx instruction on the current device (results per
+ * second, all SMs), by a kernel of independent ex2 chains timed with CUDA events on `stream`
+ * (about 1 ms; synchronises the stream).  The log-domain convolution evaluates one ex2 per kernel
+ * term, so this is the ceiling of its evaluated-term rate.  No counterpart in the paper: a
+ * measurement utility for roofline reports.  EINVAL for a NULL pointer, ECUDA on a CUDA failure. */
+SE2OT_API se2ot_status se2ot_sfu_ex2_rate(double *ex2_per_s, void *stream);
 
 /* Message for the calling host thread's most recent error ("" if none).  The pointer stays
  * valid until the thread's next failing call. */

@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -206,8 +207,8 @@ se2ot_status setup(BatchCtx &B, int nprob, const se2ot_kernel_desc *descs)
             q.h2 = a.take<float>(v2);
             q.tmax = a.take<float>((size_t)2 * nt * q.tiles);
             q.tmax2 = a.take<float>((size_t)2 * nt * q.tiles);
-            q.partial = a.take<double>(2 * STATS_BLOCKS);
-            q.scal = a.take<double>(4);
+            q.partial = a.take<double>(std::max<size_t>(STATS_PARTIAL, check_partial_doubles(2)));
+            q.scal = a.take<double>(4 + CHECK_Q * 2);   // [0, 2): mass, viol; [4, 12): input check
             if (!pass) total_v2 += (long)v2;
         }
         if (!pass) {
@@ -399,6 +400,23 @@ extern "C" se2ot_status se2ot_interpolate_batched(int nprob, const se2ot_kernel_
         }
         ++launches;
     }
+    // the inputs of every problem are measures of equal mass (Appendix A): checked on the device
+    // before any iteration is enqueued
+    std::vector<double> chk((size_t)CHECK_Q * 2 * nprob);
+    for (int p = 0; p < nprob; ++p) {
+        Prob &q = B.probs[p];
+        BCK(launch_input_check(q.mu, 2, q.V, q.partial, q.scal + 4, B.cs), "input check");
+        BCK(cudaMemcpyAsync(&chk[(size_t)CHECK_Q * 2 * p], q.scal + 4, CHECK_Q * 2 * sizeof(double),
+                            cudaMemcpyDeviceToHost, B.cs), "cudaMemcpy(check)");
+    }
+    BCK(cudaStreamSynchronize(B.cs), "cudaStreamSynchronize");
+    for (int p = 0; p < nprob; ++p) {
+        char what[32];
+        snprintf(what, sizeof what, "problem %d: mu", p);
+        se2ot_status cs = check_inputs(&chk[(size_t)CHECK_Q * 2 * p], 2, false, B.probs[p].V, what);
+        if (cs != SE2OT_OK) return cs;
+    }
+    launches += 2LL * nprob;
     BCK(cudaMemcpyAsync(B.dU, hU.data(), sizeof(UpdArgs) * nprob, cudaMemcpyHostToDevice, B.cs), "cudaMemcpy");
     BCK(cudaMemsetAsync(B.totals, 0, 2 * sizeof(unsigned long long), B.cs), "cudaMemset");
     for (int it = 0; it < o.max_iters; ++it) BCK(cudaGraphLaunch(B.graph, B.cs), "cudaGraphLaunch");
@@ -410,12 +428,12 @@ extern "C" se2ot_status se2ot_interpolate_batched(int nprob, const se2ot_kernel_
         lam.v[0] = hU[p].lam[0];
         lam.v[1] = hU[p].lam[1];
         BCK(launch_finalize(q.L, out[p], q.d.nx, q.d.ny, q.d.ntheta, B.cs), "finalize");
-        BCK(launch_stats(q.L, q.ld, lam, 2, q.V, q.partial, q.scal, B.cs), "stats");
+        BCK(launch_stats(q.L, q.ld, q.lv, lam, 2, q.V, q.partial, q.scal, B.cs), "stats");
         launches += 3;
     }
-    std::vector<double> scal(2 * (size_t)nprob);
+    std::vector<double> scal(4 * (size_t)nprob);
     for (int p = 0; p < nprob; ++p)
-        BCK(cudaMemcpyAsync(&scal[2 * p], B.probs[p].scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, B.cs),
+        BCK(cudaMemcpyAsync(&scal[4 * p], B.probs[p].scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, B.cs),
             "cudaMemcpy(stats)");
     unsigned long long counts[2] = {0, 0};
     BCK(cudaMemcpyAsync(counts, B.totals, sizeof counts, cudaMemcpyDeviceToHost, B.cs), "cudaMemcpy");
@@ -425,12 +443,14 @@ extern "C" se2ot_status se2ot_interpolate_batched(int nprob, const se2ot_kernel_
     const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - wall0).count();
     bool finite = true;
     for (int p = 0; p < nprob; ++p) {
-        if (!std::isfinite(scal[2 * p]) || !std::isfinite(scal[2 * p + 1])) finite = false;
+        if (!std::isfinite(scal[4 * p]) || !std::isfinite(scal[4 * p + 1])) finite = false;
         if (stats) {
             std::memset(&stats[p], 0, sizeof(se2ot_stats));
             stats[p].iters = o.max_iters;
-            stats[p].mass = scal[2 * p];
-            stats[p].viol = scal[2 * p + 1];
+            stats[p].mass = scal[4 * p];
+            stats[p].viol = scal[4 * p + 1];
+            stats[p].logscale_min = scal[4 * p + 2] * 0.69314718055994530942;
+            stats[p].logscale_max = scal[4 * p + 3] * 0.69314718055994530942;
             stats[p].ms = ms;
             stats[p].voxel_iters_per_s = ms > 0 ? (double)B.probs[p].V * o.max_iters / (ms * 1e-3) : 0.0;
             stats[p].kernel_launches = launches;

@@ -534,16 +534,16 @@ template <int R, bool MAXPASS>
 cudaError_t launch_tile(const ConvArgs &a, const ConvArgs *probs, const int4 *items, int nitems, cudaStream_t s)
 {
     const size_t smem = sizeof(float) * smem_floats(R);
-    static bool configured = false;
-    if (!configured) {
+    static PerDeviceOnce attrs;   // shared-memory limit above 48 KB, once per device
+    cudaError_t ea = attrs.run([&]() {
         cudaError_t e = cudaFuncSetAttribute(conv_tile_kernel<R, MAXPASS, false>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess && !MAXPASS)
             e = cudaFuncSetAttribute(conv_tile_kernel<R, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+        return e;
+    });
+    if (ea != cudaSuccess) return ea;
     if (items) {
         if (MAXPASS) return cudaErrorInvalidValue;   // batches never need the max pass
         if (nitems > 0) {

@@ -226,39 +226,70 @@ __device__ double block_sum(double v, double *sh)
     return out;
 }
 
-// partial[blk] = sum mu ; partial[STATS_BLOCKS + blk] = sum_i lambda_i sum |d_i - mu|
-__global__ void __launch_bounds__(RT) stats_partial_kernel(const float2 *L, const float2 *ld, Lambdas lam, int n,
-                                                           long V, double *partial)
+__device__ double block_min(double v, double *sh)
+{
+    const int tid = threadIdx.x;
+    sh[tid] = v;
+    __syncthreads();
+    for (int s = RT / 2; s > 0; s >>= 1) {
+        if (tid < s) sh[tid] = fmin(sh[tid], sh[tid + s]);
+        __syncthreads();
+    }
+    const double out = sh[0];
+    __syncthreads();
+    return out;
+}
+
+// partial[blk] = sum mu ; partial[STATS_BLOCKS + blk] = sum_i lambda_i sum |d_i - mu| ;
+// partial[2 STATS_BLOCKS + blk] = min lv, partial[3 STATS_BLOCKS + blk] = -max lv (finite entries)
+__global__ void __launch_bounds__(RT) stats_partial_kernel(const float2 *L, const float2 *ld, const float2 *lv,
+                                                           Lambdas lam, int n, long V, double *partial)
 {
     __shared__ double sh[RT];
-    double m = 0.0, vio = 0.0;
+    double m = 0.0, vio = 0.0, vmin = INFINITY, nvmax = INFINITY;
     for (long g = blockIdx.x * (long)RT + threadIdx.x; g < V; g += (long)STATS_BLOCKS * RT) {
         const double mu = exp2(df_to_double(L[g]));
         m += mu;
-        for (int i = 0; i < n; ++i)
+        for (int i = 0; i < n; ++i) {
             vio += df_to_double(lam.v[i]) * fabs(exp2(df_to_double(ld[(long)i * V + g])) - mu);
+            const double v = df_to_double(lv[(long)i * V + g]);
+            if (isfinite(v)) {
+                vmin = fmin(vmin, v);
+                nvmax = fmin(nvmax, -v);
+            }
+        }
     }
     m = block_sum(m, sh);
     vio = block_sum(vio, sh);
+    vmin = block_min(vmin, sh);
+    nvmax = block_min(nvmax, sh);
     if (threadIdx.x == 0) {
         partial[blockIdx.x] = m;
         partial[STATS_BLOCKS + blockIdx.x] = vio;
+        partial[2 * STATS_BLOCKS + blockIdx.x] = vmin;
+        partial[3 * STATS_BLOCKS + blockIdx.x] = nvmax;
     }
 }
 
 __global__ void __launch_bounds__(RT) stats_final_kernel(const double *partial, double *out)
 {
     __shared__ double sh[RT];
-    double m = 0.0, v = 0.0;
+    double m = 0.0, v = 0.0, vmin = INFINITY, nvmax = INFINITY;
     for (int k = threadIdx.x; k < STATS_BLOCKS; k += RT) {
         m += partial[k];
         v += partial[STATS_BLOCKS + k];
+        vmin = fmin(vmin, partial[2 * STATS_BLOCKS + k]);
+        nvmax = fmin(nvmax, partial[3 * STATS_BLOCKS + k]);
     }
     m = block_sum(m, sh);
     v = block_sum(v, sh);
+    vmin = block_min(vmin, sh);
+    nvmax = block_min(nvmax, sh);
     if (threadIdx.x == 0) {
         out[0] = m;
         out[1] = v / m;
+        out[2] = vmin;
+        out[3] = -nvmax;
     }
 }
 
@@ -296,6 +327,48 @@ __global__ void w2_stats_final_kernel(const double *partial, double *scal)
         const double t = block_sum(v, sh);
         if (threadIdx.x == 0) scal[q] = t;
     }
+}
+
+// Input check of a solve: for measure i = blockIdx.y, block blockIdx.x of CHECK_BLOCKS sums its
+// share of mu_i in FP64 and counts negative, non-finite and zero entries; check_final_kernel adds
+// the blocks in a fixed order into out[CHECK_Q i + {0..3}] = (mass, negatives, non-finite, zeros).
+__global__ void __launch_bounds__(RT) check_partial_kernel(const float *mu, long V, double *partial)
+{
+    __shared__ double sh[RT];
+    const int i = blockIdx.y;
+    const float *m = mu + (long)i * V;
+    double sum = 0.0, neg = 0.0, bad = 0.0, zero = 0.0;
+    for (long g = blockIdx.x * (long)RT + threadIdx.x; g < V; g += (long)CHECK_BLOCKS * RT) {
+        const float v = m[g];
+        if (!isfinite(v)) bad += 1.0;
+        else if (v < 0.f) neg += 1.0;
+        else if (v == 0.f) zero += 1.0;
+        else sum += (double)v;
+    }
+    const double q[CHECK_Q] = {sum, neg, bad, zero};
+    for (int k = 0; k < CHECK_Q; ++k) {
+        const double t = block_sum(q[k], sh);
+        if (threadIdx.x == 0) partial[((long)i * CHECK_Q + k) * CHECK_BLOCKS + blockIdx.x] = t;
+    }
+}
+
+__global__ void __launch_bounds__(RT) check_final_kernel(const double *partial, double *out)
+{
+    __shared__ double sh[RT];
+    const int i = blockIdx.x;
+    for (int k = 0; k < CHECK_Q; ++k) {
+        double v = 0.0;
+        for (int b = threadIdx.x; b < CHECK_BLOCKS; b += RT) v += partial[((long)i * CHECK_Q + k) * CHECK_BLOCKS + b];
+        const double t = block_sum(v, sh);
+        if (threadIdx.x == 0) out[CHECK_Q * i + k] = t;
+    }
+}
+
+cudaError_t launch_input_check(const float *mu, int n, long V, double *partial, double *out, cudaStream_t s)
+{
+    check_partial_kernel<<<dim3(CHECK_BLOCKS, n), RT, 0, s>>>(mu, V, partial);
+    check_final_kernel<<<n, RT, 0, s>>>(partial, out);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_init(const float *mu, float2 *lmu, float2 *lv, float *h1, float *h2, int n, int nx, int ny,
@@ -338,10 +411,10 @@ cudaError_t launch_w2_stats(const float2 *la, const float2 *lb, const float2 *lm
     return cudaGetLastError();
 }
 
-cudaError_t launch_stats(const float2 *L, const float2 *ld, const Lambdas &lam, int n, long V, double *partial,
-                         double *scal, cudaStream_t s)
+cudaError_t launch_stats(const float2 *L, const float2 *ld, const float2 *lv, const Lambdas &lam, int n, long V,
+                         double *partial, double *scal, cudaStream_t s)
 {
-    stats_partial_kernel<<<STATS_BLOCKS, RT, 0, s>>>(L, ld, lam, n, V, partial);
+    stats_partial_kernel<<<STATS_BLOCKS, RT, 0, s>>>(L, ld, lv, lam, n, V, partial);
     stats_final_kernel<<<1, RT, 0, s>>>(partial, scal);
     return cudaGetLastError();
 }

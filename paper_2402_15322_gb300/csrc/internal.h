@@ -3,7 +3,9 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
+#include <mutex>
 #include <string>
 
 #include "se2ot.h"
@@ -69,6 +71,30 @@ struct Taps {
 // anything (wait).  Both are no-ops for a kernel launched without the attribute.
 __device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;"); }
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// One-time set-up per device (kernel attributes such as the dynamic shared-memory limit belong to
+// the device context that is current when they are set): run(f) calls f once for each device the
+// process uses, with that device current, and is safe to call from several host threads at once.
+// A failed set-up is retried by the next call.
+struct PerDeviceOnce {
+    std::atomic<unsigned long long> done{0};   // bit d: device d is set up
+    std::mutex mu;
+    template <class F>
+    cudaError_t run(F &&f)
+    {
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+        const unsigned long long bit = 1ull << dev;
+        if (done.load(std::memory_order_acquire) & bit) return cudaSuccess;
+        std::lock_guard<std::mutex> lock(mu);
+        if (done.load(std::memory_order_relaxed) & bit) return cudaSuccess;
+        e = f();
+        if (e == cudaSuccess) done.fetch_or(bit, std::memory_order_release);
+        return e;
+    }
+};
 
 // Launch configuration with programmatic stream serialisation (the next kernel of the stream may
 // start while this one finishes; it waits in pdl_wait).
@@ -143,12 +169,28 @@ cudaError_t launch_init(const float *mu, float2 *lmu, float2 *lv, float *h1, flo
 // L = sum_i lambda_i ld_i ; lv_i += L - ld_i ; tmax_v (if not NULL) = inner-tile maxima of lv
 cudaError_t launch_update(float2 *lv, const float2 *ld, float2 *L, const Lambdas &lam, int n, int nx, int ny,
                           int nt, float *tmax_v, bool release_early, cudaStream_t s);
+// Input check of a solve (Sec. 2.2: the inputs are measures; Appendix A's iteration assumes equal
+// masses): out[CHECK_Q i + {0, 1, 2, 3}] = (FP64 sum of mu_i over its finite nonnegative entries,
+// number of negative entries, of non-finite entries, of zero entries) for the n measures of mu
+// ([n][V] floats, any layout).  partial holds check_partial_doubles(n) doubles, out CHECK_Q n.
+// Deterministic (fixed-order sums).
+constexpr int CHECK_BLOCKS = 64, CHECK_Q = 4;
+constexpr size_t check_partial_doubles(int n) { return (size_t)CHECK_Q * n * CHECK_BLOCKS; }
+cudaError_t launch_input_check(const float *mu, int n, long V, double *partial, double *out, cudaStream_t s);
+// The verdict on launch_input_check's out (host copy): OK, or EINVAL with a message when an entry
+// is negative or not finite, a measure has zero mass (strictly positive entries required when
+// positive_entries is set), or two masses differ by more than 1e-6 relative to the largest.
+se2ot_status check_inputs(const double *out, int n, bool positive_entries, long V, const char *what);
+
 // bary (caller layout) = 2^L
 cudaError_t launch_finalize(const float2 *L, float *bary, int nx, int ny, int nt, cudaStream_t s);
-// scal[0] = sum 2^L, scal[1] = sum_i lambda_i |2^ld_i - 2^L| / scal[0]  (FP64, fixed order)
+// scal[0] = sum 2^L, scal[1] = sum_i lambda_i |2^ld_i - 2^L| / scal[0]  (FP64, fixed order);
+// scal[2], scal[3] = smallest and largest finite log2 v_i over all measures and voxels (lv: the n
+// scaling vectors; -inf / +inf when none is finite).  partial holds STATS_PARTIAL doubles.
 constexpr int STATS_BLOCKS = 256;
-cudaError_t launch_stats(const float2 *L, const float2 *ld, const Lambdas &lam, int n, long V, double *partial,
-                         double *scal, cudaStream_t s);
+constexpr int STATS_PARTIAL = 4 * STATS_BLOCKS;
+cudaError_t launch_stats(const float2 *L, const float2 *ld, const float2 *lv, const Lambdas &lam, int n, long V,
+                         double *partial, double *scal, cudaStream_t s);
 // JKO scaling step of the porous-medium energy (slice-major, one field): with lq = -log2(K a) (the
 // EPI_W output for a zero aux), u = log2 prox_{sigma F}(K a) for F = s^m / (m - 1) per voxel,
 // lb = u + lq (log2 b) and lu = u (log2 of the plan's second marginal); tmax_b (if not NULL) =

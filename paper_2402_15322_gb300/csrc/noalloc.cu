@@ -89,14 +89,56 @@ struct Carver {
     }
 };
 
-bool on_device(const void *p)
+// Device memory of device `dev` (a pointer on another GPU would be read across the link or fault).
+bool on_device(const void *p, int dev)
 {
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) && at.device == dev;
+}
+
+// The sub-buffers of one solve, in order; with base == nullptr only the size is computed.
+struct Layout {
+    Taps taps;
+    float *tmax, *tmax2;
+    float2 *lmu, *lv, *lw, *ld, *L;
+    float *h1, *h2;
+    int2 *redo;
+    unsigned *ord, *count;
+    unsigned long long *totals;
+    double *partial, *scal, *chk;
+    size_t bytes;
+};
+
+Layout carve(unsigned char *base, size_t npair, int D, size_t ntmax, size_t nV, size_t V, int n)
+{
+    Carver c{base};
+    Layout l;
+    l.taps.ltheta = c.take<float2>(npair);
+    l.taps.ls = c.take<float>(npair * D * D);
+    l.taps.ls_lo = c.take<float>(npair * D * D);
+    l.taps.lsrow = c.take<float>(npair * D);
+    l.tmax = c.take<float>(ntmax);
+    l.tmax2 = c.take<float>(ntmax);
+    l.lmu = c.take<float2>(nV);
+    l.lv = c.take<float2>(nV);
+    l.lw = c.take<float2>(nV);
+    l.ld = c.take<float2>(nV);
+    l.L = c.take<float2>(V);
+    l.h1 = c.take<float>(nV);
+    l.h2 = c.take<float>(nV);
+    l.redo = c.take<int2>(nV);
+    l.ord = c.take<unsigned>(4 * ntmax + 2);
+    l.count = c.take<unsigned>(4);
+    l.totals = c.take<unsigned long long>(2);
+    l.partial = c.take<double>(STATS_PARTIAL);
+    l.scal = c.take<double>(4);
+    l.chk = c.take<double>(check_partial_doubles(n) + CHECK_Q * (size_t)n);
+    l.bytes = c.off;
+    return l;
 }
 
 }  // namespace
@@ -126,8 +168,11 @@ extern "C" se2ot_status se2ot_barycenter_noalloc(const se2ot_kernel_desc *desc, 
         lsum += lambda[i];
     }
     if (std::fabs(lsum - 1.0) > 1e-12) return nfail(SE2OT_EINVAL, "lambda sums to %.17g, not 1", lsum);
-    if (!on_device(mu) || !on_device(bary))
-        return nfail(SE2OT_EINVAL, "mu and bary must be device memory (this entry point copies nothing)");
+    int dev = 0, sms = 152;
+    NCK(cudaGetDevice(&dev), "cudaGetDevice");
+    if (!on_device(mu, dev) || !on_device(bary, dev))
+        return nfail(SE2OT_EINVAL, "mu and bary must be memory of the current device %d (this entry point copies "
+                                   "nothing)", dev);
 
     const int nt = desc->ntheta, D = 2 * desc->radius + 1;
     const long V = (long)desc->nx * desc->ny * nt;
@@ -136,61 +181,47 @@ extern "C" se2ot_status se2ot_barycenter_noalloc(const se2ot_kernel_desc *desc, 
     const size_t ntmax = (size_t)n * nt * conv_tiles(desc->nx, desc->ny);
     if ((double)n * nt > 65535.0) return nfail(SE2OT_EINVAL, "n*ntheta too large");
 
-    // Lay out the scratch array; first a dry run to size it.
-    Carver dry{nullptr};
-    dry.take<float2>(npair);
-    dry.take<float>(npair * D * D);
-    dry.take<float>(npair * D * D);
-    dry.take<float>(npair * D);
-    dry.take<float>(ntmax);
-    dry.take<float>(ntmax);
-    for (int k = 0; k < 4; ++k) dry.take<float2>(nV);
-    dry.take<float2>((size_t)V);
-    dry.take<float>(nV);
-    dry.take<float>(nV);
-    dry.take<int2>(nV);
-    dry.take<unsigned>(4 * ntmax + 2);
-    dry.take<unsigned>(4);
-    dry.take<unsigned long long>(2);
-    dry.take<double>(2 * STATS_BLOCKS);
-    dry.take<double>(4);
-    if (dry.off > SCRATCH_BYTES)
+    // lay out the scratch array: first a dry run to size it
+    const Layout need = carve(nullptr, npair, D, ntmax, nV, (size_t)V, n);
+    if (need.bytes > SCRATCH_BYTES)
         return nfail(SE2OT_EINVAL, "problem needs %zu bytes of scratch, more than the %zu-byte static array",
-                     dry.off, SCRATCH_BYTES);
+                     need.bytes, SCRATCH_BYTES);
 
     unsigned char *base = nullptr;
     st = scratch_address(&base);
     if (st != SE2OT_OK) return st;
-    Carver c{base};
-    Taps taps;
-    taps.ltheta = c.take<float2>(npair);
-    taps.ls = c.take<float>(npair * D * D);
-    taps.ls_lo = c.take<float>(npair * D * D);
-    taps.lsrow = c.take<float>(npair * D);
-    float *tmax = c.take<float>(ntmax);
-    float *tmax2 = c.take<float>(ntmax);
-    float2 *lmu = c.take<float2>(nV), *lv = c.take<float2>(nV), *lw = c.take<float2>(nV), *ld = c.take<float2>(nV);
-    float2 *L = c.take<float2>((size_t)V);
-    float *h1 = c.take<float>(nV), *h2 = c.take<float>(nV);
-    int2 *redo = c.take<int2>(nV);
-    unsigned *ord = c.take<unsigned>(4 * ntmax + 2);
-    unsigned *count = c.take<unsigned>(4);
-    unsigned long long *totals = c.take<unsigned long long>(2);
-    double *partial = c.take<double>(2 * STATS_BLOCKS);
-    double *scal = c.take<double>(4);
+    const Layout l = carve(base, npair, D, ntmax, nV, (size_t)V, n);
+    Taps taps = l.taps;
+    float *tmax = l.tmax, *tmax2 = l.tmax2;
+    float2 *lmu = l.lmu, *lv = l.lv, *lw = l.lw, *ld = l.ld, *L = l.L;
+    float *h1 = l.h1, *h2 = l.h2;
+    int2 *redo = l.redo;
+    unsigned *ord = l.ord, *count = l.count;
+    unsigned long long *totals = l.totals;
+    double *partial = l.partial, *scal = l.scal;
 
     cudaStream_t s = (cudaStream_t)stream;
-    int dev = 0, sms = 152;
-    NCK(cudaGetDevice(&dev), "cudaGetDevice");
     NCK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "cudaDeviceGetAttribute");
+
+    // the inputs are measures of equal mass (Appendix A), checked on the device before any iteration
+    {
+        double hc[CHECK_Q * 64];
+        NCK(launch_input_check(mu, n, V, l.chk, l.chk + check_partial_doubles(n), s), "input check launch");
+        NCK(cudaMemcpyAsync(hc, l.chk + check_partial_doubles(n), (size_t)CHECK_Q * n * sizeof(double),
+                            cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync(check)");
+        NCK(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+        st = check_inputs(hc, n, false, V, "mu");
+        if (st != SE2OT_OK) return st;
+    }
 
     // everything read below is (re)initialised here: the array keeps the previous call's values
     NCK(cudaMemsetAsync(totals, 0, 2 * sizeof(unsigned long long), s), "cudaMemsetAsync");
+    NCK(cudaMemsetAsync(count, 0, 2 * sizeof(unsigned), s), "cudaMemsetAsync(redo counts)");
     NCK(build_taps(*desc, taps, s), "tap build");
     NCK(launch_init(mu, lmu, lv, h1, h2, n, desc->nx, desc->ny, nt, s), "init launch");
     const bool fused_max = desc->boundary == SE2OT_BOUNDARY_ZERO;
     if (fused_max) NCK(cudaMemsetAsync(tmax, 0, ntmax * sizeof(float), s), "cudaMemsetAsync(tmax)");
-    long long launches = 5;
+    long long launches = 7;
 
     ConvArgs aw;
     std::memset(&aw, 0, sizeof aw);
@@ -238,12 +269,18 @@ extern "C" se2ot_status se2ot_barycenter_noalloc(const se2ot_kernel_desc *desc, 
     NCK(launch_order_init(ad.order, ad.cost, ad.done, (long)ntmax, s), "order init");
     if (!conv_order_pays((long)ntmax)) aw.order = ad.order = nullptr;
 
+    // The recompute counters alternate as in se2ot_barycenter: a convolution appends to
+    // count[phase] (zeroed above, or by the previous recompute pass) and its recompute pass clears
+    // count[1 - phase] for the next convolution, so no memset runs between launches.
+    int phase = 0;
     int it = 0;
     bool converged = false;
     for (it = 0; it < o.max_iters;) {
         aw.sort_order = ad.sort_order = order_sort_launch(it);
-        for (const ConvArgs *a : {&aw, &ad}) {
-            NCK(cudaMemsetAsync(count, 0, sizeof(unsigned), s), "cudaMemsetAsync");
+        for (ConvArgs *a : {&aw, &ad}) {
+            a->redo_count = count + phase;
+            a->redo_clear = count + (1 - phase);
+            phase = 1 - phase;
             NCK(launch_conv(*a, s), "conv launch");
             NCK(launch_redo(*a, 2 * sms, s), "redo launch");
             launches += fused_max ? 2 : 3;
@@ -253,7 +290,7 @@ extern "C" se2ot_status se2ot_barycenter_noalloc(const se2ot_kernel_desc *desc, 
         ++launches;
         ++it;
         if (o.tol_viol > 0 && o.check_every > 0 && it % o.check_every == 0 && it < o.max_iters) {
-            NCK(launch_stats(L, ld, lam, n, V, partial, scal, s), "stats launch");
+            NCK(launch_stats(L, ld, lv, lam, n, V, partial, scal, s), "stats launch");
             launches += 2;
             double h[2];
             NCK(cudaMemcpyAsync(h, scal, sizeof h, cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync(stats)");
@@ -265,9 +302,9 @@ extern "C" se2ot_status se2ot_barycenter_noalloc(const se2ot_kernel_desc *desc, 
         }
     }
     NCK(launch_finalize(L, bary, desc->nx, desc->ny, nt, s), "finalize launch");
-    NCK(launch_stats(L, ld, lam, n, V, partial, scal, s), "stats launch");
+    NCK(launch_stats(L, ld, lv, lam, n, V, partial, scal, s), "stats launch");
     launches += 3;
-    double h[2];
+    double h[4];
     unsigned long long counts[2] = {0, 0};
     NCK(cudaMemcpyAsync(h, scal, sizeof h, cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync(stats)");
     NCK(cudaMemcpyAsync(counts, totals, sizeof counts, cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync(counters)");
@@ -283,6 +320,8 @@ extern "C" se2ot_status se2ot_barycenter_noalloc(const se2ot_kernel_desc *desc, 
         stats->kernel_launches = launches;
         stats->redo_outputs = (long long)counts[0];
         stats->evaluated_terms = (long long)counts[1];
+        stats->logscale_min = h[2] * 0.69314718055994530942;
+        stats->logscale_max = h[3] * 0.69314718055994530942;
     }
     if (!std::isfinite(h[0]) || !std::isfinite(h[1]))
         return nfail(SE2OT_ENONFINITE, "non-finite iterate (mass=%g, viol=%g)", h[0], h[1]);

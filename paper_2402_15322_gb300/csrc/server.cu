@@ -51,7 +51,7 @@ struct Request {
     char *dev = nullptr;
     cudaStream_t s = nullptr;
     cudaEvent_t ev = nullptr;
-    double *h_scal = nullptr;      // pinned read-back of {mass, viol}
+    double *h_scal = nullptr;      // pinned read-back of {mass, viol, min log2 v, max log2 v}
     SolveState st;
     int chunk = 0;
     bool in_flight = false;
@@ -111,7 +111,7 @@ cudaError_t launch_chunk(const ReqPtr &r)
     const int k = left < r->chunk ? left : r->chunk;
     cudaError_t e = state_iterate(r->st, k, r->s);
     if (e == cudaSuccess) e = state_stats(r->st, r->s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(r->h_scal, r->st.scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, r->s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(r->h_scal, r->st.scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, r->s);
     if (e == cudaSuccess) e = cudaEventRecord(r->ev, r->s);
     r->in_flight = e == cudaSuccess;
     return e;
@@ -178,6 +178,8 @@ void step(se2ot_server_s *sv, const ReqPtr &r)
     r->stats.voxel_iters_per_s = run_ms > 0 ? (double)r->st.V * r->st.iters_done / (run_ms * 1e-3) : 0.0;
     r->stats.redo_outputs = (long long)counts[0];
     r->stats.evaluated_terms = (long long)counts[1];
+    r->stats.logscale_min = r->h_scal[2] * 0.69314718055994530942;
+    r->stats.logscale_max = r->h_scal[3] * 0.69314718055994530942;
     release(sv, r);
     complete(sv, r, e == cudaSuccess ? st : SE2OT_ECUDA);
 }
@@ -301,6 +303,29 @@ se2ot_status se2ot_serve_submit(se2ot_server sv, const se2ot_kernel_desc *desc, 
     if (cudaMemcpy(r->mu.data(), mu, nV * sizeof(float), cudaMemcpyDefault) != cudaSuccess) {
         set_last_error("se2ot_serve_submit: cannot read mu");
         return SE2OT_ECUDA;
+    }
+    {
+        // the inputs are measures of equal mass (Appendix A); the same verdict as the solves' device
+        // check, on the request's host copy
+        std::vector<double> q((size_t)CHECK_Q * n, 0.0);
+        const size_t V = (size_t)desc->nx * desc->ny * desc->ntheta;
+        for (int i = 0; i < n; ++i) {
+            const float *m = r->mu.data() + (size_t)i * V;
+            double sum = 0.0, neg = 0.0, bad = 0.0, zero = 0.0;
+            for (size_t g = 0; g < V; ++g) {
+                const float v = m[g];
+                if (!std::isfinite(v)) bad += 1.0;
+                else if (v < 0.f) neg += 1.0;
+                else if (v == 0.f) zero += 1.0;
+                else sum += (double)v;
+            }
+            q[CHECK_Q * i] = sum;
+            q[CHECK_Q * i + 1] = neg;
+            q[CHECK_Q * i + 2] = bad;
+            q[CHECK_Q * i + 3] = zero;
+        }
+        se2ot_status cs = check_inputs(q.data(), n, false, (long)V, "se2ot_serve_submit: mu");
+        if (cs != SE2OT_OK) return cs;
     }
     r->t_submit = Clock::now();
     std::lock_guard<std::mutex> lock(sv->mu);

@@ -136,6 +136,7 @@ struct se2ot_kernel_s {
     float *hint_ws = nullptr;
     size_t c_hint_ws = 0;
     double *partial = nullptr, *scal = nullptr;
+    double *chk = nullptr;                     // input check: check_partial_doubles(64) partials + CHECK_Q * 64 results
     float *tmax = nullptr, *tmax2 = nullptr;   // tile maxima of lv (and apply inputs), of lw
     int last_n = 0;                            // measures of the last completed solve
     size_t c_tmax = 0, c_tmax2 = 0;
@@ -243,9 +244,44 @@ se2ot_status run_conv(se2ot_kernel k, const ConvArgs &a0, cudaStream_t s, long l
     return SE2OT_OK;
 }
 
+// Enqueue the input check of n measures (device memory, [n][V]) on the handle's buffers, wait for it
+// and return check_inputs' verdict.
+se2ot_status run_input_check(se2ot_kernel k, const float *mu_dev, int n, bool positive_entries, cudaStream_t s,
+                             const char *what)
+{
+    double *out = k->chk + check_partial_doubles(64);
+    double h[CHECK_Q * 64];
+    CK(launch_input_check(mu_dev, n, k->V, k->chk, out, s), "input check launch");
+    CK(cudaMemcpyAsync(h, out, (size_t)CHECK_Q * n * sizeof(double), cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync(check)");
+    CK(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    return check_inputs(h, n, positive_entries, k->V, what);
+}
+
 }  // namespace
 
 namespace se2ot {
+
+se2ot_status check_inputs(const double *out, int n, bool positive_entries, long V, const char *what)
+{
+    double mmax = 0.0;
+    for (int i = 0; i < n; ++i) {
+        const double *q = out + CHECK_Q * i;
+        if (q[2] > 0) return fail(SE2OT_EINVAL, "%s[%d] has %.0f non-finite entries", what, i, q[2]);
+        if (q[1] > 0) return fail(SE2OT_EINVAL, "%s[%d] has %.0f negative entries", what, i, q[1]);
+        if (positive_entries && q[3] > 0)
+            return fail(SE2OT_EINVAL, "%s[%d] has %.0f zero entries (a zero density makes the scaling update 0/0)",
+                        what, i, q[3]);
+        if (!(q[0] > 0)) return fail(SE2OT_EINVAL, "%s[%d] has zero mass", what, i);
+        mmax = std::max(mmax, q[0]);
+    }
+    for (int i = 0; i < n; ++i)
+        if (std::fabs(out[CHECK_Q * i] - mmax) > 1e-6 * mmax)
+            return fail(SE2OT_EINVAL,
+                        "%s: the masses differ (%s[%d] = %.9g, largest %.9g; equal masses to 1e-6 relative are required)",
+                        what, what, i, out[CHECK_Q * i], mmax);
+    (void)V;
+    return SE2OT_OK;
+}
 
 se2ot_status validate_kernel_desc(const se2ot_kernel_desc *d) { return validate_desc(d); }
 
@@ -283,8 +319,9 @@ se2ot_status se2ot_kernel_build(const se2ot_kernel_desc *desc, void *stream, se2
     if (e == cudaSuccess) e = cudaMalloc((void **)&k->taps.lsrow, npair * D * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc((void **)&k->counters, 4 * sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMalloc((void **)&k->redo_total, 2 * sizeof(unsigned long long));
-    if (e == cudaSuccess) e = cudaMalloc((void **)&k->partial, 2 * STATS_BLOCKS * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&k->partial, STATS_PARTIAL * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc((void **)&k->scal, 4 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&k->chk, (check_partial_doubles(64) + CHECK_Q * 64) * sizeof(double));
     if (e == cudaSuccess) e = cudaMemsetAsync(k->counters, 0, 4 * sizeof(unsigned), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(k->redo_total, 0, 2 * sizeof(unsigned long long), s);
     if (e == cudaSuccess) e = build_taps(*desc, k->taps, s);
@@ -302,7 +339,7 @@ se2ot_status se2ot_kernel_destroy(se2ot_kernel k)
     if (!k) return SE2OT_OK;
     cudaDeviceSynchronize();
     void *ptrs[] = {k->taps.ltheta, k->taps.ls, k->taps.ls_lo, k->taps.lsrow, k->tmax, k->tmax2, k->lmu, k->lv, k->lw, k->ld, k->L, k->lf, k->h1, k->h2, k->hint_ws,
-                    k->mu_stage, k->bary_stage, k->redo, k->counters, k->redo_total, k->partial, k->scal, k->ord, k->ctaps.ltheta, k->ctaps.ls,
+                    k->mu_stage, k->bary_stage, k->redo, k->counters, k->redo_total, k->partial, k->scal, k->chk, k->ord, k->ctaps.ltheta, k->ctaps.ls,
                     k->ctaps.ls_lo, k->ctaps.lsrow, k->w2p, k->zero};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -425,9 +462,11 @@ se2ot_status se2ot_barycenter(se2ot_kernel k, int n, const float *mu, const doub
         bary_dev = k->bary_stage;
     }
 
-    // validate the inputs on the device: masses (FP64) and the sign of every entry are checked by
-    // the reductions below once log2 mu exists
-    long long launches = 0;
+    // the inputs are measures of equal mass (Appendix A): checked on the device in FP64 before any
+    // iteration is enqueued
+    st = run_input_check(k, mu_dev, n, false, s, "mu");
+    if (st != SE2OT_OK) return st;
+    long long launches = 2;
     CK(launch_init(mu_dev, k->lmu, k->lv, k->h1, k->h2, n, k->d.nx, k->d.ny, k->d.ntheta, s), "init launch");
     // tile maxima of lv = 0 for the first w-convolution (the update kernel writes them afterwards)
     const bool fused_max = k->d.boundary == SE2OT_BOUNDARY_ZERO;
@@ -490,7 +529,7 @@ se2ot_status se2ot_barycenter(se2ot_kernel k, int n, const float *mu, const doub
         ++launches;
         ++it;
         if (o.tol_viol > 0 && o.check_every > 0 && (it % o.check_every == 0) && it < max_it) {
-            CK(launch_stats(k->L, k->ld, lam, n, V, k->partial, k->scal, s), "stats launch");
+            CK(launch_stats(k->L, k->ld, k->lv, lam, n, V, k->partial, k->scal, s), "stats launch");
             launches += 2;
             double h[2];
             CK(cudaMemcpyAsync(h, k->scal, sizeof h, cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync(stats)");
@@ -502,12 +541,12 @@ se2ot_status se2ot_barycenter(se2ot_kernel k, int n, const float *mu, const doub
         }
     }
     CK(launch_finalize(k->L, bary_dev, k->d.nx, k->d.ny, k->d.ntheta, s), "finalize launch");
-    CK(launch_stats(k->L, k->ld, lam, n, V, k->partial, k->scal, s), "stats launch");
+    CK(launch_stats(k->L, k->ld, k->lv, lam, n, V, k->partial, k->scal, s), "stats launch");
     launches += 3;
     if (bary_host)
         CK(cudaMemcpyAsync(bary, bary_dev, (size_t)V * sizeof(float), cudaMemcpyDeviceToHost, s),
            "cudaMemcpyAsync(bary)");
-    double h[2];
+    double h[4];
     unsigned long long counts[2] = {0, 0};
     CK(cudaMemcpyAsync(h, k->scal, sizeof h, cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync(stats)");
     CK(cudaMemcpyAsync(counts, k->redo_total, sizeof counts, cudaMemcpyDeviceToHost, s),
@@ -527,6 +566,8 @@ se2ot_status se2ot_barycenter(se2ot_kernel k, int n, const float *mu, const doub
         stats->kernel_launches = launches;
         stats->redo_outputs = (long long)counts[0];
         stats->evaluated_terms = (long long)counts[1];
+        stats->logscale_min = h[2] * LN2;
+        stats->logscale_max = h[3] * LN2;
         if (timing) {
             double tot = 0.0;
             for (int j = 0; j < it; ++j)
@@ -600,6 +641,9 @@ se2ot_status se2ot_w2(se2ot_kernel k, const float *mu, const float *nu, const se
                        is_device_ptr(mu) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s), "cudaMemcpyAsync(mu)");
     CK(cudaMemcpyAsync(k->mu_stage + V, nu, (size_t)V * sizeof(float),
                        is_device_ptr(nu) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s), "cudaMemcpyAsync(nu)");
+    st = run_input_check(k, k->mu_stage, 2, false, s, "mu, nu");
+    if (st != SE2OT_OK) return st;
+    launches += 2;
     CK(launch_init(k->mu_stage, k->lmu, k->lv, k->h1, k->h2, 2, k->d.nx, k->d.ny, k->d.ntheta, s), "init launch");
     ++launches;
     const bool fused_max = k->d.boundary == SE2OT_BOUNDARY_ZERO;
@@ -738,6 +782,9 @@ se2ot_status se2ot_jko(se2ot_kernel k, const float *mu0, double tau, double m, i
         CK(cudaMemcpyAsync(k->mu_stage, mu0, (size_t)V * sizeof(float), cudaMemcpyHostToDevice, s), "cudaMemcpyAsync(mu0)");
         mu_dev = k->mu_stage;
     }
+    st = run_input_check(k, mu_dev, 1, true, s, "mu0");
+    if (st != SE2OT_OK) return st;
+    launches += 2;
     float *out_dev = mu_out;
     const bool out_host = !is_device_ptr(mu_out);
     if (out_host) {

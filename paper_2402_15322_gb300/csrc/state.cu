@@ -44,7 +44,7 @@ void layout(SolveState &st, Carve &c)
     st.ord = c.take<unsigned>(4 * ntm + 2);
     st.count = c.take<unsigned>(4);
     st.totals = c.take<unsigned long long>(2);
-    st.partial = c.take<double>(2 * STATS_BLOCKS);
+    st.partial = c.take<double>(STATS_PARTIAL);
     st.scal = c.take<double>(4);
 }
 
@@ -155,7 +155,7 @@ cudaError_t state_iterate(SolveState &st, int iters, cudaStream_t s)
 
 cudaError_t state_stats(SolveState &st, cudaStream_t s)
 {
-    return launch_stats(st.L, st.ld, st.lam, st.n, st.V, st.partial, st.scal, s);
+    return launch_stats(st.L, st.ld, st.lv, st.lam, st.n, st.V, st.partial, st.scal, s);
 }
 
 cudaError_t state_finish(SolveState &st, cudaStream_t s)

@@ -47,7 +47,8 @@ class se2ot_stats(ctypes.Structure):
                 ("ms", ctypes.c_double), ("voxel_iters_per_s", ctypes.c_double),
                 ("conv_ms", ctypes.c_double), ("conv_launches", ctypes.c_longlong),
                 ("kernel_launches", ctypes.c_longlong), ("redo_outputs", ctypes.c_longlong),
-                ("evaluated_terms", ctypes.c_longlong)]
+                ("evaluated_terms", ctypes.c_longlong), ("logscale_min", ctypes.c_double),
+                ("logscale_max", ctypes.c_double)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -111,12 +112,13 @@ def lib():
     L.se2ot_serve_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(i)]
     L.se2ot_serve_wait.argtypes = [vp, ctypes.c_uint64, vp, ctypes.POINTER(se2ot_stats), i]
     L.se2ot_serve_destroy.argtypes = [vp]
+    L.se2ot_sfu_ex2_rate.argtypes = [ctypes.POINTER(d), vp]
     L.se2ot_last_error.restype = ctypes.c_char_p
     L.se2ot_version.restype = ctypes.c_char_p
     for name in ("se2ot_kernel_build", "se2ot_kernel_destroy", "se2ot_kernel_taps", "se2ot_apply",
                  "se2ot_apply_log", "se2ot_barycenter", "se2ot_interpolate", "se2ot_barycenter_noalloc",
                  "se2ot_state_export", "se2ot_interpolate_batched", "se2ot_serve_create", "se2ot_serve_submit",
-                 "se2ot_serve_poll", "se2ot_serve_wait", "se2ot_serve_destroy"):
+                 "se2ot_serve_poll", "se2ot_serve_wait", "se2ot_serve_destroy", "se2ot_sfu_ex2_rate"):
         getattr(L, name).restype = ctypes.c_int
     _LIB = L
     return L
@@ -139,6 +141,36 @@ def _ptr(t, dtype):
     if not t.is_contiguous():
         raise ValueError("tensor must be contiguous")
     return ctypes.c_void_p(t.data_ptr())
+
+
+def _shape(desc):
+    return (desc.ny, desc.nx, desc.ntheta)
+
+
+def _need(t, shape, what, cuda=None, device=None):
+    """Argument check before a raw pointer is handed to the library: the C side reads and writes
+    exactly prod(shape) elements, so a smaller tensor would be an out-of-bounds access."""
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError("%s has shape %s, expected %s" % (what, tuple(t.shape), tuple(shape)))
+    if cuda is True and not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % what)
+    if device is not None and t.is_cuda and t.device != device:
+        raise ValueError("%s is on %s, expected %s" % (what, t.device, device))
+
+
+def _weights(lam, n):
+    lam = [float(x) for x in lam]
+    if len(lam) != n:
+        raise ValueError("%d weights for %d measures" % (len(lam), n))
+    return (ctypes.c_double * n)(*lam)
+
+
+def se2ot_sfu_ex2_rate(stream=None):
+    """Measured ex2 results per second of the current device (the SFU ceiling of the log-domain
+    convolution's evaluated terms)."""
+    v = ctypes.c_double()
+    _check(lib().se2ot_sfu_ex2_rate(ctypes.byref(v), _stream(stream)))
+    return v.value
 
 
 def se2ot_last_error():
@@ -209,9 +241,11 @@ def se2ot_kernel_taps(kernel):
 
 def se2ot_apply(kernel, f, out=None, stream=None):
     """out = K * f for f of shape [batch, ny, nx, ntheta] (float32, CUDA)."""
+    batch = f.numel() // kernel.V
+    _need(f, (batch,) + kernel.shape, "f", cuda=True)
     if out is None:
         out = torch.empty_like(f)
-    batch = f.numel() // kernel.V
+    _need(out, tuple(f.shape), "out", cuda=True, device=f.device)
     _check(lib().se2ot_apply(kernel.handle, _ptr(f, torch.float32), _ptr(out, torch.float32), batch,
                              _stream(stream)))
     return out
@@ -219,9 +253,11 @@ def se2ot_apply(kernel, f, out=None, stream=None):
 
 def se2ot_apply_log(kernel, lf, out=None, stream=None):
     """out = log(K * exp(lf)) (float64, CUDA)."""
+    batch = lf.numel() // kernel.V
+    _need(lf, (batch,) + kernel.shape, "lf", cuda=True)
     if out is None:
         out = torch.empty_like(lf)
-    batch = lf.numel() // kernel.V
+    _need(out, tuple(lf.shape), "out", cuda=True, device=lf.device)
     _check(lib().se2ot_apply_log(kernel.handle, _ptr(lf, torch.float64), _ptr(out, torch.float64), batch,
                                  _stream(stream)))
     return out
@@ -235,9 +271,11 @@ def se2ot_barycenter(kernel, mu, lam, opts=None, out=None, stream=None, raise_on
     """Barycenter of mu [n, ny, nx, ntheta] (float32, CUDA or pinned/pageable CPU) with weights
     lam (n floats).  Returns (bary, stats dict, status)."""
     n = mu.shape[0]
+    _need(mu, (n,) + kernel.shape, "mu")
     if out is None:
         out = torch.empty(mu.shape[1:], dtype=torch.float32, device=mu.device)
-    lam_c = (ctypes.c_double * n)(*[float(x) for x in lam])
+    _need(out, kernel.shape, "out")
+    lam_c = _weights(lam, n)
     st = se2ot_stats()
     status = lib().se2ot_barycenter(kernel.handle, n, _ptr(mu, torch.float32), lam_c,
                                     ctypes.byref(opts if opts is not None else solve_opts()),
@@ -262,6 +300,8 @@ def se2ot_state_export(kernel, n, device="cuda", stream=None):
 def se2ot_w2(kernel, mu, nu, opts=None, stream=None, raise_on_error=True):
     """Entropic transport between mu and nu (Sec. 4.1): returns (result dict with cost <c, pi>,
     dual, plan mass, first-marginal violation, iterations; status)."""
+    _need(mu, kernel.shape, "mu")
+    _need(nu, kernel.shape, "nu")
     res = se2ot_w2_result()
     status = lib().se2ot_w2(kernel.handle, _ptr(mu, torch.float32), _ptr(nu, torch.float32),
                             ctypes.byref(opts if opts is not None else solve_opts()), ctypes.byref(res),
@@ -274,8 +314,10 @@ def se2ot_w2(kernel, mu, nu, opts=None, stream=None, raise_on_error=True):
 def se2ot_jko(kernel, mu0, tau, m, steps, opts=None, out=None, stream=None, raise_on_error=True):
     """`steps` entropic JKO steps of the porous-medium energy sum mu^m / (m - 1) from mu0 [ny, nx, nt]
     (opts.max_iters scaling iterations per step).  Returns (mu, stats dict, status)."""
+    _need(mu0, kernel.shape, "mu0")
     if out is None:
         out = torch.empty_like(mu0)
+    _need(out, kernel.shape, "out")
     st = se2ot_stats()
     status = lib().se2ot_jko(kernel.handle, _ptr(mu0, torch.float32), float(tau), float(m), int(steps),
                              ctypes.byref(opts if opts is not None else solve_opts()), _ptr(out, torch.float32),
@@ -313,6 +355,8 @@ def se2ot_reconstruct_field(U, stream=None):
 def se2ot_interpolate_signed(kernel, U0, U1, t, opts=None, stream=None, raise_on_error=True):
     """Signed-score interpolation b_t = m+_t P(Phi_t(U0+, U1+)) - m-_t P(Phi_t(U0-, U1-)).
     Returns (b [ny, nx], [stats of the positive part, of the negative part], status)."""
+    _need(U0, kernel.shape, "U0", cuda=True)
+    _need(U1, kernel.shape, "U1", cuda=True, device=U0.device)
     ny, nx = U0.shape[:2]
     b = torch.empty((ny, nx), dtype=torch.float32, device=U0.device)
     st = (se2ot_stats * 2)()
@@ -326,8 +370,11 @@ def se2ot_interpolate_signed(kernel, U0, U1, t, opts=None, stream=None, raise_on
 
 def se2ot_interpolate(kernel, mu0, mu1, t, opts=None, out=None, stream=None, raise_on_error=True):
     """Phi_t(mu0, mu1): the barycenter with weights (1 - t, t)."""
+    _need(mu0, kernel.shape, "mu0")
+    _need(mu1, kernel.shape, "mu1")
     if out is None:
         out = torch.empty_like(mu0)
+    _need(out, kernel.shape, "out")
     st = se2ot_stats()
     status = lib().se2ot_interpolate(kernel.handle, _ptr(mu0, torch.float32), _ptr(mu1, torch.float32),
                                      float(t), ctypes.byref(opts if opts is not None else solve_opts()),
@@ -346,9 +393,11 @@ def se2ot_barycenter_noalloc(desc, mu, lam, opts=None, out=None, stream=None, ra
     workspace live in the library's static 16 MiB device array, shared by every call.
     Returns (bary, stats dict, status)."""
     n = mu.shape[0]
+    _need(mu, (n,) + _shape(desc), "mu", cuda=True)
     if out is None:
         out = torch.empty(mu.shape[1:], dtype=torch.float32, device=mu.device)
-    lam_c = (ctypes.c_double * n)(*[float(x) for x in lam])
+    _need(out, _shape(desc), "out", cuda=True, device=mu.device)
+    lam_c = _weights(lam, n)
     st = se2ot_stats()
     status = lib().se2ot_barycenter_noalloc(ctypes.byref(desc), n, _ptr(mu, torch.float32), lam_c,
                                             ctypes.byref(opts if opts is not None else solve_opts()),
@@ -362,8 +411,15 @@ def se2ot_interpolate_batched(descs, mu0s, mu1s, ts, opts=None, outs=None, strea
     """Batched interpolations: descs, mu0s, mu1s (CUDA float32 tensors [ny, nx, ntheta] per problem),
     ts (floats).  Returns (outs, list of stats dicts, status)."""
     n = len(descs)
+    if not (len(mu0s) == len(mu1s) == len(ts) == n):
+        raise ValueError("descs, mu0s, mu1s and ts must have the same length")
+    for p in range(n):
+        _need(mu0s[p], _shape(descs[p]), "mu0s[%d]" % p, cuda=True)
+        _need(mu1s[p], _shape(descs[p]), "mu1s[%d]" % p, cuda=True, device=mu0s[p].device)
     if outs is None:
         outs = [torch.empty_like(m) for m in mu0s]
+    for p in range(n):
+        _need(outs[p], _shape(descs[p]), "outs[%d]" % p, cuda=True, device=mu0s[p].device)
     darr = (se2ot_kernel_desc * n)(*descs)
     p0 = (ctypes.c_void_p * n)(*[_ptr(m, torch.float32).value for m in mu0s])
     p1 = (ctypes.c_void_p * n)(*[_ptr(m, torch.float32).value for m in mu1s])
@@ -389,14 +445,17 @@ class Server:
         h = ctypes.c_void_p()
         _check(lib().se2ot_serve_create(int(budget_bytes), int(max_slots), int(device), ctypes.byref(h)))
         self.handle = h
+        self._shapes = {}   # ticket -> result shape, to check the tensor wait() writes into
 
     def submit(self, desc, mu, lam, opts=None):
         """Queue a barycenter of mu [n, ny, nx, ntheta] (float32, CPU or CUDA); returns a ticket."""
         n = mu.shape[0]
+        _need(mu, (n,) + _shape(desc), "mu")
         t = ctypes.c_uint64()
-        lam_c = (ctypes.c_double * n)(*[float(x) for x in lam])
+        lam_c = _weights(lam, n)
         _check(lib().se2ot_serve_submit(self.handle, ctypes.byref(desc), n, _ptr(mu, torch.float32), lam_c,
                                         ctypes.byref(opts if opts is not None else solve_opts()), ctypes.byref(t)))
+        self._shapes[t.value] = _shape(desc)
         return t.value
 
     def poll(self, ticket):
@@ -406,9 +465,13 @@ class Server:
 
     def wait(self, ticket, out, timeout_ms=-1):
         """Copy the result into out (float32 tensor, CPU or CUDA); returns (stats dict, status)."""
+        if out is not None and ticket in self._shapes:
+            _need(out, self._shapes[ticket], "out")
         st = se2ot_stats()
         status = lib().se2ot_serve_wait(self.handle, ticket, _ptr(out, torch.float32) if out is not None else None,
                                         ctypes.byref(st), int(timeout_ms))
+        if status != SE2OT_ETIMEOUT:
+            self._shapes.pop(ticket, None)
         return st.as_dict(), status
 
     def close(self):

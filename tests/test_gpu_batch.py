@@ -75,3 +75,23 @@ def test_batch_rejects_what_it_does_not_support():
     assert st == se2ot.SE2OT_EINVAL
     _, _, st = se2ot.se2ot_interpolate_batched([d], [mu.cpu()], [mu], [0.5], raise_on_error=False)
     assert st == se2ot.SE2OT_EINVAL
+
+
+def test_batch_checks_every_problems_inputs():
+    """Each problem's pair must be measures of equal mass (Appendix A): a negative entry or unequal
+    masses in one problem of the batch is refused, naming that problem, before any iteration."""
+    d = se2ot.make_desc(32, 32, 8, 3, W, 5e-4)
+    good = torch.full((32, 32, 8), 1.0 / 8192, device="cuda")
+    neg = good.clone()
+    neg[3, 4, 5] = -1e-9
+    heavy = good * (1.0 + 1e-5)
+    for bad, words in ((neg, "negative"), (heavy, "masses differ")):
+        _, _, st = se2ot.se2ot_interpolate_batched([d, d], [good, good], [good, bad], [0.5, 0.5],
+                                                   se2ot.solve_opts(5), raise_on_error=False)
+        assert st == se2ot.SE2OT_EINVAL
+        msg = se2ot.se2ot_last_error()
+        assert "problem 1" in msg and words in msg
+    outs, stats, st = se2ot.se2ot_interpolate_batched([d, d], [good, good], [good, good], [0.5, 0.5],
+                                                      se2ot.solve_opts(5))
+    assert st == se2ot.SE2OT_OK and all(torch.isfinite(o).all() for o in outs)
+    assert all(s["logscale_min"] <= s["logscale_max"] for s in stats)

@@ -79,3 +79,17 @@ def test_jko_host_buffers_and_errors():
         _, _, status = se2ot.se2ot_jko(k, torch.from_numpy(mu0).cuda(), tau, m, steps, opts, raise_on_error=False)
         assert status == se2ot.SE2OT_EINVAL
     k.close()
+
+
+def test_jko_refuses_zero_or_nonfinite_densities():
+    """A zero density makes the b-update 0/0 (reading J2); zeros, negatives and non-finite entries
+    are refused before the first step."""
+    mu0 = torch.from_numpy(density(20, 20, 4, seed=8)).cuda()
+    k = se2ot.se2ot_kernel_build(se2ot.make_desc(20, 20, 4, 2, WJ, 5e-3))
+    for idx, val, words in (((2, 3, 1), 0.0, "zero entries"), ((5, 5, 0), -1.0, "negative"),
+                            ((7, 1, 2), float("nan"), "non-finite")):
+        bad = mu0.clone()
+        bad[idx] = val
+        _, _, status = se2ot.se2ot_jko(k, bad, 1e-3, 5.0, 1, se2ot.solve_opts(5), raise_on_error=False)
+        assert status == se2ot.SE2OT_EINVAL and words in se2ot.se2ot_last_error()
+    k.close()

@@ -215,13 +215,54 @@ def test_error_statuses():
     assert st == se2ot.SE2OT_EINVAL
     _, _, st = se2ot.se2ot_barycenter(k, mu, [0.5, 0.5], se2ot.solve_opts(0), raise_on_error=False)
     assert st == se2ot.SE2OT_EINVAL
-    bad = mu.clone()
-    bad[0, 3, 3, 1] = float("nan")
-    _, _, st = se2ot.se2ot_barycenter(k, bad, [0.5, 0.5], se2ot.solve_opts(5), raise_on_error=False)
-    assert st == se2ot.SE2OT_ENONFINITE
+    # inputs that are not measures of equal mass (Appendix A assumes them) are refused before any
+    # iteration, on device and host buffers alike
+    for edit, words in ((lambda b: b[0, 3, 3].__setitem__(1, float("nan")), "non-finite"),
+                        (lambda b: b[1, 2, 5].__setitem__(0, float("inf")), "non-finite"),
+                        (lambda b: b[0, 3, 3].__setitem__(1, -1e-7), "negative"),
+                        (lambda b: b[1].mul_(1.0 + 3e-6), "masses differ"),
+                        (lambda b: b[1].zero_(), "zero mass")):
+        for dev in ("cuda", "cpu"):
+            bad = mu.clone().to(dev)
+            edit(bad)
+            _, _, st = se2ot.se2ot_barycenter(k, bad, [0.5, 0.5], se2ot.solve_opts(5), raise_on_error=False)
+            assert st == se2ot.SE2OT_EINVAL, (words, dev)
+            assert words in se2ot.se2ot_last_error()
+    # masses equal within 1e-6 and a common scale of all inputs are accepted
+    ok = mu.clone()
+    ok[1].mul_(1.0 + 4e-7)
+    _, _, st = se2ot.se2ot_barycenter(k, ok, [0.5, 0.5], se2ot.solve_opts(5), raise_on_error=False)
+    assert st == se2ot.SE2OT_OK
+    _, _, st = se2ot.se2ot_barycenter(k, mu * 3.0, [0.5, 0.5], se2ot.solve_opts(5), raise_on_error=False)
+    assert st == se2ot.SE2OT_OK
+    # the binding refuses tensors that do not match the kernel's grid before calling the library
+    with pytest.raises(ValueError):
+        se2ot.se2ot_barycenter(k, mu[:, :10], [0.5, 0.5])
+    with pytest.raises(ValueError):
+        se2ot.se2ot_barycenter(k, mu, [1.0])
     # the handle is still usable after an error
     out, _, st = se2ot.se2ot_barycenter(k, mu, [0.5, 0.5], se2ot.solve_opts(5))
     assert st == se2ot.SE2OT_OK and torch.isfinite(out).all()
+
+
+def test_logscale_range_matches_exported_state():
+    """stats.logscale_min/max are the extreme natural logs of the scaling vectors v_i after the last
+    iteration (the dynamic range the log-domain storage exists for): they equal the min and max of
+    the exported state, and on the 32^2 x 8 workload they exceed FP32's exponent range."""
+    k, g = kernel(32, 32, 8, 3, 5e-4)
+    mu = torch.from_numpy(synth.measures(2, 32, 32, 8, config_seed=1, nbumps=4).astype(np.float32)).cuda()
+    _, st, _ = se2ot.se2ot_barycenter(k, mu, [0.5, 0.5], se2ot.solve_opts(100))
+    lv, _, _ = se2ot.se2ot_state_export(k, 2)
+    assert st["logscale_min"] == pytest.approx(float(lv.min()), rel=1e-12, abs=1e-9)
+    assert st["logscale_max"] == pytest.approx(float(lv.max()), rel=1e-12, abs=1e-9)
+    assert st["logscale_min"] < -88.0 and st["logscale_max"] > 88.0
+    # after the first iteration from v = 1 the range is a few nats, as the oracle's state says
+    _, st1, _ = se2ot.se2ot_barycenter(k, mu, [0.5, 0.5], se2ot.solve_opts(1))
+    _, ost = oracle.interpolate_log(g, mu[0].cpu().double().numpy(), mu[1].cpu().double().numpy(), 0.5, 1,
+                                    want_state=True)
+    assert st1["logscale_min"] == pytest.approx(float(ost["lv"].min()), rel=1e-5, abs=1e-5)
+    assert st1["logscale_max"] == pytest.approx(float(ost["lv"].max()), rel=1e-5, abs=1e-5)
+    k.close()
 
 
 # ------------------------------------------------------- the 128^2 x 16 barycenter workload

@@ -109,3 +109,67 @@ def test_injected_admission_failure_rejects_only_that_request():
         del os.environ["SE2OT_TEST_FAIL_ADMISSION"]
     assert [r[2] for r in res] == [se2ot.SE2OT_OK, se2ot.SE2OT_ENOMEM, se2ot.SE2OT_OK]
     assert torch.isfinite(res[0][0]).all() and torch.isfinite(res[2][0]).all()
+
+
+def test_submit_refuses_inputs_that_are_not_equal_mass_measures():
+    """The server runs se2ot_barycenter's input check on its host copy of the request."""
+    d, mu, lam, o = make(0)
+    sv = se2ot.Server(1 << 30, 2)
+    for edit, words in ((lambda m: m[0, 1, 1].__setitem__(0, float("nan")), "non-finite"),
+                        (lambda m: m[1].mul_(1.0 + 1e-5), "masses differ")):
+        bad = mu.clone()
+        edit(bad)
+        with pytest.raises(se2ot.SE2OTError) as ei:
+            sv.submit(d, bad, lam, o)
+        assert ei.value.status == se2ot.SE2OT_EINVAL and words in str(ei.value)
+    with pytest.raises(ValueError):
+        sv.submit(d, mu[:, :5], lam, o)
+    t = sv.submit(d, mu, lam, o)
+    out = torch.empty(mu.shape[1:], dtype=torch.float32)
+    st, status = sv.wait(t, out)
+    assert status == se2ot.SE2OT_OK and st["logscale_min"] <= st["logscale_max"]
+    sv.close()
+
+
+def test_server_on_a_fresh_process_races_a_solve_on_another_thread():
+    """Kernel attributes are set once per device under a lock: a server's worker thread and a
+    caller thread that launch their first convolutions at the same time in a fresh process both get
+    correct results (each equal to a later single-threaded solve)."""
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = r'''
+import sys, threading, numpy as np, torch
+sys.path.insert(0, %r)
+from paper_2402_15322_gb300 import se2ot, synth
+torch.cuda.set_device(0)
+W = (1.0, 3.0, 0.5)
+d1 = se2ot.make_desc(40, 36, 16, 10, W, 1e-3)
+d2 = se2ot.make_desc(48, 40, 8, 7, W, 2e-3)
+mu1 = torch.from_numpy(synth.coupled_measures(3, 40, 36, 16, 5, 1, nbumps=3).astype(np.float32))
+mu2 = torch.from_numpy(synth.coupled_measures(2, 48, 40, 8, 6, 1, nbumps=3).astype(np.float32))
+lam1, lam2 = [0.2, 0.3, 0.5], [0.5, 0.5]
+res = {}
+def solve():
+    k = se2ot.se2ot_kernel_build(d1)
+    res["solve"] = se2ot.se2ot_barycenter(k, mu1.cuda(), lam1, se2ot.solve_opts(30))[0].cpu()
+    k.close()
+th = threading.Thread(target=solve)
+sv = se2ot.Server(1 << 30, 2)
+th.start()
+t = sv.submit(d2, mu2, lam2, se2ot.solve_opts(30))
+out = torch.empty((40, 48, 8), dtype=torch.float32)
+st, status = sv.wait(t, out)
+th.join()
+sv.close()
+assert status == se2ot.SE2OT_OK
+k = se2ot.se2ot_kernel_build(d1)
+want1 = se2ot.se2ot_barycenter(k, mu1.cuda(), lam1, se2ot.solve_opts(30))[0].cpu()
+k = se2ot.se2ot_kernel_build(d2)
+want2 = se2ot.se2ot_barycenter(k, mu2.cuda(), lam2, se2ot.solve_opts(30))[0].cpu()
+assert torch.equal(res["solve"], want1), "threaded solve differs"
+assert torch.equal(out, want2), "served result differs"
+print("race ok")
+''' % root
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0 and "race ok" in r.stdout, r.stdout + r.stderr
