@@ -57,6 +57,11 @@ JKO = dict(tau=1e-3, m=5.0, steps=10, iters=50, eps=2e-3,
            workload="10 entropic JKO steps (50 scaling iterations each) of the porous-medium energy (m=5), "
                     "tau=1e-3, 128x128x16 SE(2) grid, kernel 21x21x16 (r=10), w=(1,sqrt(10),sqrt(2)), eps=2e-3, "
                     "FP32 log-domain path")
+SMOOTH_EPS = 1e-3
+SMOOTH_WORKLOAD = ("barycenter of 4 measures, 128x128x16 SE(2) grid, kernel 21x21x16 (r=10), w=(1,3,0.5), "
+                   "eps=1e-3 (ten times the headline's: potentials smooth enough for the tensor cores on every "
+                   "tile), 500 Sinkhorn iterations")
+GOLDEN = os.path.join(ROOT, "tests", "golden", "barycenter_128x128x16_r10_500it.json")
 # Other workloads (parity cases and scale points; not the headline line): `--config large` is the
 # 512^2 x 32 single solve, `--config batched` the 64 uneven interpolations.
 LARGE = dict(nx=512, ny=512, nt=32, r=15, eps=2e-5, n=3, iters=1000,
@@ -303,6 +308,20 @@ def conv_traffic():
     return rec.get("dram_bytes_per_launch")
 
 
+def golden_error(bary):
+    """Relative L1 error of a 500-iteration headline barycenter against the stored FP64 oracle run
+    (its 4096 sampled voxels and 8x8 block sums)."""
+    g = json.load(open(GOLDEN))
+    flat = bary.reshape(-1)
+    idx = np.asarray(g["sample_index"])
+    want = np.asarray(g["sample_value"])
+    ny, nx, nt = bary.shape
+    blocks = bary.reshape(ny // 8, 8, nx // 8, 8, nt).sum(axis=(1, 3, 4)).reshape(-1)
+    wb = np.asarray(g["block_sum_8x8"])
+    return {"sample": float(np.abs(flat[idx] - want).sum() / np.abs(want).sum()),
+            "block_8x8": float(np.abs(blocks - wb).sum() / np.abs(wb).sum())}
+
+
 def run_gpu(args):
     import torch
 
@@ -384,6 +403,11 @@ def run_gpu(args):
             mu_h = torch.from_numpy(large_inputs(problem=rank))
             iters = args.iters or LARGE["iters"]
             workload = LARGE["workload"]
+        elif args.config == "smooth":
+            nx, ny, nt, r, eps, n = NX, NY, NT, R, SMOOTH_EPS, N_MEAS
+            mu_h = torch.from_numpy(inputs(problem=rank))
+            iters = args.iters or ITERS
+            workload = SMOOTH_WORKLOAD
         else:
             nx, ny, nt, r, eps, n = NX, NY, NT, R, EPS, N_MEAS
             mu_h = torch.from_numpy(inputs(problem=rank))
@@ -397,8 +421,16 @@ def run_gpu(args):
         out = torch.empty((ny, nx, nt), dtype=torch.float32, device=device)
         mu_pin = mu_h.pin_memory()
         out_pin = torch.empty((ny, nx, nt), dtype=torch.float32).pin_memory()
-        opts = se2ot.solve_opts(iters)
-        opts_events = se2ot.solve_opts(iters, flags=se2ot.SE2OT_FLAG_TIME_CONV)
+        prec = se2ot.SE2OT_BF16TC if args.precision == "bf16" else se2ot.SE2OT_FP32
+        refine = min(args.refine, iters) if args.precision == "bf16" else 0
+        opts = se2ot.solve_opts(iters, precision=prec, refine_iters=refine)
+        opts_events = se2ot.solve_opts(iters, flags=se2ot.SE2OT_FLAG_TIME_CONV, precision=prec, refine_iters=refine)
+        if args.precision == "bf16":
+            base = workload.replace(", FP32 log-domain path", "")
+            workload = base + ", BF16 tensor cores with FP32 accumulation, the last %d iterations FP32" % refine
+        elif "FP32" not in workload:
+            workload += ", FP32 log-domain path"
+        cfg.update({"precision": args.precision, "refine_iters": refine})
 
         def solve(e2e=False, conv_events=False):
             if e2e:
@@ -415,6 +447,7 @@ def run_gpu(args):
     launches = 0
     redo = 0
     evaluated = 0
+    tc_tiles = [0, 0]
     barrier(world, device)
     torch.cuda.synchronize()
     ev0 = torch.cuda.Event(enable_timing=True)
@@ -427,6 +460,8 @@ def run_gpu(args):
             launches += st["kernel_launches"]
             redo += st["redo_outputs"]
             evaluated += st["evaluated_terms"]
+            tc_tiles[0] += st.get("tc_tiles", 0)
+            tc_tiles[1] += st.get("tc_fallback_tiles", 0)
         ev1.record(stream)
         torch.cuda.synchronize()
     barrier(world, device)
@@ -529,6 +564,13 @@ def run_gpu(args):
                         "terms all lie below 2^-64 of the output's shift are skipped"}
         if literal is not None:
             result["literal_inputs"] = literal
+        if args.precision == "bf16" and args.config in ("barycenter", "smooth", "large"):
+            result["dtype"] = "bf16"
+            result["tc"] = {"tiles_tensor_cores": tc_tiles[0], "tiles_fp32_fallback": tc_tiles[1],
+                            "share_tensor_cores": tc_tiles[0] / max(1, tc_tiles[0] + tc_tiles[1]),
+                            "tile": "4 output rows x 128 positions x all orientations, per convolution launch"}
+            if args.config == "barycenter" and os.path.exists(GOLDEN):
+                result["tc"]["rel_l1_vs_oracle"] = golden_error(out.cpu().double().numpy())
         result["clocks"] = clocks.summary()
     return result
 
@@ -590,7 +632,11 @@ def main(argv=None):
                     help="Sinkhorn iterations per solve (profiling runs only; default: the workload's)")
     ap.add_argument("--rate", type=float, default=0.0, help="serve: Poisson arrival rate (req/s)")
     ap.add_argument("--requests", type=int, default=0, help="serve: number of requests")
-    ap.add_argument("--config", default="barycenter", choices=["barycenter", "large", "batched", "serve", "w2", "jko"],
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"],
+                    help="bf16: the convolutions on the tcgen05 tensor cores (SE2OT_BF16TC)")
+    ap.add_argument("--refine", type=int, default=20, help="bf16: last iterations on the FP32 path")
+    ap.add_argument("--config", default="barycenter", choices=["barycenter", "large", "batched", "serve", "w2", "jko",
+                                                                "smooth"],
                     help="workload: the 128^2x16 barycenter (default, the headline), the 512^2x32 "
                          "large solve, or the 64-problem uneven batch")
     args = ap.parse_args(argv)

@@ -65,7 +65,9 @@ typedef enum {
 } se2ot_status;
 
 typedef enum {
-    SE2OT_FP32 = 0         /* log-domain convolution, FP32 terms, FP64 log storage          */
+    SE2OT_FP32 = 0,        /* log-domain convolution, FP32 terms, FP64 log storage          */
+    SE2OT_BF16TC = 1       /* tcgen05 tensor cores, BF16 operands, FP32 accumulation, on the
+                              tiles a per-tile rescaling can represent; FP32 path elsewhere   */
 } se2ot_precision;
 
 typedef enum {
@@ -93,13 +95,17 @@ typedef struct se2ot_kernel_s *se2ot_kernel;   /* opaque; owns tap tables and wo
 /* Solver options.  max_iters >= 1 Sinkhorn iterations (one iteration = every line of the
  * Appendix A loop body).  check_every > 0 together with tol_viol > 0 evaluates the marginal
  * violation every check_every iterations (a host synchronisation each time) and stops once
- * viol <= tol_viol.  flags: bitwise OR of SE2OT_FLAG_*. */
+ * viol <= tol_viol.  flags: bitwise OR of SE2OT_FLAG_*.
+ * precision SE2OT_BF16TC runs the convolutions on the tensor cores (see se2ot_apply) except for
+ * the last refine_iters (0 <= refine_iters <= max_iters) of the max_iters iterations, which run on
+ * the FP32 path (refinement sweeps); refine_iters is ignored for SE2OT_FP32. */
 typedef struct {
     int max_iters;
     int check_every;
     double tol_viol;
     int precision;               /* se2ot_precision */
     int flags;
+    int refine_iters;
 } se2ot_solve_opts;
 
 #define SE2OT_FLAG_TIME_CONV 1   /* time every convolution launch with CUDA events (stats.conv_ms) */
@@ -124,7 +130,10 @@ typedef struct {
  *                    v_i over all measures and voxels after the last iteration (FP64, finite entries
  *                    only): the dynamic range the solve needed, the reason the library keeps the
  *                    scaling vectors as logarithms (FP32 holds e^-87 .. e^88, FP64 e^-708 .. e^709).
- *                    Not measured by se2ot_jko (0). */
+ *                    Not measured by se2ot_jko (0).
+ *   tc_tiles, tc_fallback_tiles  SE2OT_BF16TC: tiles of 4 rows x 128 positions (all orientations)
+ *                    the tensor cores computed, and those they left to the FP32 path because a
+ *                    per-tile rescaling could not represent them (0 for SE2OT_FP32). */
 typedef struct {
     int iters;
     double mass, viol, ms, voxel_iters_per_s;
@@ -134,6 +143,7 @@ typedef struct {
     long long redo_outputs;
     long long evaluated_terms;
     double logscale_min, logscale_max;
+    long long tc_tiles, tc_fallback_tiles;
 } se2ot_stats;
 
 /* Build the kernel for a grid: validates desc, evaluates the taps
@@ -155,13 +165,21 @@ SE2OT_API se2ot_status se2ot_kernel_taps(se2ot_kernel k, float *taps_host);
 
 /* out = K * f for `batch` fields (Sec. 4.2).  f and out: device pointers to batch*V floats,
  * f >= 0 (zeros allowed), may not alias.  Evaluated as exp2 of a log-domain convolution.
- * EINVAL on batch < 1 or NULL pointers. */
-SE2OT_API se2ot_status se2ot_apply(se2ot_kernel k, const float *f, float *out, int batch, void *stream);
+ * precision: SE2OT_FP32, or SE2OT_BF16TC for the tcgen05 tensor cores (ntheta <= 16, nx >= 64):
+ * per tile of 4 rows x 128 positions and all orientations, the log-domain sum is rescaled by a
+ * tilt plane fitted to the outputs, one shift per input and per output orientation, and computed
+ * as a GEMM of BF16 operands with FP32 accumulation (relative error of an output ~1e-3, BF16
+ * rounding).  Tiles whose rescaled operands cannot represent every output go to the FP32 path,
+ * outputs whose accumulator is too small to be trusted to the exact recompute; the result is
+ * therefore never worse than BF16 rounding.  EINVAL on batch < 1, NULL pointers, an unknown
+ * precision or an unsupported grid. */
+SE2OT_API se2ot_status se2ot_apply(se2ot_kernel k, const float *f, float *out, int batch, int precision, void *stream);
 
 /* lout = log(K * exp(lf)) (natural logarithms) for `batch` fields: device pointers to
- * batch*V doubles; -inf entries of lf are zero densities.  May not alias. */
-SE2OT_API se2ot_status se2ot_apply_log(se2ot_kernel k, const double *lf, double *lout, int batch,
-                             void *stream);
+ * batch*V doubles; -inf entries of lf are zero densities.  May not alias.  precision as in
+ * se2ot_apply. */
+SE2OT_API se2ot_status se2ot_apply_log(se2ot_kernel k, const double *lf, double *lout, int batch, int precision,
+                                       void *stream);
 
 /* Barycenter of n >= 1 measures with weights lambda (Appendix A; Eq. barywass with the
  * entropic kernel of Sec. 4.2).  mu: n*V floats, host or device memory (detected).  The inputs

@@ -73,6 +73,7 @@ __global__ void redo_kernel(ConvArgs a0, const ConvArgs *probs)
     if (!a0.release_early) pdl_launch_dependents();
     const unsigned n = *a0.redo_count;
     if (a0.redo_clear && blockIdx.x == 0 && threadIdx.x == 0) *a0.redo_clear = 0;
+    if (a0.fb_clear && blockIdx.x == 0 && threadIdx.x == 0) *a0.fb_clear = 0;
     const int lane = threadIdx.x & 31;
     const int wpb = blockDim.x >> 5;
     const long nwarps = (long)gridDim.x * wpb;
@@ -181,14 +182,18 @@ int conv_tiles(int nx, int ny) { return ((nx + tile::TX - 1) / tile::TX) * ((ny 
 
 size_t conv_smem_bytes(int r) { return sizeof(float) * tile::smem_floats(r); }
 
+cudaError_t launch_tile_max(const ConvArgs &a, cudaStream_t s)
+{
+    if (a.tmax_ready && !a.periodic) return cudaSuccess;
+    dim3 g((a.nx + tile::TX - 1) / tile::TX, (a.ny + tile::TY - 1) / tile::TY, a.batch * a.nt);
+    tile_max_kernel<<<g, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_conv(const ConvArgs &a, cudaStream_t s)
 {
-    if (!a.tmax_ready || a.periodic) {
-        dim3 g((a.nx + tile::TX - 1) / tile::TX, (a.ny + tile::TY - 1) / tile::TY, a.batch * a.nt);
-        tile_max_kernel<<<g, 256, 0, s>>>(a);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-    }
+    cudaError_t e = launch_tile_max(a, s);
+    if (e != cudaSuccess) return e;
     return dispatch(a.r, a, false, nullptr, nullptr, 0, s);
 }
 

@@ -1,0 +1,586 @@
+// conv_tc.cu -- the SE(2) group convolution (Sec. 4.2) on the tcgen05 tensor cores: BF16 operands,
+// FP32 accumulation in tensor memory, for the tiles whose log-domain sum a per-tile rescaling makes
+// representable.  Every other tile is queued for the FP32 log-domain kernel (conv_tile.cuh).
+//
+// The log-domain convolution  out(p, o) = log2 sum_{i, d} 2^(lk(o, i, d) + lf(p - d, i))  is a GEMM
+// C[p, o] = sum_{(i, d)} A[p, (i, d)] B[(i, d), o] once each exponent is split into a part of the
+// input position and a part of the tap.  A tile of S = 4 output rows x 128 positions takes one
+// tilt plane P(y, x) = gy y + gx x (least squares on the previous outputs of the same
+// convolution), a shift alpha_i per input slice and c_o per output orientation:
+//   A(q, i)    = 2^(lf(q, i) - P(q) - alpha_i)                 (BF16, <= 2^55)
+//   B(i, d, o) = 2^(lk(o, i, d) - P(d) + alpha_i - c_o)        (BF16, <= 2^55)
+//   out(p, o)  = log2 C[p, o] + P(p) + c_o                     (q + d = p, so P(q) + P(d) = P(p))
+// with alpha_i = max_q (lf - P) - 55 over the tile's halo and c_o such that the largest possible
+// product is 2^110 (a sum of at most 2^13 terms stays below FP32's 2^128).  A product of two BF16
+// values >= 2^-126 each is exact in the FP32 accumulator, so a term is lost to underflow only when
+// one factor is below 2^-126, i.e. when the product is below 2^(55 - 126) = 2^-71.  An output with
+// log2 C >= -40 therefore loses only terms below 2^-31 of itself (at most 2^13 of them: < 4e-6
+// relative), far below the BF16 rounding of its operands (each within 2^-8, a product within
+// 2^-7 relative): such outputs are accepted; the others are queued for the exact recompute
+// (conv.cu).  A tile whose previous outputs predict log2 C < -30 anywhere is not computed here: its
+// 16 x 32 tiles of the FP32 kernel are queued in a work list that the FP32 kernel runs next.
+//
+// GEMM shape: M = 128 positions of one row (an MMA of the instruction shape 128 x N x 16), K = the
+// 16 input orientations of one tap, N = 16 output orientations x the output rows that one input row
+// q feeds (dy = y - q in [-r, r]).  The A operand of tap dx is the staged input row q shifted by dx
+// positions: in the no-swizzle K-major layout a row of 8 channels is 16 bytes, so the shift is a
+// 16-byte offset of the shared-memory descriptor.  Per input row q and tap dx one MMA covers every
+// output row of the tile that q reaches, with the B blocks of consecutive dy stored consecutively.
+// Producer warps fill a ring of input rows (A) and a ring of dy blocks of taps (B) while one warp
+// issues the MMAs; tcgen05.commit on an mbarrier frees the slots.  Every wait is bounded.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "dfloat.cuh"
+#include "internal.h"
+
+namespace se2ot {
+
+namespace {
+
+constexpr int TC_S = 4;            // output rows of a tile
+constexpr int TC_M = 128;          // positions of a row (MMA M)
+constexpr int TC_NT = 16;          // orientation slots (K of one tap, N of one output row)
+constexpr int TC_THREADS = 256;    // warps 0-6 produce operands, warp 7 issues the MMAs
+constexpr int TC_PRODUCERS = 224;
+constexpr int NA = 3;              // input-row slots
+constexpr int NB = TC_S + 1;       // dy-block slots
+constexpr int NST = 4;             // pipeline stages of the barriers
+constexpr int APLANE = (TC_M + 2 * MAX_RADIUS) * 16;   // bytes of one half (8 channels) of an input row
+constexpr float A_TOP = 55.f, PMAX = 110.f;
+constexpr float ELIG_MIN = -30.f, ACCEPT_MIN = -40.f;
+constexpr long SPIN_LIMIT = 1L << 24;
+
+__host__ __device__ constexpr int bplane(int D) { return D * NB * 256; }
+__host__ __device__ constexpr size_t tc_smem(int D) { return (size_t)NA * 2 * APLANE + 2 * (size_t)bplane(D); }
+
+__device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor: no swizzle, K-major core matrices of 8 rows x 16 bytes; lbo = byte
+// distance between the two 8-element halves of K, sbo = between groups of 8 rows; version 1.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::f16: BF16 A and B, FP32 D, both K-major, M = 128, N.
+__device__ __forceinline__ uint32_t idesc(int n)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id)
+{
+    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, 1, 0;\n"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+                 "l"(a), "l"(b), "r"(id)
+                 : "memory");
+}
+
+__device__ __forceinline__ void commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void bar_init(uint64_t *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void bar_arrive(uint64_t *bar)
+{
+    asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}" ::"r"(su32(bar)) : "memory");
+}
+
+// Wait for the phase of parity `par` of an mbarrier, at most SPIN_LIMIT polls; false if it gave up.
+__device__ __forceinline__ bool bar_wait(uint64_t *bar, uint32_t par)
+{
+    for (long it = 0; it < SPIN_LIMIT; ++it) {
+        uint32_t ok;
+        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+                     : "=r"(ok)
+                     : "r"(su32(bar)), "r"(par)
+                     : "memory");
+        if (ok) return true;
+        if (it > 64) __nanosleep(64);
+    }
+    return false;
+}
+
+__device__ __forceinline__ float ex2f(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ uint32_t pack2(float lo, float hi)
+{
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t *>(&v);
+}
+
+// Float maximum through integer atomics (valid for any mix of signs; the location starts at -inf).
+__device__ __forceinline__ void atomic_fmax(float *addr, float v)
+{
+    if (v >= 0.f) atomicMax((int *)addr, __float_as_int(v));
+    else atomicMin((unsigned *)addr, __float_as_uint(v));
+}
+
+__device__ __forceinline__ int wrapi(int v, int n)
+{
+    v %= n;
+    return v < 0 ? v + n : v;
+}
+
+__device__ __forceinline__ void epilogue_out(const ConvArgs &a, long flat, int b, int o, int y, int x, float sh, float l)
+{
+    const float2 s = make_float2(sh, 0.f);
+    switch (a.epi) {
+    case EPI_LOG_OUT:
+        a.out64[(((long)b * a.ny + y) * a.nx + x) * a.nt + o] = ((double)sh + (double)l) * a.out_scale;
+        break;
+    case EPI_LIN_OUT:
+        a.out32[(((long)b * a.ny + y) * a.nx + x) * a.nt + o] = (float)exp2((double)sh + (double)l);
+        break;
+    case EPI_W: {
+        const float2 c = df_add(s, make_float2(l, 0.f));
+        a.out2[flat] = df_add(a.aux[flat], df_neg(c));
+        a.hint[flat] = c.x + c.y;
+        break;
+    }
+    default: {
+        const float2 c = df_add(s, make_float2(l, 0.f));
+        a.out2[flat] = df_add(a.aux[flat], c);
+        a.hint[flat] = c.x + c.y;
+        break;
+    }
+    }
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 2) tc_conv_kernel(const ConvArgs a, const TcArgs t)
+{
+    pdl_launch_dependents();
+    pdl_wait();
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char *sA = smem, *sB = smem + NA * 2 * APLANE;
+    __shared__ __align__(8) uint64_t full_bar[NST], empty_bar[NST], done_bar;
+    __shared__ uint32_t s_tmem;
+    __shared__ float s_alpha[TC_NT], s_rmax[TC_NT], s_c[TC_NT], s_tmx[TC_NT * TC_NT];
+    __shared__ float s_part[TC_THREADS / 32][TC_NT];
+    __shared__ double s_red[TC_THREADS / 32][9];
+    __shared__ float s_g[2];
+    __shared__ int s_ok, s_abort;
+
+    const int nx = a.nx, ny = a.ny, nt = a.nt, r = a.r, D = 2 * r + 1;
+    const int x0 = blockIdx.x * TC_M, y0 = blockIdx.y * TC_S, b = blockIdx.z;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const long plane = (long)nx * ny;
+    const float2 *in_b = a.in + (long)b * nt * plane;
+    const int BPL = bplane(D);
+
+    // ---- 1. tilt plane: least squares of the previous outputs (the shifts) over the tile.
+    //      sum_{p,o} (S(p,o) - c_o - gy Y_p - gx X_p)^2 with Y, X relative to the tile origin; the
+    //      per-orientation intercepts drop out of the slopes because every valid position has all nt
+    //      orientations.  FP64 sums (positions up to 512, shifts up to ~1e4).
+    double q9[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};   // n, Y, X, YY, XX, XY, T, YT, XT (T = sum_o S)
+    bool finite = true;
+    for (int e = tid; e < TC_S * TC_M; e += TC_THREADS) {
+        const int s = e / TC_M, m = e - s * TC_M, y = y0 + s, x = x0 + m;
+        if (y >= ny || x >= nx) continue;
+        double T = 0.0;
+        for (int o = 0; o < nt; ++o) {
+            const float h = a.hint[((long)(b * nt + o) * ny + y) * nx + x];
+            finite &= isfinite(h);
+            T += (double)h;
+        }
+        const double Y = s, X = m;
+        q9[0] += 1.0; q9[1] += Y; q9[2] += X; q9[3] += Y * Y; q9[4] += X * X; q9[5] += X * Y;
+        q9[6] += T; q9[7] += Y * T; q9[8] += X * T;
+    }
+#pragma unroll
+    for (int k = 0; k < 9; ++k)
+#pragma unroll
+        for (int off = 16; off; off >>= 1) q9[k] += __shfl_xor_sync(0xffffffffu, q9[k], off);
+    if (lane == 0)
+        for (int k = 0; k < 9; ++k) s_red[warp][k] = q9[k];
+    const int all_finite = __syncthreads_and(finite);
+    if (tid == 0) {
+        double s9[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        for (int w = 0; w < TC_THREADS / 32; ++w)
+            for (int k = 0; k < 9; ++k) s9[k] += s_red[w][k];
+        const double n = s9[0];
+        const double syy = (s9[3] - s9[1] * s9[1] / n) * nt, sxx = (s9[4] - s9[2] * s9[2] / n) * nt;
+        const double sxy = (s9[5] - s9[1] * s9[2] / n) * nt;
+        const double syt = s9[7] - s9[1] * s9[6] / n, sxt = s9[8] - s9[2] * s9[6] / n;
+        double gy = 0.0, gx = 0.0;
+        const double det = syy * sxx - sxy * sxy;
+        if (det > 1e-9 * (syy * sxx + 1.0)) {
+            gy = (syt * sxx - sxt * sxy) / det;
+            gx = (sxt * syy - syt * sxy) / det;
+        } else if (sxx > 0.0) {
+            gx = sxt / sxx;
+        } else if (syy > 0.0) {
+            gy = syt / syy;
+        }
+        s_g[0] = (float)gy;
+        s_g[1] = (float)gx;
+        s_ok = all_finite && n > 0.0;
+        s_abort = 0;
+    }
+    __syncthreads();
+    const float gy = s_g[0], gx = s_g[1];
+    const int HX = TC_M + 2 * r, HY = TC_S + 2 * r;
+
+    // ---- 2. largest residual R_i = max (lf - P) of every input slice over the halo (hi parts).
+    //      A NaN or +inf input makes the tile ineligible.
+    float rm[TC_NT];
+#pragma unroll
+    for (int i = 0; i < TC_NT; ++i) rm[i] = -INFINITY;
+    bool bad = false;
+    if (s_ok) {
+        for (int e = tid; e < HY * HX; e += TC_THREADS) {
+            const int hy = e / HX, hx = e - hy * HX;
+            int qy = y0 - r + hy, qx = x0 - r + hx;
+            if (qx >= x0 + TC_M + r) continue;
+            if (a.periodic) {
+                qy = wrapi(qy, ny);
+                qx = wrapi(qx, nx);
+            } else if (qy < 0 || qy >= ny || qx < 0 || qx >= nx) {
+                continue;
+            }
+            const float P = gy * (float)(hy - r) + gx * (float)(hx - r);
+#pragma unroll
+            for (int i = 0; i < TC_NT; ++i) {
+                if (i >= nt) break;
+                const float h = in_b[(long)i * plane + (long)qy * nx + qx].x;
+                bad |= !(h <= 3.0e38f) && h == h && h > 0.f;   // +inf
+                bad |= h != h;                                   // NaN
+                rm[i] = fmaxf(rm[i], h - P);
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < TC_NT; ++i) {
+#pragma unroll
+        for (int off = 16; off; off >>= 1) rm[i] = fmaxf(rm[i], __shfl_xor_sync(0xffffffffu, rm[i], off));
+        if (lane == 0) s_part[warp][i] = rm[i];
+    }
+    const int any_bad = __syncthreads_or(bad);
+    if (tid < TC_NT) {
+        float m = -INFINITY;
+        for (int w = 0; w < TC_THREADS / 32; ++w) m = fmaxf(m, s_part[w][tid]);
+        s_rmax[tid] = m;
+        s_alpha[tid] = isfinite(m) ? m - A_TOP : 0.f;
+    }
+    if (tid == 0 && any_bad) s_ok = 0;
+    __syncthreads();
+
+    // ---- 3. largest tilted tap of every orientation pair, Tmax(o, i) = max_d lk(o, i, d) - P(d)
+    //      (thread = pair; the combined tap table is [dy][dx][o][i]), then c_o.
+    if (s_ok) {
+        const int o = tid / TC_NT, i = tid - o * TC_NT;
+        float tm = -INFINITY;
+        if (o < nt && i < nt)
+            for (int dyi = 0; dyi < D; ++dyi)
+                for (int dxi = 0; dxi < D; ++dxi)
+                    tm = fmaxf(tm, t.lk[((dyi * D + dxi) * TC_NT + o) * TC_NT + i] - (gy * (float)(dyi - r) +
+                                                                                      gx * (float)(dxi - r)));
+        s_tmx[tid] = tm;
+    }
+    __syncthreads();
+    if (s_ok && tid < TC_NT) {
+        float c = -INFINITY;
+        for (int i = 0; i < nt; ++i)
+            if (isfinite(s_rmax[i])) c = fmaxf(c, s_rmax[i] + s_tmx[tid * TC_NT + i]);
+        s_c[tid] = isfinite(c) ? c - PMAX : 0.f;
+        if (tid < nt && !isfinite(c)) s_ok = 0;
+    }
+    __syncthreads();
+
+    // ---- 4. eligibility: the previous outputs predict log2 C = S - P(p) - c_o >= ELIG_MIN everywhere
+    bool elig = s_ok != 0;
+    if (elig) {
+        for (int e = tid; e < TC_S * TC_M; e += TC_THREADS) {
+            const int s = e / TC_M, m = e - s * TC_M, y = y0 + s, x = x0 + m;
+            if (y >= ny || x >= nx) continue;
+            const float P = gy * (float)s + gx * (float)m;
+            for (int o = 0; o < nt; ++o) {
+                const float h = a.hint[((long)(b * nt + o) * ny + y) * nx + x];
+                elig &= h - P - s_c[o] >= ELIG_MIN;
+            }
+        }
+    }
+    elig = __syncthreads_and(elig);
+    if (!elig) {
+        // queue the FP32 kernel's 16 x 32 tiles (every orientation) that cover this tile, once each
+        if (tid == 0) {
+            const int ntx = (nx + TILE_X - 1) / TILE_X, nty = (ny + TILE_Y - 1) / TILE_Y;
+            const int ty = y0 / TILE_Y;
+            for (int tx = x0 / TILE_X; tx < ntx && tx * TILE_X < x0 + TC_M; ++tx) {
+                unsigned *cl = t.fb_claim + ((long)b * nty + ty) * ntx + tx;
+                if (atomicMax(cl, t.seq) < t.seq) {
+                    const unsigned k = atomicAdd(t.fb_count, (unsigned)nt);
+                    for (int o = 0; o < nt; ++o) t.fb_items[k + o] = make_int4(0, b * nt + o, tx, ty);
+                }
+            }
+            atomicAdd(t.tiles + 1, 1ull);
+        }
+        return;
+    }
+
+    // ---- 5. the GEMM.  TMEM: 64 columns, output row s at columns [16 s, 16 s + 16).
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&s_tmem)),
+                     "r"(TC_S * TC_NT)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int k = 0; k < NST; ++k) {
+            bar_init(&full_bar[k], 1);
+            bar_init(&empty_bar[k], 1);
+        }
+        bar_init(&done_bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = s_tmem;
+    if (warp < 4) {   // zero the accumulators (every MMA accumulates)
+        const uint32_t ta = tmem + ((uint32_t)(32 * warp) << 16);
+#pragma unroll
+        for (int c = 0; c < TC_S * TC_NT; c += 16)
+            asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};"
+                         ::"r"(ta + c), "r"(0u)
+                         : "memory");
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+
+    const int NQ = TC_S + 2 * r;   // input rows y0 - r .. y0 + S - 1 + r
+    if (warp < 7) {
+        // producers: step qi stages input row q = y0 - r + qi in A slot qi % NA and, for qi <= 2r,
+        // the taps of dy = r - qi in B slot (dy + r) % NB.  Slots of step qi were last read by the MMAs
+        // of step qi - 2 (B: dy + NB used up to step qi - NB + S - 1 = qi - 2; A: step qi - 3).
+        for (int qi = 0; qi < NQ; ++qi) {
+            // every producer waits with the same bound; the decision to stop is one vote of all
+            // producers, so none is left behind in the named barrier below
+            const uint32_t gave_up = qi >= 2 && !bar_wait(&empty_bar[(qi - 2) % NST], ((qi - 2) / NST) & 1);
+            uint32_t any;
+            asm volatile("{\n.reg .pred p, q;\nsetp.ne.u32 p, %1, 0;\nbar.red.or.pred q, 1, %2, p;\nselp.u32 %0, 1, 0, q;\n}"
+                         : "=r"(any)
+                         : "r"(gave_up), "n"(TC_PRODUCERS)
+                         : "memory");
+            if (any) {
+                if (tid == 0) {
+                    s_abort = 1;
+                    atomicExch(t.err, 1u);
+                }
+                break;
+            }
+            unsigned char *ar = sA + (qi % NA) * 2 * APLANE;
+            int qy = y0 - r + qi;
+            bool row_in = true;
+            if (a.periodic) qy = wrapi(qy, ny);
+            else row_in = qy >= 0 && qy < ny;
+            const float Pq = gy * (float)(qi - r);
+            for (int e = tid; e < 2 * HX; e += TC_PRODUCERS) {
+                const int ih = e / HX, hx = e - ih * HX;
+                int qx = x0 - r + hx;
+                bool in = row_in && qx < x0 + TC_M + r;
+                if (a.periodic) qx = wrapi(qx, nx);
+                else in = in && qx >= 0 && qx < nx;
+                float v[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const int i = 8 * ih + k;
+                    v[k] = 0.f;
+                    if (in && i < nt) {
+                        const float2 h = in_b[(long)i * plane + (long)qy * nx + qx];
+                        const float ex = ((h.x - s_alpha[i]) - (Pq + gx * (float)(hx - r))) + h.y;
+                        v[k] = ex2f(ex);   // -inf input: 0
+                    }
+                }
+                uint4 w = make_uint4(pack2(v[0], v[1]), pack2(v[2], v[3]), pack2(v[4], v[5]), pack2(v[6], v[7]));
+                *reinterpret_cast<uint4 *>(ar + ih * APLANE + hx * 16) = w;
+            }
+            if (qi <= 2 * r) {
+                const int dyi = 2 * r - qi, sl = (2 * r - qi) % NB;   // dy = r - qi, slot (dy + r) % NB
+                const float Py = gy * (float)(dyi - r);
+                for (int e = tid; e < D * TC_NT * 2; e += TC_PRODUCERS) {
+                    const int ih = e & 1, o = (e >> 1) & (TC_NT - 1), dxi = e >> 5;
+                    const float4 *src = reinterpret_cast<const float4 *>(t.lk + ((dyi * D + dxi) * TC_NT + o) * TC_NT + 8 * ih);
+                    const float4 l0 = __ldg(src), l1 = __ldg(src + 1);
+                    const float lv[8] = {l0.x, l0.y, l0.z, l0.w, l1.x, l1.y, l1.z, l1.w};
+                    const float base = -(Py + gx * (float)(dxi - r)) - s_c[o];
+                    float v[8];
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) v[k] = ex2f(lv[k] + base + s_alpha[8 * ih + k]);
+                    uint4 w = make_uint4(pack2(v[0], v[1]), pack2(v[2], v[3]), pack2(v[4], v[5]), pack2(v[6], v[7]));
+                    *reinterpret_cast<uint4 *>(sB + ih * BPL + (dxi * NB + sl) * 256 + o * 16) = w;
+                }
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("bar.sync 1, %0;" ::"n"(TC_PRODUCERS) : "memory");
+            if (tid == 0) bar_arrive(&full_bar[qi % NST]);
+        }
+    } else if (lane == 0) {
+        // the MMA issuer: step qi covers output rows s in [max(0, qi - 2r), min(S - 1, qi)] with
+        // dy = s - qi + r, B slots (s - qi + 2r) % NB ascending in s (split where the ring wraps)
+        const uint32_t a0 = su32(sA), b0 = su32(sB);
+        for (int qi = 0; qi < NQ; ++qi) {
+            if (!bar_wait(&full_bar[qi % NST], (qi / NST) & 1)) {
+                s_abort = 1;
+                atomicExch(t.err, 1u);
+            }
+            if (s_abort) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int s_lo = max(0, qi - 2 * r), s_hi = min(TC_S - 1, qi);
+            const int sl_lo = (s_lo - qi + 2 * r) % NB;
+            const int run1 = min(s_hi - s_lo + 1, NB - sl_lo);   // rows before the ring wraps
+            const uint32_t arow = a0 + (qi % NA) * 2 * APLANE;
+            for (int dxi = 0; dxi < D; ++dxi) {
+                const uint64_t da = sdesc(arow + (2 * r - dxi) * 16, APLANE, 128);
+                mma(tmem + s_lo * TC_NT, da, sdesc(b0 + (dxi * NB + sl_lo) * 256, BPL, 128), idesc(TC_NT * run1));
+                if (run1 < s_hi - s_lo + 1)
+                    mma(tmem + (s_lo + run1) * TC_NT, da, sdesc(b0 + (dxi * NB) * 256, BPL, 128),
+                        idesc(TC_NT * (s_hi - s_lo + 1 - run1)));
+            }
+            commit(&empty_bar[qi % NST]);
+        }
+        commit(&done_bar);
+    }
+
+    // ---- 6. epilogue: warps 0-3 read their 32 lanes (positions) of every output row
+    float omax[TC_NT];
+#pragma unroll
+    for (int o = 0; o < TC_NT; ++o) omax[o] = -INFINITY;
+    if (warp < 4) {
+        if (!bar_wait(&done_bar, 0)) {
+            s_abort = 1;
+            atomicExch(t.err, 1u);
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int m = 32 * warp + lane, x = x0 + m;
+        for (int s = 0; s < TC_S; ++s) {
+            uint32_t v[16];
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                         : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                           "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                           "=r"(v[14]), "=r"(v[15])
+                         : "r"(tmem + ((uint32_t)(32 * warp) << 16) + s * TC_NT));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            const int y = y0 + s;
+            if (y >= ny || x >= nx || s_abort) continue;
+            const float P = gy * (float)s + gx * (float)m;
+#pragma unroll
+            for (int o = 0; o < TC_NT; ++o) {
+                if (o >= nt) break;
+                const long flat = ((long)(b * nt + o) * ny + y) * nx + x;
+                const float C = __uint_as_float(v[o]);
+                const float lc = log2f(C);
+                if (!(lc >= ACCEPT_MIN && lc <= 127.f)) {
+                    const unsigned k = atomicAdd(a.redo_count, 1u);
+                    a.redo_list[k] = make_int2(0, (int)flat);
+                    omax[o] = INFINITY;
+                    continue;
+                }
+                epilogue_out(a, flat, b, o, y, x, P + s_c[o], lc);
+                if (a.tmax_out) omax[o] = fmaxf(omax[o], a.out2[flat].x);
+            }
+        }
+        if (a.tmax_out) {   // inner-tile maxima of the output for the FP32 kernel's 16 x 32 tiles
+            const int ntx = (nx + TILE_X - 1) / TILE_X, nty = (ny + TILE_Y - 1) / TILE_Y;
+            const int tx = (x0 + 32 * warp) / TILE_X, ty = y0 / TILE_Y;
+#pragma unroll
+            for (int o = 0; o < TC_NT; ++o) {
+                if (o >= nt) break;
+                float mv = omax[o];
+#pragma unroll
+                for (int off = 16; off; off >>= 1) mv = fmaxf(mv, __shfl_xor_sync(0xffffffffu, mv, off));
+                if (lane == 0 && tx < ntx && mv > -INFINITY)
+                    atomic_fmax(a.tmax_out + ((long)(b * nt + o) * nty + ty) * ntx + tx, mv);
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_S * TC_NT) : "memory");
+    if (tid == 0) atomicAdd(t.tiles, 1ull);
+}
+
+// Combined taps for the tensor-core kernel: lk[dy][dx][o][i] = ltheta(o, i) + ls(o, i, dy, dx) in FP32,
+// orientation slots beyond nt set to -inf.
+__global__ void tc_taps_kernel(const float2 *ltheta, const float *ls, const float *ls_lo, int nt, int D, float *lk)
+{
+    const long total = (long)D * D * TC_NT * TC_NT;
+    for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+        const int i = (int)(idx % TC_NT), o = (int)((idx / TC_NT) % TC_NT);
+        const long dd = idx / (TC_NT * TC_NT);
+        const int dxi = (int)(dd % D), dyi = (int)(dd / D);
+        float v = -INFINITY;
+        if (o < nt && i < nt) {
+            const long p = (long)o * nt + i;
+            const long k = (p * D + dyi) * D + dxi;
+            v = (float)(((double)ltheta[p].x + (double)ltheta[p].y) + ((double)ls[k] + (double)ls_lo[k]));
+        }
+        lk[idx] = v;
+    }
+}
+
+// Set the tile maxima an EPI_W launch of the tensor-core kernel accumulates into to -inf.
+__global__ void fill_kernel(float *p, long n, float v)
+{
+    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x) p[k] = v;
+}
+
+}  // namespace
+
+bool tc_supported(const se2ot_kernel_desc &d) { return d.ntheta <= TC_NT && d.radius <= MAX_RADIUS && d.nx >= TC_M / 2; }
+
+size_t tc_taps_floats(const se2ot_kernel_desc &d)
+{
+    const long D = 2 * d.radius + 1;
+    return (size_t)D * D * TC_NT * TC_NT;
+}
+
+cudaError_t build_tc_taps(const se2ot_kernel_desc &d, const Taps &taps, float *lk, cudaStream_t s)
+{
+    const int D = 2 * d.radius + 1;
+    const long total = (long)tc_taps_floats(d);
+    tc_taps_kernel<<<(int)std::min(4096L, (total + 255) / 256), 256, 0, s>>>(taps.ltheta, taps.ls, taps.ls_lo, d.ntheta,
+                                                                             D, lk);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill(float *p, long n, float v, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    fill_kernel<<<(int)std::min(1024L, (n + 255) / 256), 256, 0, s>>>(p, n, v);
+    return cudaGetLastError();
+}
+
+int tc_tiles(int nx, int ny) { return ((nx + TC_M - 1) / TC_M) * ((ny + TC_S - 1) / TC_S); }
+
+cudaError_t launch_conv_tc(const ConvArgs &a, const TcArgs &t, cudaStream_t s)
+{
+    const int D = 2 * a.r + 1;
+    const size_t smem = tc_smem(D);
+    static PerDeviceOnce attrs;
+    cudaError_t e = attrs.run([&]() {
+        return cudaFuncSetAttribute(tc_conv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem(2 * MAX_RADIUS + 1));
+    });
+    if (e != cudaSuccess) return e;
+    dim3 grid((a.nx + TC_M - 1) / TC_M, (a.ny + TC_S - 1) / TC_S, a.batch);
+    PdlLaunch L(grid, dim3(TC_THREADS), smem, s);
+    return cudaLaunchKernelEx(&L.cfg, tc_conv_kernel, a, t);
+}
+
+}  // namespace se2ot

@@ -182,6 +182,7 @@ __global__ void __launch_bounds__(THREADS, 6) conv_tile_kernel(const ConvArgs a0
     int p = 0, bo, tx, ty;
     unsigned tile_id = 0;   // single problem: (bo * tiles y + ty) * tiles x + tx; batch: the item index
     if (BATCHED) {
+        if (a0.item_count && blockIdx.x >= *a0.item_count) return;   // a device-built work list
         tile_id = a0.order ? a0.order[blockIdx.x] : blockIdx.x;
         const int4 it = items[tile_id];
         p = it.x;

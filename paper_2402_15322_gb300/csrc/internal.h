@@ -56,6 +56,19 @@ struct ConvArgs {
     int sort_order;
     int nx, ny, nt, r, periodic, batch, epi;
     int release_early;       // the recompute pass releases the next kernel before its wait (pdl_release_early)
+    const unsigned *item_count;  // batched launches: if not NULL, only items [0, *item_count) are computed
+    unsigned *fb_clear;      // if not NULL: set to 0 by the recompute pass (the tensor-core fallback count)
+};
+
+// Arguments of the tensor-core convolution (conv_tc.cu) beyond ConvArgs.
+struct TcArgs {
+    const float *lk;              // [D][D][16][16] combined taps log2 K (lt + ls), -inf beyond ntheta
+    int4 *fb_items;               // FP32-kernel work items (problem 0, b * nt + o, tile x, tile y) of the
+    unsigned *fb_count;           //   tiles this launch could not represent, and their number
+    unsigned *fb_claim;           // [batch][tiles y][tiles x] of the FP32 kernel: launch number that queued it
+    unsigned seq;                 // this launch's number (> every earlier one on the same claim array)
+    unsigned *err;                // set to 1 if a bounded wait gave up (the results are then invalid)
+    unsigned long long *tiles;    // [0] += tiles computed on the tensor cores, [1] += tiles queued
 };
 
 // Device tap tables of one kernel handle.
@@ -122,6 +135,8 @@ cudaError_t build_taps(const se2ot_kernel_desc &d, Taps &t, cudaStream_t s, bool
                        double *cost_scale = nullptr);
 // tile-max pre-pass + summing convolution (needs a.hint holding a shift for every output)
 cudaError_t launch_conv(const ConvArgs &a, cudaStream_t s);
+// the tile-max pre-pass alone (nothing when a producer already wrote the maxima)
+cudaError_t launch_tile_max(const ConvArgs &a, cudaStream_t s);
 // same tiling, writing the largest term of every output to a.hint (the shift of a later launch)
 cudaError_t launch_conv_max(const ConvArgs &a, cudaStream_t s);
 cudaError_t launch_redo(const ConvArgs &a, int max_blocks, cudaStream_t s);
@@ -132,6 +147,14 @@ cudaError_t launch_conv_batch(int r, const ConvArgs &shared, const ConvArgs *pro
                               cudaStream_t s);
 cudaError_t launch_redo_batch(const ConvArgs &shared, const ConvArgs *probs, int max_blocks, cudaStream_t s);
 int conv_tiles(int nx, int ny);          // spatial tiles of one slice (size of tmax per slice)
+// Tensor-core convolution (conv_tc.cu): supported grids (ntheta <= 16), its tap table size and
+// builder, the launch (one CTA per 4 x 128 tile of every field), and a fill helper.
+bool tc_supported(const se2ot_kernel_desc &d);
+size_t tc_taps_floats(const se2ot_kernel_desc &d);
+cudaError_t build_tc_taps(const se2ot_kernel_desc &d, const Taps &taps, float *lk, cudaStream_t s);
+cudaError_t launch_conv_tc(const ConvArgs &a, const TcArgs &t, cudaStream_t s);
+int tc_tiles(int nx, int ny);
+cudaError_t launch_fill(float *p, long n, float v, cudaStream_t s);
 // Whether a convolution of `tiles` CTAs gets a heaviest-first launch order: only when the launch
 // has few waves.  With the one-CTA sort on every launch, the 54-wave 512^2 x 32 launches lost
 // 7.7% to it; with the sort on every 8th launch they would gain 0.5%.

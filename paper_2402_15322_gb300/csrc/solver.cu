@@ -147,6 +147,16 @@ struct se2ot_kernel_s {
     double *w2p = nullptr;                     // se2ot_w2 reductions: 5 * STATS_BLOCKS partials + 5 sums
     float2 *zero = nullptr;                    // V zeros (se2ot_jko: the aux of the K a convolution)
     size_t c_zero = 0;
+    // tensor-core path (SE2OT_BF16TC), set up on first use
+    float *lk_tc = nullptr;                    // combined taps [D][D][16][16]
+    int4 *fb_items = nullptr;                  // FP32-kernel work list of the tiles the tensor cores leave
+    size_t c_fb = 0;
+    unsigned *fb = nullptr;                    // [0] work-list length, [1] error flag of bounded waits
+    unsigned *fb_claim = nullptr;              // launch number that queued each FP32-kernel tile
+    size_t c_claim = 0;
+    unsigned long long *tc_count = nullptr;    // [0] tensor-core tiles, [1] tiles left to the FP32 path
+    ConvArgs *d_args = nullptr;                // device copies of the two lines' arguments (work-list launches)
+    unsigned tc_seq = 0;
     std::vector<cudaEvent_t> ev;
 };
 
@@ -257,6 +267,79 @@ se2ot_status run_input_check(se2ot_kernel k, const float *mu_dev, int n, bool po
     return check_inputs(h, n, positive_entries, k->V, what);
 }
 
+// Buffers of the tensor-core path for `batch` fields (grown on demand; the taps built once).
+se2ot_status ensure_tc(se2ot_kernel k, int batch, cudaStream_t s)
+{
+    if (!k->lk_tc) {
+        CK(cudaMalloc((void **)&k->lk_tc, tc_taps_floats(k->d) * sizeof(float)), "cudaMalloc(tc taps)");
+        CK(build_tc_taps(k->d, k->taps, k->lk_tc, s), "tc tap build");
+        CK(cudaMalloc((void **)&k->fb, 2 * sizeof(unsigned)), "cudaMalloc(tc counters)");
+        CK(cudaMalloc((void **)&k->tc_count, 2 * sizeof(unsigned long long)), "cudaMalloc(tc counters)");
+        CK(cudaMalloc((void **)&k->d_args, 2 * sizeof(ConvArgs)), "cudaMalloc(tc args)");
+    }
+    const size_t tiles = (size_t)batch * conv_tiles(k->d.nx, k->d.ny);
+    if (k->c_claim < tiles) {
+        if (k->fb_claim) cudaFree(k->fb_claim);
+        k->fb_claim = nullptr;
+        k->c_claim = 0;
+        CK(cudaMalloc((void **)&k->fb_claim, tiles * sizeof(unsigned)), "cudaMalloc(tc claims)");
+        CK(cudaMemsetAsync(k->fb_claim, 0, tiles * sizeof(unsigned), s), "cudaMemsetAsync(tc claims)");
+        k->c_claim = tiles;
+        k->tc_seq = 0;
+    }
+    CK(grow(k->fb_items, k->c_fb, tiles * k->d.ntheta), "cudaMalloc(tc work list)");
+    // an output can be queued for the exact recompute twice: by the tensor-core epilogue and by the
+    // FP32 kernel that recomputes its whole 16 x 32 tile for a neighbouring strip
+    CK(grow(k->redo, k->c_redo, 2 * (size_t)batch * k->V), "cudaMalloc(redo)");
+    CK(cudaMemsetAsync(k->fb, 0, 2 * sizeof(unsigned), s), "cudaMemsetAsync(tc counters)");
+    CK(cudaMemsetAsync(k->tc_count, 0, 2 * sizeof(unsigned long long), s), "cudaMemsetAsync(tc counters)");
+    return SE2OT_OK;
+}
+
+// One convolution on the tensor-core path: [tile-max pre-pass,] [tile maxima of the output set to
+// -inf,] the tensor-core kernel, the FP32 kernel over the work list of the tiles it could not
+// represent, and the exact recompute pass (which also empties the work list for the next launch).
+// line (0 or 1) selects the device copy of the arguments the work-list launch reads; it is uploaded
+// when the recompute counter of the line changes.
+se2ot_status run_conv_tc(se2ot_kernel k, const ConvArgs &a0, int line, cudaStream_t s, long long *launches,
+                         cudaEvent_t t0 = nullptr, cudaEvent_t t1 = nullptr, ConvArgs *uploaded = nullptr)
+{
+    ConvArgs a = a0;
+    a.redo_count = k->counters + k->phase;
+    a.redo_clear = k->counters + (1 - k->phase);
+    a.order = nullptr;
+    a.sort_order = 0;
+    k->phase = 1 - k->phase;
+    if (!uploaded || std::memcmp(uploaded, &a, sizeof a) != 0) {
+        CK(cudaMemcpyAsync(k->d_args + line, &a, sizeof a, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync(tc args)");
+        if (uploaded) *uploaded = a;
+    }
+    const long tiles = (long)a.batch * a.nt * conv_tiles(a.nx, a.ny);
+    if (t0) CK(cudaEventRecord(t0, s), "cudaEventRecord");
+    CK(launch_tile_max(a, s), "tile-max launch");
+    if (a.tmax_out) {
+        CK(launch_fill(a.tmax_out, tiles, -INFINITY, s), "fill launch");
+        if (launches) ++*launches;
+    }
+    TcArgs t;
+    t.lk = k->lk_tc;
+    t.fb_items = k->fb_items;
+    t.fb_count = k->fb;
+    t.fb_claim = k->fb_claim;
+    t.seq = ++k->tc_seq;
+    t.err = k->fb + 1;
+    t.tiles = k->tc_count;
+    CK(launch_conv_tc(a, t, s), "tensor-core conv launch");
+    ConvArgs shared = a;
+    shared.item_count = k->fb;
+    CK(launch_conv_batch(a.r, shared, k->d_args + line, k->fb_items, (int)tiles, s), "work-list conv launch");
+    if (t1) CK(cudaEventRecord(t1, s), "cudaEventRecord");
+    a.fb_clear = k->fb;
+    CK(launch_redo(a, 2 * k->sms, s), "redo launch");
+    if (launches) *launches += ((a.tmax_ready && !a.periodic) ? 3 : 4);
+    return SE2OT_OK;
+}
+
 }  // namespace
 
 namespace se2ot {
@@ -340,7 +423,8 @@ se2ot_status se2ot_kernel_destroy(se2ot_kernel k)
     cudaDeviceSynchronize();
     void *ptrs[] = {k->taps.ltheta, k->taps.ls, k->taps.ls_lo, k->taps.lsrow, k->tmax, k->tmax2, k->lmu, k->lv, k->lw, k->ld, k->L, k->lf, k->h1, k->h2, k->hint_ws,
                     k->mu_stage, k->bary_stage, k->redo, k->counters, k->redo_total, k->partial, k->scal, k->chk, k->ord, k->ctaps.ltheta, k->ctaps.ls,
-                    k->ctaps.ls_lo, k->ctaps.lsrow, k->w2p, k->zero};
+                    k->ctaps.ls_lo, k->ctaps.lsrow, k->w2p, k->zero, k->lk_tc, k->fb_items, k->fb,
+                    k->fb_claim, k->tc_count, k->d_args};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : k->ev) cudaEventDestroy(e);
@@ -367,9 +451,32 @@ se2ot_status se2ot_kernel_taps(se2ot_kernel k, float *taps_host)
     return SE2OT_OK;
 }
 
-se2ot_status se2ot_apply(se2ot_kernel k, const float *f, float *out, int batch, void *stream)
+// The convolution of an apply call on the chosen path (the shifts come from a max pass).
+static se2ot_status apply_conv(se2ot_kernel k, ConvArgs &a, int precision, cudaStream_t s)
+{
+    CK(launch_conv_max(a, s), "conv max-pass launch");
+    se2ot_status rs = reset_counters(k, s);
+    if (rs != SE2OT_OK) return rs;
+    if (precision != SE2OT_BF16TC) return run_conv(k, a, s, nullptr);
+    rs = ensure_tc(k, a.batch, s);
+    if (rs != SE2OT_OK) return rs;
+    a.redo_list = k->redo;   // ensure_tc may have grown the recompute list
+    return run_conv_tc(k, a, 0, s, nullptr);
+}
+
+static se2ot_status check_precision(se2ot_kernel k, int precision)
+{
+    if (precision != SE2OT_FP32 && precision != SE2OT_BF16TC) return fail(SE2OT_EINVAL, "precision=%d unknown", precision);
+    if (precision == SE2OT_BF16TC && !tc_supported(k->d))
+        return fail(SE2OT_EINVAL, "the tensor-core path supports ntheta <= 16 and nx >= 64 (grid %dx%dx%d)", k->d.nx,
+                    k->d.ny, k->d.ntheta);
+    return SE2OT_OK;
+}
+
+se2ot_status se2ot_apply(se2ot_kernel k, const float *f, float *out, int batch, int precision, void *stream)
 {
     if (!k || !f || !out) return fail(SE2OT_EINVAL, "NULL argument");
+    if (check_precision(k, precision) != SE2OT_OK) return SE2OT_EINVAL;
     if (batch < 1) return fail(SE2OT_EINVAL, "batch=%d < 1", batch);
     if ((double)batch * k->V >= 2147483647.0 || (double)batch * k->d.ntheta > 65535.0)
         return fail(SE2OT_EINVAL, "batch too large");
@@ -385,14 +492,13 @@ se2ot_status se2ot_apply(se2ot_kernel k, const float *f, float *out, int batch, 
     a.in = k->lf;
     a.hint = k->hint_ws;
     a.out32 = out;
-    CK(launch_conv_max(a, s), "conv max-pass launch");
-    se2ot_status rs = reset_counters(k, s);
-    return rs == SE2OT_OK ? run_conv(k, a, s, nullptr) : rs;
+    return apply_conv(k, a, precision, s);
 }
 
-se2ot_status se2ot_apply_log(se2ot_kernel k, const double *lf, double *lout, int batch, void *stream)
+se2ot_status se2ot_apply_log(se2ot_kernel k, const double *lf, double *lout, int batch, int precision, void *stream)
 {
     if (!k || !lf || !lout) return fail(SE2OT_EINVAL, "NULL argument");
+    if (check_precision(k, precision) != SE2OT_OK) return SE2OT_EINVAL;
     if (batch < 1) return fail(SE2OT_EINVAL, "batch=%d < 1", batch);
     if ((double)batch * k->V >= 2147483647.0 || (double)batch * k->d.ntheta > 65535.0)
         return fail(SE2OT_EINVAL, "batch too large");
@@ -409,9 +515,7 @@ se2ot_status se2ot_apply_log(se2ot_kernel k, const double *lf, double *lout, int
     a.hint = k->hint_ws;
     a.out64 = lout;
     a.out_scale = LN2;
-    CK(launch_conv_max(a, s), "conv max-pass launch");
-    se2ot_status rs = reset_counters(k, s);
-    return rs == SE2OT_OK ? run_conv(k, a, s, nullptr) : rs;
+    return apply_conv(k, a, precision, s);
 }
 
 se2ot_status se2ot_barycenter(se2ot_kernel k, int n, const float *mu, const double *lambda,
@@ -425,7 +529,14 @@ se2ot_status se2ot_barycenter(se2ot_kernel k, int n, const float *mu, const doub
     se2ot_solve_opts o = {100, 0, 0.0, SE2OT_FP32, 0};
     if (opts) o = *opts;
     if (o.max_iters < 1) return fail(SE2OT_EINVAL, "max_iters=%d < 1", o.max_iters);
-    if (o.precision != SE2OT_FP32) return fail(SE2OT_EINVAL, "precision=%d unsupported", o.precision);
+    if (o.precision != SE2OT_FP32 && o.precision != SE2OT_BF16TC)
+        return fail(SE2OT_EINVAL, "precision=%d unknown", o.precision);
+    const bool tc = o.precision == SE2OT_BF16TC;
+    if (tc && !tc_supported(k->d))
+        return fail(SE2OT_EINVAL, "the tensor-core path supports ntheta <= 16 and nx >= 64 (grid %dx%dx%d)", k->d.nx,
+                    k->d.ny, k->d.ntheta);
+    if (tc && (o.refine_iters < 0 || o.refine_iters > o.max_iters))
+        return fail(SE2OT_EINVAL, "refine_iters=%d not in [0, max_iters]", o.refine_iters);
     if (o.tol_viol < 0 || !std::isfinite(o.tol_viol)) return fail(SE2OT_EINVAL, "tol_viol invalid");
     Lambdas lam;
     double lsum = 0.0;
@@ -444,6 +555,10 @@ se2ot_status se2ot_barycenter(se2ot_kernel k, int n, const float *mu, const doub
     const size_t nV = (size_t)n * V;
     se2ot_status st = ensure_solver_ws(k, n);
     if (st != SE2OT_OK) return st;
+    if (tc) {
+        st = ensure_tc(k, n, s);   // before any ConvArgs takes the workspace pointers
+        if (st != SE2OT_OK) return st;
+    }
     st = reset_counters(k, s);
     if (st != SE2OT_OK) return st;
 
@@ -512,6 +627,10 @@ se2ot_status se2ot_barycenter(se2ot_kernel k, int n, const float *mu, const doub
     ad.tmax = k->tmax2;
     ad.tmax_w = k->tmax2;
     ad.tmax_ready = fused_max;
+    ConvArgs up[2];   // the argument copies the tensor-core path's work-list launches read
+    std::memset(up, 0, sizeof up);
+    // the last refine_iters iterations of a tensor-core solve run on the FP32 path (refinement sweeps)
+    const int tc_iters = tc ? max_it - o.refine_iters : 0;
 
     int it = 0;
     double viol = NAN, mass = NAN;
@@ -519,10 +638,17 @@ se2ot_status se2ot_barycenter(se2ot_kernel k, int n, const float *mu, const doub
     for (it = 0; it < max_it;) {
         cudaEvent_t *e = timing ? &k->ev[(size_t)4 * it] : nullptr;
         aw.sort_order = ad.sort_order = order_sort_launch(it);
-        st = run_conv(k, aw, s, &launches, e ? e[0] : nullptr, e ? e[1] : nullptr);
-        if (st != SE2OT_OK) return st;
-        st = run_conv(k, ad, s, &launches, e ? e[2] : nullptr, e ? e[3] : nullptr);
-        if (st != SE2OT_OK) return st;
+        if (it < tc_iters) {
+            st = run_conv_tc(k, aw, 0, s, &launches, e ? e[0] : nullptr, e ? e[1] : nullptr, &up[0]);
+            if (st != SE2OT_OK) return st;
+            st = run_conv_tc(k, ad, 1, s, &launches, e ? e[2] : nullptr, e ? e[3] : nullptr, &up[1]);
+            if (st != SE2OT_OK) return st;
+        } else {
+            st = run_conv(k, aw, s, &launches, e ? e[0] : nullptr, e ? e[1] : nullptr);
+            if (st != SE2OT_OK) return st;
+            st = run_conv(k, ad, s, &launches, e ? e[2] : nullptr, e ? e[3] : nullptr);
+            if (st != SE2OT_OK) return st;
+        }
         CK(launch_update(k->lv, k->ld, k->L, lam, n, k->d.nx, k->d.ny, k->d.ntheta, fused_max ? k->tmax : nullptr,
                          aw.release_early, s),
            "update launch");
@@ -547,11 +673,17 @@ se2ot_status se2ot_barycenter(se2ot_kernel k, int n, const float *mu, const doub
         CK(cudaMemcpyAsync(bary, bary_dev, (size_t)V * sizeof(float), cudaMemcpyDeviceToHost, s),
            "cudaMemcpyAsync(bary)");
     double h[4];
-    unsigned long long counts[2] = {0, 0};
+    unsigned long long counts[2] = {0, 0}, tcc[2] = {0, 0};
+    unsigned tc_err[2] = {0, 0};
     CK(cudaMemcpyAsync(h, k->scal, sizeof h, cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync(stats)");
     CK(cudaMemcpyAsync(counts, k->redo_total, sizeof counts, cudaMemcpyDeviceToHost, s),
        "cudaMemcpyAsync(counters)");
+    if (tc) {
+        CK(cudaMemcpyAsync(tcc, k->tc_count, sizeof tcc, cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync(tc counters)");
+        CK(cudaMemcpyAsync(tc_err, k->fb, sizeof tc_err, cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync(tc counters)");
+    }
     CK(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    if (tc_err[1]) return fail(SE2OT_ECUDA, "a bounded wait of the tensor-core kernel gave up; results are invalid");
     mass = h[0];
     viol = h[1];
     k->last_n = n;
@@ -568,6 +700,8 @@ se2ot_status se2ot_barycenter(se2ot_kernel k, int n, const float *mu, const doub
         stats->evaluated_terms = (long long)counts[1];
         stats->logscale_min = h[2] * LN2;
         stats->logscale_max = h[3] * LN2;
+        stats->tc_tiles = (long long)tcc[0];
+        stats->tc_fallback_tiles = (long long)tcc[1];
         if (timing) {
             double tot = 0.0;
             for (int j = 0; j < it; ++j)

@@ -24,6 +24,7 @@ SE2OT_ENOTCONV = 5
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENONFINITE", 5: "ENOTCONV",
                 6: "ETIMEOUT", 7: "EBUSY", 8: "ESHUTDOWN"}
 SE2OT_FP32 = 0
+SE2OT_BF16TC = 1
 SE2OT_BOUNDARY_ZERO = 0
 SE2OT_BOUNDARY_PERIODIC = 1
 SE2OT_DIST_RHO_B, SE2OT_DIST_RHO_C = 0, 1
@@ -39,7 +40,8 @@ class se2ot_kernel_desc(ctypes.Structure):
 
 class se2ot_solve_opts(ctypes.Structure):
     _fields_ = [("max_iters", ctypes.c_int), ("check_every", ctypes.c_int),
-                ("tol_viol", ctypes.c_double), ("precision", ctypes.c_int), ("flags", ctypes.c_int)]
+                ("tol_viol", ctypes.c_double), ("precision", ctypes.c_int), ("flags", ctypes.c_int),
+                ("refine_iters", ctypes.c_int)]
 
 
 class se2ot_stats(ctypes.Structure):
@@ -48,7 +50,8 @@ class se2ot_stats(ctypes.Structure):
                 ("conv_ms", ctypes.c_double), ("conv_launches", ctypes.c_longlong),
                 ("kernel_launches", ctypes.c_longlong), ("redo_outputs", ctypes.c_longlong),
                 ("evaluated_terms", ctypes.c_longlong), ("logscale_min", ctypes.c_double),
-                ("logscale_max", ctypes.c_double)]
+                ("logscale_max", ctypes.c_double), ("tc_tiles", ctypes.c_longlong),
+                ("tc_fallback_tiles", ctypes.c_longlong)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -85,8 +88,8 @@ def lib():
     L.se2ot_kernel_build.argtypes = [ctypes.POINTER(se2ot_kernel_desc), vp, ctypes.POINTER(vp)]
     L.se2ot_kernel_destroy.argtypes = [vp]
     L.se2ot_kernel_taps.argtypes = [vp, vp]
-    L.se2ot_apply.argtypes = [vp, vp, vp, i, vp]
-    L.se2ot_apply_log.argtypes = [vp, vp, vp, i, vp]
+    L.se2ot_apply.argtypes = [vp, vp, vp, i, i, vp]
+    L.se2ot_apply_log.argtypes = [vp, vp, vp, i, i, vp]
     L.se2ot_barycenter.argtypes = [vp, i, vp, vp, ctypes.POINTER(se2ot_solve_opts), vp,
                                    ctypes.POINTER(se2ot_stats), vp]
     L.se2ot_interpolate.argtypes = [vp, vp, vp, d, ctypes.POINTER(se2ot_solve_opts), vp,
@@ -239,32 +242,34 @@ def se2ot_kernel_taps(kernel):
     return out
 
 
-def se2ot_apply(kernel, f, out=None, stream=None):
-    """out = K * f for f of shape [batch, ny, nx, ntheta] (float32, CUDA)."""
+def se2ot_apply(kernel, f, out=None, stream=None, precision=SE2OT_FP32):
+    """out = K * f for f of shape [batch, ny, nx, ntheta] (float32, CUDA); precision SE2OT_FP32 or
+    SE2OT_BF16TC (tensor cores)."""
     batch = f.numel() // kernel.V
     _need(f, (batch,) + kernel.shape, "f", cuda=True)
     if out is None:
         out = torch.empty_like(f)
     _need(out, tuple(f.shape), "out", cuda=True, device=f.device)
     _check(lib().se2ot_apply(kernel.handle, _ptr(f, torch.float32), _ptr(out, torch.float32), batch,
-                             _stream(stream)))
+                             int(precision), _stream(stream)))
     return out
 
 
-def se2ot_apply_log(kernel, lf, out=None, stream=None):
-    """out = log(K * exp(lf)) (float64, CUDA)."""
+def se2ot_apply_log(kernel, lf, out=None, stream=None, precision=SE2OT_FP32):
+    """out = log(K * exp(lf)) (float64, CUDA); precision as in se2ot_apply."""
     batch = lf.numel() // kernel.V
     _need(lf, (batch,) + kernel.shape, "lf", cuda=True)
     if out is None:
         out = torch.empty_like(lf)
     _need(out, tuple(lf.shape), "out", cuda=True, device=lf.device)
     _check(lib().se2ot_apply_log(kernel.handle, _ptr(lf, torch.float64), _ptr(out, torch.float64), batch,
-                                 _stream(stream)))
+                                 int(precision), _stream(stream)))
     return out
 
 
-def solve_opts(max_iters=100, check_every=0, tol_viol=0.0, precision=SE2OT_FP32, flags=0):
-    return se2ot_solve_opts(int(max_iters), int(check_every), float(tol_viol), int(precision), int(flags))
+def solve_opts(max_iters=100, check_every=0, tol_viol=0.0, precision=SE2OT_FP32, flags=0, refine_iters=0):
+    return se2ot_solve_opts(int(max_iters), int(check_every), float(tol_viol), int(precision), int(flags),
+                            int(refine_iters))
 
 
 def se2ot_barycenter(kernel, mu, lam, opts=None, out=None, stream=None, raise_on_error=True):

@@ -74,7 +74,7 @@ def test_unknown_boundary_or_distance_is_rejected_on_the_host(lib):
 
 def test_null_arguments_are_rejected(lib):
     assert lib.se2ot_kernel_build(None, None, None) == se2ot.SE2OT_EINVAL
-    assert lib.se2ot_apply(None, None, None, 1, None) == se2ot.SE2OT_EINVAL
+    assert lib.se2ot_apply(None, None, None, 1, 0, None) == se2ot.SE2OT_EINVAL
     assert lib.se2ot_barycenter(None, 2, None, None, None, None, None, None) == se2ot.SE2OT_EINVAL
     assert lib.se2ot_w2(None, None, None, None, None, None) == se2ot.SE2OT_EINVAL
     assert lib.se2ot_project(None, None, 1, 4, 4, 4, None) == se2ot.SE2OT_EINVAL

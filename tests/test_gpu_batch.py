@@ -73,7 +73,14 @@ def test_batch_rejects_what_it_does_not_support():
     _, _, st = se2ot.se2ot_interpolate_batched([d], [mu], [mu], [0.5], se2ot.solve_opts(10, 5, 1e-3),
                                                raise_on_error=False)
     assert st == se2ot.SE2OT_EINVAL
-    _, _, st = se2ot.se2ot_interpolate_batched([d], [mu.cpu()], [mu], [0.5], raise_on_error=False)
+    # host tensors: refused by the binding, and by the C entry point itself
+    with pytest.raises(ValueError):
+        se2ot.se2ot_interpolate_batched([d], [mu.cpu()], [mu], [0.5], raise_on_error=False)
+    import ctypes
+    host = mu.cpu()
+    arr = lambda *ts: (ctypes.c_void_p * 1)(*[t.data_ptr() for t in ts])
+    st = se2ot.lib().se2ot_interpolate_batched(1, (se2ot.se2ot_kernel_desc * 1)(d), arr(host), arr(mu),
+                                               (ctypes.c_double * 1)(0.5), None, arr(mu), None, None)
     assert st == se2ot.SE2OT_EINVAL
 
 
