@@ -51,8 +51,14 @@ constexpr float A_TOP = 55.f, PMAX = 110.f;
 constexpr float ELIG_MIN = -30.f, ACCEPT_MIN = -40.f;
 constexpr long SPIN_LIMIT = 1L << 24;
 
+constexpr int RAWROW = (TC_M + 2 * MAX_RADIUS + 2) * 8;   // bytes of one slice of a raw input row
+constexpr int RAWA = TC_NT * RAWROW;                        // bytes of a raw input row (all slices)
+
 __host__ __device__ constexpr int bplane(int D) { return D * NB * 256; }
-__host__ __device__ constexpr size_t tc_smem(int D) { return (size_t)NA * 2 * APLANE + 2 * (size_t)bplane(D); }
+__host__ __device__ constexpr size_t tc_smem(int D)
+{
+    return (size_t)NA * 2 * APLANE + 2 * (size_t)bplane(D) + 2 * (size_t)RAWA + 2 * (size_t)D * 1024;
+}
 
 __device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -160,13 +166,82 @@ __device__ __forceinline__ void epilogue_out(const ConvArgs &a, long flat, int b
     }
 }
 
-__global__ void __launch_bounds__(TC_THREADS, 2) tc_conv_kernel(const ConvArgs a, const TcArgs t)
+// Bulk copy (TMA, 1D) of `bytes` (a multiple of 16; both addresses 16-byte aligned) from global to
+// shared memory, completing on `bar`'s transaction count.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(su32(dst)),
+                 "l"(src), "r"(bytes), "r"(su32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void bar_expect(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}" ::"r"(su32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// Raw input row: the double-floats of input row qy, all slices, positions [x0 - r, x0 + 128 + r) of the
+// tile (wrapped on a periodic grid), copied to raw[slice][p - X0s] with X0s = (x0 - r) rounded down to
+// even, so that every copy starts on a 16-byte boundary (nx is even).  Cells outside a zero-boundary
+// grid are not copied (the converters never read them).  plan() lays out the copies and returns their
+// bytes; issue() starts them (one thread, after the barrier's single arrive.expect_tx of all the bytes
+// of the step, so that the phase completes only when every copy has landed).
+struct RowCopy {
+    int qy = 0, ns = 0, X0s = 0;
+    int dst[3], src[3], n[3];   // in positions
+    __device__ uint32_t plan(const ConvArgs &a, int qy_, int x0)
+    {
+        const int nx = a.nx, ny = a.ny, r = a.r;
+        const int lo = x0 - r, hi = x0 + TC_M + r;   // wanted positions [lo, hi)
+        X0s = lo & ~1;
+        qy = qy_;
+        ns = 0;
+        if (a.periodic) {
+            qy = wrapi(qy, ny);
+            if (lo < 0) { dst[ns] = X0s; src[ns] = nx + X0s; n[ns] = -X0s; ++ns; }
+            const int m0 = max(lo, 0) & ~1, m1 = min(hi, nx);
+            dst[ns] = m0; src[ns] = m0; n[ns] = ((m1 + 1) & ~1) - m0; ++ns;
+            if (hi > nx) { dst[ns] = nx; src[ns] = 0; n[ns] = (hi - nx + 1) & ~1; ++ns; }
+        } else if (qy >= 0 && qy < ny) {
+            const int m0 = max(lo, 0) & ~1, m1 = min(hi, nx);
+            if (m1 > m0) { dst[ns] = m0; src[ns] = m0; n[ns] = ((m1 + 1) & ~1) - m0; ++ns; }
+        }
+        uint32_t bytes = 0;
+        for (int k = 0; k < ns; ++k) bytes += (uint32_t)n[k] * 8u * (uint32_t)a.nt;
+        return bytes;
+    }
+    __device__ void issue(const ConvArgs &a, const float2 *in_b, unsigned char *raw, uint64_t *bar) const
+    {
+        const long plane = (long)a.nx * a.ny;
+        for (int i = 0; i < a.nt; ++i)
+            for (int k = 0; k < ns; ++k)
+                bulk_g2s(raw + (size_t)i * RAWROW + (size_t)(dst[k] - X0s) * 8,
+                         in_b + (long)i * plane + (long)qy * a.nx + src[k], (uint32_t)n[k] * 8u, bar);
+    }
+};
+
+// One raw input row alone (the statistics pass): a single arrive with its bytes, then the copies.
+__device__ void issue_row(const ConvArgs &a, const float2 *in_b, int qy, int x0, unsigned char *raw, uint64_t *bar)
+{
+    RowCopy rc;
+    const uint32_t bytes = rc.plan(a, qy, x0);
+    bar_expect(bar, bytes);
+    rc.issue(a, in_b, raw, bar);
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1) tc_conv_kernel(const ConvArgs a, const TcArgs t)
 {
     pdl_launch_dependents();
     pdl_wait();
     extern __shared__ __align__(1024) unsigned char smem[];
-    unsigned char *sA = smem, *sB = smem + NA * 2 * APLANE;
-    __shared__ __align__(8) uint64_t full_bar[NST], empty_bar[NST], done_bar;
+    const int nx = a.nx, ny = a.ny, nt = a.nt, r = a.r, D = 2 * r + 1;
+    const int BPL = bplane(D);
+    unsigned char *sA = smem;                                  // NA x 2 planes of APLANE: BF16 A rows
+    unsigned char *sB = sA + NA * 2 * APLANE;                  // 2 planes of BPL: BF16 B dy-blocks
+    unsigned char *rawA = sB + 2 * BPL;                        // 2 x RAWA: raw input rows
+    unsigned char *rawB = rawA + 2 * RAWA;                     // 2 x D x 1 KB: raw tap rows of one dy
+    __shared__ __align__(8) uint64_t full_bar[NST], empty_bar[NST], raw_bar[2], stat_bar[2], done_bar;
     __shared__ uint32_t s_tmem;
     __shared__ float s_alpha[TC_NT], s_rmax[TC_NT], s_c[TC_NT], s_tmx[TC_NT * TC_NT];
     __shared__ float s_part[TC_THREADS / 32][TC_NT];
@@ -174,12 +249,26 @@ __global__ void __launch_bounds__(TC_THREADS, 2) tc_conv_kernel(const ConvArgs a
     __shared__ float s_g[2];
     __shared__ int s_ok, s_abort;
 
-    const int nx = a.nx, ny = a.ny, nt = a.nt, r = a.r, D = 2 * r + 1;
     const int x0 = blockIdx.x * TC_M, y0 = blockIdx.y * TC_S, b = blockIdx.z;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const long plane = (long)nx * ny;
     const float2 *in_b = a.in + (long)b * nt * plane;
-    const int BPL = bplane(D);
+    const int HX = TC_M + 2 * r, HY = TC_S + 2 * r;
+    const int xoff = (x0 - r) - ((x0 - r) & ~1);   // raw index of position x0 - r (0 or 1)
+
+    if (tid == 0) {
+        for (int k = 0; k < NST; ++k) {
+            bar_init(&full_bar[k], 1);
+            bar_init(&empty_bar[k], 1);
+        }
+        for (int k = 0; k < 2; ++k) {
+            bar_init(&raw_bar[k], 1);
+            bar_init(&stat_bar[k], 1);
+        }
+        bar_init(&done_bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_abort = 0;
+    }
 
     // ---- 1. tilt plane: least squares of the previous outputs (the shifts) over the tile.
     //      sum_{p,o} (S(p,o) - c_o - gy Y_p - gx X_p)^2 with Y, X relative to the tile origin; the
@@ -206,7 +295,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) tc_conv_kernel(const ConvArgs a
         for (int off = 16; off; off >>= 1) q9[k] += __shfl_xor_sync(0xffffffffu, q9[k], off);
     if (lane == 0)
         for (int k = 0; k < 9; ++k) s_red[warp][k] = q9[k];
-    const int all_finite = __syncthreads_and(finite);
+    const int all_finite = __syncthreads_and(finite);   // also publishes the barrier initialisation
     if (tid == 0) {
         double s9[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
         for (int w = 0; w < TC_THREADS / 32; ++w)
@@ -228,38 +317,46 @@ __global__ void __launch_bounds__(TC_THREADS, 2) tc_conv_kernel(const ConvArgs a
         s_g[0] = (float)gy;
         s_g[1] = (float)gx;
         s_ok = all_finite && n > 0.0;
-        s_abort = 0;
+        if (s_ok) {   // the first two halo rows of the statistics pass
+            issue_row(a, in_b, y0 - r, x0, rawA, &stat_bar[0]);
+            if (HY > 1) issue_row(a, in_b, y0 - r + 1, x0, rawA + RAWA, &stat_bar[1]);
+        }
     }
     __syncthreads();
     const float gy = s_g[0], gx = s_g[1];
-    const int HX = TC_M + 2 * r, HY = TC_S + 2 * r;
 
-    // ---- 2. largest residual R_i = max (lf - P) of every input slice over the halo (hi parts).
-    //      A NaN or +inf input makes the tile ineligible.
+    // ---- 2. largest residual R_i = max (lf - P) of every input slice over the halo (hi parts), from
+    //      the raw rows staged by bulk copies (two buffers).  A NaN or +inf input makes the tile
+    //      ineligible.
     float rm[TC_NT];
 #pragma unroll
     for (int i = 0; i < TC_NT; ++i) rm[i] = -INFINITY;
     bool bad = false;
     if (s_ok) {
-        for (int e = tid; e < HY * HX; e += TC_THREADS) {
-            const int hy = e / HX, hx = e - hy * HX;
-            int qy = y0 - r + hy, qx = x0 - r + hx;
-            if (qx >= x0 + TC_M + r) continue;
-            if (a.periodic) {
-                qy = wrapi(qy, ny);
-                qx = wrapi(qx, nx);
-            } else if (qy < 0 || qy >= ny || qx < 0 || qx >= nx) {
-                continue;
-            }
-            const float P = gy * (float)(hy - r) + gx * (float)(hx - r);
+        for (int hy = 0; hy < HY; ++hy) {
+            const bool got = bar_wait(&stat_bar[hy & 1], (hy >> 1) & 1);
+            if (!got) bad = true;
+            int qy = y0 - r + hy;
+            const bool row_in = a.periodic || (qy >= 0 && qy < ny);
+            const float *raw = reinterpret_cast<const float *>(rawA + (hy & 1) * RAWA);
+            if (got && row_in) {
+                const float Py = gy * (float)(hy - r);
+                for (int hx = tid; hx < HX; hx += TC_THREADS) {
+                    const int qx = x0 - r + hx;
+                    if (!a.periodic && (qx < 0 || qx >= nx)) continue;
+                    const float P = Py + gx * (float)(hx - r);
 #pragma unroll
-            for (int i = 0; i < TC_NT; ++i) {
-                if (i >= nt) break;
-                const float h = in_b[(long)i * plane + (long)qy * nx + qx].x;
-                bad |= !(h <= 3.0e38f) && h == h && h > 0.f;   // +inf
-                bad |= h != h;                                   // NaN
-                rm[i] = fmaxf(rm[i], h - P);
+                    for (int i = 0; i < TC_NT; ++i) {
+                        if (i >= nt) break;
+                        const float h = raw[(i * RAWROW) / 4 + 2 * (hx + xoff)];
+                        bad |= !(h <= 3.0e38f) && h == h && h > 0.f;   // +inf
+                        bad |= h != h;                                   // NaN
+                        rm[i] = fmaxf(rm[i], h - P);
+                    }
+                }
             }
+            __syncthreads();   // every thread is done with this buffer
+            if (tid == 0 && hy + 2 < HY) issue_row(a, in_b, y0 - r + hy + 2, x0, rawA + (hy & 1) * RAWA, &stat_bar[hy & 1]);
         }
     }
 #pragma unroll
@@ -278,16 +375,29 @@ __global__ void __launch_bounds__(TC_THREADS, 2) tc_conv_kernel(const ConvArgs a
     if (tid == 0 && any_bad) s_ok = 0;
     __syncthreads();
 
-    // ---- 3. largest tilted tap of every orientation pair, Tmax(o, i) = max_d lk(o, i, d) - P(d)
-    //      (thread = pair; the combined tap table is [dy][dx][o][i]), then c_o.
+    // ---- 3. largest tilted tap of every orientation pair, Tmax(o, i) = lt + max_d ls(d) - P(d).  The
+    //      spatial taps are an exact quadratic form, ls = -(a dx^2 + b2 dx dy + c dy^2): for each dy the
+    //      maximum over integer dx of the concave parabola lies at floor or ceil of its vertex.
     if (s_ok) {
         const int o = tid / TC_NT, i = tid - o * TC_NT;
+        const float4 q = reinterpret_cast<const float4 *>(t.lk + (size_t)D * D * TC_NT * TC_NT)[tid];
         float tm = -INFINITY;
-        if (o < nt && i < nt)
-            for (int dyi = 0; dyi < D; ++dyi)
-                for (int dxi = 0; dxi < D; ++dxi)
-                    tm = fmaxf(tm, t.lk[((dyi * D + dxi) * TC_NT + o) * TC_NT + i] - (gy * (float)(dyi - r) +
-                                                                                      gx * (float)(dxi - r)));
+        if (o < nt && i < nt) {
+            for (int dy = -r; dy <= r; ++dy) {
+                const float beta = q.z * (float)dy + gx;   // h(dx) = -a dx^2 - beta dx
+                float best = -INFINITY;
+                if (q.y > 0.f) {
+                    const float v = -beta / (2.f * q.y);
+                    const float c0 = fminf(fmaxf(floorf(v), (float)-r), (float)r);
+                    const float c1 = fminf(fmaxf(c0 + 1.f, (float)-r), (float)r);
+                    best = fmaxf(-q.y * c0 * c0 - beta * c0, -q.y * c1 * c1 - beta * c1);
+                } else {
+                    best = fabsf(beta) * (float)r;   // a = 0 (radius 0): the row is linear in dx
+                }
+                tm = fmaxf(tm, best - q.w * (float)(dy * dy) - gy * (float)dy);
+            }
+            tm += q.x;
+        }
         s_tmx[tid] = tm;
     }
     __syncthreads();
@@ -328,7 +438,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) tc_conv_kernel(const ConvArgs a
             }
             atomicAdd(t.tiles + 1, 1ull);
         }
-        return;
+        return;   // no bulk copy is in flight: the statistics pass waited for every row
     }
 
     // ---- 5. the GEMM.  TMEM: 64 columns, output row s at columns [16 s, 16 s + 16).
@@ -338,19 +448,26 @@ __global__ void __launch_bounds__(TC_THREADS, 2) tc_conv_kernel(const ConvArgs a
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    if (tid == 0) {
-        for (int k = 0; k < NST; ++k) {
-            bar_init(&full_bar[k], 1);
-            bar_init(&empty_bar[k], 1);
-        }
-        bar_init(&done_bar, 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    const int NQ = TC_S + 2 * r;   // input rows y0 - r .. y0 + S - 1 + r
+    // raw data of step qi: input row y0 - r + qi and (qi <= 2r) the tap rows of dy = r - qi
+    auto issue_step = [&](int qi) {
+        RowCopy rc;
+        const uint32_t tap_bytes = qi <= 2 * r ? (uint32_t)D * TC_NT * TC_NT * 4u : 0u;
+        bar_expect(&raw_bar[qi & 1], rc.plan(a, y0 - r + qi, x0) + tap_bytes);
+        rc.issue(a, in_b, rawA + (qi & 1) * RAWA, &raw_bar[qi & 1]);
+        if (tap_bytes)
+            bulk_g2s(rawB + (qi & 1) * (size_t)D * 1024, t.lk + (size_t)(2 * r - qi) * D * TC_NT * TC_NT, tap_bytes,
+                     &raw_bar[qi & 1]);
+    };
+    if (tid == 0) issue_step(0);
+    if (warp < 4) {   // zero the accumulators (every MMA accumulates)
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = s_tmem;
-    if (warp < 4) {   // zero the accumulators (every MMA accumulates)
+    if (warp < 4) {
         const uint32_t ta = tmem + ((uint32_t)(32 * warp) << 16);
 #pragma unroll
         for (int c = 0; c < TC_S * TC_NT; c += 16)
@@ -363,19 +480,26 @@ __global__ void __launch_bounds__(TC_THREADS, 2) tc_conv_kernel(const ConvArgs a
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
-    const int NQ = TC_S + 2 * r;   // input rows y0 - r .. y0 + S - 1 + r
+    int issued = 0;   // steps whose raw copies tid 0 issued (tid 0 only)
     if (warp < 7) {
-        // producers: step qi stages input row q = y0 - r + qi in A slot qi % NA and, for qi <= 2r,
-        // the taps of dy = r - qi in B slot (dy + r) % NB.  Slots of step qi were last read by the MMAs
-        // of step qi - 2 (B: dy + NB used up to step qi - NB + S - 1 = qi - 2; A: step qi - 3).
+        // producers: step qi converts input row q = y0 - r + qi into A slot qi % NA and, for qi <= 2r,
+        // the taps of dy = r - qi into B slot (dy + r) % NB.  Slots of step qi were last read by the
+        // MMAs of step qi - 2 (B: dy + NB used up to step qi - NB + S - 1 = qi - 2; A: step qi - 3).
+        // The raw data of step qi + 1 is copied (bulk, one thread) while step qi is converted.
+        if (tid == 0) issued = 1;
         for (int qi = 0; qi < NQ; ++qi) {
-            // every producer waits with the same bound; the decision to stop is one vote of all
+            bool gave_up = qi >= 2 && !bar_wait(&empty_bar[(qi - 2) % NST], ((qi - 2) / NST) & 1);
+            if (tid == 0 && qi + 1 < NQ && !gave_up) {
+                issue_step(qi + 1);
+                issued = qi + 2;
+            }
+            gave_up |= !bar_wait(&raw_bar[qi & 1], (qi >> 1) & 1);
+            // every producer waits with the same bounds; the decision to stop is one vote of all
             // producers, so none is left behind in the named barrier below
-            const uint32_t gave_up = qi >= 2 && !bar_wait(&empty_bar[(qi - 2) % NST], ((qi - 2) / NST) & 1);
             uint32_t any;
             asm volatile("{\n.reg .pred p, q;\nsetp.ne.u32 p, %1, 0;\nbar.red.or.pred q, 1, %2, p;\nselp.u32 %0, 1, 0, q;\n}"
                          : "=r"(any)
-                         : "r"(gave_up), "n"(TC_PRODUCERS)
+                         : "r"((uint32_t)gave_up), "n"(TC_PRODUCERS)
                          : "memory");
             if (any) {
                 if (tid == 0) {
@@ -385,44 +509,42 @@ __global__ void __launch_bounds__(TC_THREADS, 2) tc_conv_kernel(const ConvArgs a
                 break;
             }
             unsigned char *ar = sA + (qi % NA) * 2 * APLANE;
-            int qy = y0 - r + qi;
-            bool row_in = true;
-            if (a.periodic) qy = wrapi(qy, ny);
-            else row_in = qy >= 0 && qy < ny;
+            const float *raw = reinterpret_cast<const float *>(rawA + (qi & 1) * RAWA);
+            const int qy = y0 - r + qi;
+            const bool row_in = a.periodic || (qy >= 0 && qy < ny);
             const float Pq = gy * (float)(qi - r);
             for (int e = tid; e < 2 * HX; e += TC_PRODUCERS) {
                 const int ih = e / HX, hx = e - ih * HX;
-                int qx = x0 - r + hx;
-                bool in = row_in && qx < x0 + TC_M + r;
-                if (a.periodic) qx = wrapi(qx, nx);
-                else in = in && qx >= 0 && qx < nx;
+                const int qx = x0 - r + hx;
+                const bool in = row_in && (a.periodic || (qx >= 0 && qx < nx));
+                const float P = Pq + gx * (float)(hx - r);
                 float v[8];
 #pragma unroll
                 for (int k = 0; k < 8; ++k) {
                     const int i = 8 * ih + k;
                     v[k] = 0.f;
                     if (in && i < nt) {
-                        const float2 h = in_b[(long)i * plane + (long)qy * nx + qx];
-                        const float ex = ((h.x - s_alpha[i]) - (Pq + gx * (float)(hx - r))) + h.y;
-                        v[k] = ex2f(ex);   // -inf input: 0
+                        const float2 h = reinterpret_cast<const float2 *>(raw + (i * RAWROW) / 4)[hx + xoff];
+                        v[k] = ex2f(((h.x - s_alpha[i]) - P) + h.y);   // -inf input: 0
                     }
                 }
-                uint4 w = make_uint4(pack2(v[0], v[1]), pack2(v[2], v[3]), pack2(v[4], v[5]), pack2(v[6], v[7]));
+                const uint4 w = make_uint4(pack2(v[0], v[1]), pack2(v[2], v[3]), pack2(v[4], v[5]), pack2(v[6], v[7]));
                 *reinterpret_cast<uint4 *>(ar + ih * APLANE + hx * 16) = w;
             }
             if (qi <= 2 * r) {
                 const int dyi = 2 * r - qi, sl = (2 * r - qi) % NB;   // dy = r - qi, slot (dy + r) % NB
                 const float Py = gy * (float)(dyi - r);
+                const float *rb = reinterpret_cast<const float *>(rawB + (qi & 1) * (size_t)D * 1024);
                 for (int e = tid; e < D * TC_NT * 2; e += TC_PRODUCERS) {
                     const int ih = e & 1, o = (e >> 1) & (TC_NT - 1), dxi = e >> 5;
-                    const float4 *src = reinterpret_cast<const float4 *>(t.lk + ((dyi * D + dxi) * TC_NT + o) * TC_NT + 8 * ih);
-                    const float4 l0 = __ldg(src), l1 = __ldg(src + 1);
+                    const float4 *src = reinterpret_cast<const float4 *>(rb + (dxi * TC_NT + o) * TC_NT + 8 * ih);
+                    const float4 l0 = src[0], l1 = src[1];
                     const float lv[8] = {l0.x, l0.y, l0.z, l0.w, l1.x, l1.y, l1.z, l1.w};
                     const float base = -(Py + gx * (float)(dxi - r)) - s_c[o];
                     float v[8];
 #pragma unroll
                     for (int k = 0; k < 8; ++k) v[k] = ex2f(lv[k] + base + s_alpha[8 * ih + k]);
-                    uint4 w = make_uint4(pack2(v[0], v[1]), pack2(v[2], v[3]), pack2(v[4], v[5]), pack2(v[6], v[7]));
+                    const uint4 w = make_uint4(pack2(v[0], v[1]), pack2(v[2], v[3]), pack2(v[4], v[5]), pack2(v[6], v[7]));
                     *reinterpret_cast<uint4 *>(sB + ih * BPL + (dxi * NB + sl) * 256 + o * 16) = w;
                 }
             }
@@ -430,6 +552,9 @@ __global__ void __launch_bounds__(TC_THREADS, 2) tc_conv_kernel(const ConvArgs a
             asm volatile("bar.sync 1, %0;" ::"n"(TC_PRODUCERS) : "memory");
             if (tid == 0) bar_arrive(&full_bar[qi % NST]);
         }
+        // after an abort, the copies tid 0 issued for a step not yet consumed may still be in flight
+        if (tid == 0 && s_abort)
+            for (int q = 0; q < issued; ++q) bar_wait(&raw_bar[q & 1], (q >> 1) & 1);
     } else if (lane == 0) {
         // the MMA issuer: step qi covers output rows s in [max(0, qi - 2r), min(S - 1, qi)] with
         // dy = s - qi + r, B slots (s - qi + 2r) % NB ascending in s (split where the ring wraps)
@@ -517,11 +642,35 @@ __global__ void __launch_bounds__(TC_THREADS, 2) tc_conv_kernel(const ConvArgs a
 }
 
 // Combined taps for the tensor-core kernel: lk[dy][dx][o][i] = ltheta(o, i) + ls(o, i, dy, dx) in FP32,
-// orientation slots beyond nt set to -inf.
+// orientation slots beyond nt set to -inf; then per pair (o, i) the float4 (lt, a, b2, c) of the
+// spatial taps' quadratic form ls = -(a dx^2 + b2 dx dy + c dy^2), read off the table's offsets
+// (1, 0), (0, 1) and (1, 1) (the form is exact: the half-angle coordinates are linear in the offset).
 __global__ void tc_taps_kernel(const float2 *ltheta, const float *ls, const float *ls_lo, int nt, int D, float *lk)
 {
     const long total = (long)D * D * TC_NT * TC_NT;
-    for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+    for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total + TC_NT * TC_NT;
+         idx += (long)gridDim.x * blockDim.x) {
+        if (idx >= total) {
+            const int p16 = (int)(idx - total), o = p16 / TC_NT, i = p16 - o * TC_NT;
+            float4 q = make_float4(-INFINITY, 0.f, 0.f, 0.f);
+            if (o < nt && i < nt) {
+                const long p = (long)o * nt + i;
+                const int r = D / 2;
+                auto tap = [&](int dx, int dy) {
+                    const long k = (p * D + dy + r) * D + dx + r;
+                    return (double)ls[k] + (double)ls_lo[k];
+                };
+                q.x = (float)((double)ltheta[p].x + (double)ltheta[p].y);
+                if (r > 0) {
+                    const double a = -tap(1, 0), c = -tap(0, 1), b2 = -(tap(1, 1) - tap(1, 0) - tap(0, 1));
+                    q.y = (float)a;
+                    q.z = (float)b2;
+                    q.w = (float)c;
+                }
+            }
+            reinterpret_cast<float4 *>(lk + total)[idx - total] = q;
+            continue;
+        }
         const int i = (int)(idx % TC_NT), o = (int)((idx / TC_NT) % TC_NT);
         const long dd = idx / (TC_NT * TC_NT);
         const int dxi = (int)(dd % D), dyi = (int)(dd / D);
@@ -543,18 +692,25 @@ __global__ void fill_kernel(float *p, long n, float v)
 
 }  // namespace
 
-bool tc_supported(const se2ot_kernel_desc &d) { return d.ntheta <= TC_NT && d.radius <= MAX_RADIUS && d.nx >= TC_M / 2; }
+// Grids of the tensor-core path: ntheta <= 16 (the K and N slots of one tap), nx even (16-byte bulk
+// copies of double-float rows), at least half a tile wide, and on a periodic grid wide enough that a
+// halo row wraps at most once on each side.
+bool tc_supported(const se2ot_kernel_desc &d)
+{
+    if (d.ntheta > TC_NT || d.radius > MAX_RADIUS || d.nx < TC_M / 2 || (d.nx & 1)) return false;
+    return d.boundary != SE2OT_BOUNDARY_PERIODIC || d.nx >= TC_M + 2 * d.radius;
+}
 
 size_t tc_taps_floats(const se2ot_kernel_desc &d)
 {
     const long D = 2 * d.radius + 1;
-    return (size_t)D * D * TC_NT * TC_NT;
+    return (size_t)D * D * TC_NT * TC_NT + 4 * TC_NT * TC_NT;
 }
 
 cudaError_t build_tc_taps(const se2ot_kernel_desc &d, const Taps &taps, float *lk, cudaStream_t s)
 {
     const int D = 2 * d.radius + 1;
-    const long total = (long)tc_taps_floats(d);
+    const long total = (long)D * D * TC_NT * TC_NT + TC_NT * TC_NT;
     tc_taps_kernel<<<(int)std::min(4096L, (total + 255) / 256), 256, 0, s>>>(taps.ltheta, taps.ls, taps.ls_lo, d.ntheta,
                                                                              D, lk);
     return cudaGetLastError();
