@@ -28,8 +28,12 @@
 // output row of the tile that q reaches, with the B blocks of consecutive dy stored consecutively.
 // Producer warps fill a ring of input rows (A) and a ring of dy blocks of taps (B) while one warp
 // issues the MMAs; tcgen05.commit on an mbarrier frees the slots.  Every wait is bounded.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
 
 #include "dfloat.cuh"
 #include "internal.h"
@@ -51,13 +55,22 @@ constexpr float A_TOP = 55.f, PMAX = 110.f;
 constexpr float ELIG_MIN = -30.f, ACCEPT_MIN = -40.f;
 constexpr long SPIN_LIMIT = 1L << 24;
 
-constexpr int RAWROW = (TC_M + 2 * MAX_RADIUS + 2) * 8;   // bytes of one slice of a raw input row
+constexpr int BOXW = TC_M + 2 * MAX_RADIUS + 8;          // positions of a raw input row (TMA box width)
+constexpr int RAWROW = BOXW * 8;                         // bytes of one slice of a raw input row
 constexpr int RAWA = TC_NT * RAWROW;                        // bytes of a raw input row (all slices)
+constexpr int NSB = 7;      // raw rows in flight in the halo statistics pass (over the whole dynamic smem)
+constexpr size_t SMEM_MAX = 227 * 1024 - 4096;   // dynamic shared memory of a CTA (static part reserved)
 
 __host__ __device__ constexpr int bplane(int D) { return D * NB * 256; }
+// Raw-data depth of the pipeline: three steps in flight where they fit, else two.
+__host__ __device__ constexpr size_t tc_smem_depth(int D, int nraw)
+{
+    return (size_t)NA * 2 * APLANE + 2 * (size_t)bplane(D) + (size_t)nraw * (RAWA + (size_t)D * 1024);
+}
+__host__ __device__ constexpr int tc_nraw(int D) { return tc_smem_depth(D, 3) <= SMEM_MAX ? 3 : 2; }
 __host__ __device__ constexpr size_t tc_smem(int D)
 {
-    return (size_t)NA * 2 * APLANE + 2 * (size_t)bplane(D) + 2 * (size_t)RAWA + 2 * (size_t)D * 1024;
+    return tc_smem_depth(D, tc_nraw(D)) > (size_t)NSB * RAWA ? tc_smem_depth(D, tc_nraw(D)) : (size_t)NSB * RAWA;
 }
 
 __device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -181,56 +194,32 @@ __device__ __forceinline__ void bar_expect(uint64_t *bar, uint32_t bytes)
                  : "memory");
 }
 
-// Raw input row: the double-floats of input row qy, all slices, positions [x0 - r, x0 + 128 + r) of the
-// tile (wrapped on a periodic grid), copied to raw[slice][p - X0s] with X0s = (x0 - r) rounded down to
-// even, so that every copy starts on a 16-byte boundary (nx is even).  Cells outside a zero-boundary
-// grid are not copied (the converters never read them).  plan() lays out the copies and returns their
-// bytes; issue() starts them (one thread, after the barrier's single arrive.expect_tx of all the bytes
-// of the step, so that the phase completes only when every copy has landed).
-struct RowCopy {
-    int qy = 0, ns = 0, X0s = 0;
-    int dst[3], src[3], n[3];   // in positions
-    __device__ uint32_t plan(const ConvArgs &a, int qy_, int x0)
-    {
-        const int nx = a.nx, ny = a.ny, r = a.r;
-        const int lo = x0 - r, hi = x0 + TC_M + r;   // wanted positions [lo, hi)
-        X0s = lo & ~1;
-        qy = qy_;
-        ns = 0;
-        if (a.periodic) {
-            qy = wrapi(qy, ny);
-            if (lo < 0) { dst[ns] = X0s; src[ns] = nx + X0s; n[ns] = -X0s; ++ns; }
-            const int m0 = max(lo, 0) & ~1, m1 = min(hi, nx);
-            dst[ns] = m0; src[ns] = m0; n[ns] = ((m1 + 1) & ~1) - m0; ++ns;
-            if (hi > nx) { dst[ns] = nx; src[ns] = 0; n[ns] = (hi - nx + 1) & ~1; ++ns; }
-        } else if (qy >= 0 && qy < ny) {
-            const int m0 = max(lo, 0) & ~1, m1 = min(hi, nx);
-            if (m1 > m0) { dst[ns] = m0; src[ns] = m0; n[ns] = ((m1 + 1) & ~1) - m0; ++ns; }
-        }
-        uint32_t bytes = 0;
-        for (int k = 0; k < ns; ++k) bytes += (uint32_t)n[k] * 8u * (uint32_t)a.nt;
-        return bytes;
-    }
-    __device__ void issue(const ConvArgs &a, const float2 *in_b, unsigned char *raw, uint64_t *bar) const
-    {
-        const long plane = (long)a.nx * a.ny;
-        for (int i = 0; i < a.nt; ++i)
-            for (int k = 0; k < ns; ++k)
-                bulk_g2s(raw + (size_t)i * RAWROW + (size_t)(dst[k] - X0s) * 8,
-                         in_b + (long)i * plane + (long)qy * a.nx + src[k], (uint32_t)n[k] * 8u, bar);
-    }
-};
+// Raw input row: the double-floats of input row qy, slices b nt .. b nt + nt - 1, positions
+// [X0s, X0s + BOXW) with X0s = (x0 - r) rounded down to even (a 16-byte boundary), as one TMA load of a
+// box of the 3D tensor map (x, y, b nt + i) to raw[slice][p - X0s].  Cells outside the grid arrive as
+// zeros, which the converters never read (they test the geometry).  One thread issues, after the
+// single arrive.expect_tx of all the bytes of its barrier's phase.
+__device__ __forceinline__ uint32_t row_bytes(int nt) { return (uint32_t)BOXW * 8u * (uint32_t)nt; }
 
-// One raw input row alone (the statistics pass): a single arrive with its bytes, then the copies.
-__device__ void issue_row(const ConvArgs &a, const float2 *in_b, int qy, int x0, unsigned char *raw, uint64_t *bar)
+__device__ __forceinline__ void issue_row_tma(const CUtensorMap *map, int x0, int r, int qy, int zslice,
+                                              unsigned char *raw, uint64_t *bar)
 {
-    RowCopy rc;
-    const uint32_t bytes = rc.plan(a, qy, x0);
-    bar_expect(bar, bytes);
-    rc.issue(a, in_b, raw, bar);
+    const int X0s = (x0 - r) & ~1;
+    asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+                 ::"r"(su32(raw)), "l"(reinterpret_cast<uint64_t>(map)), "r"(X0s), "r"(qy), "r"(zslice), "r"(su32(bar))
+                 : "memory");
 }
 
-__global__ void __launch_bounds__(TC_THREADS, 1) tc_conv_kernel(const ConvArgs a, const TcArgs t)
+// One raw input row alone (the statistics pass): a single arrive with its bytes, then the load.
+__device__ void issue_row(const CUtensorMap *map, int nt, int x0, int r, int qy, int zslice, unsigned char *raw,
+                          uint64_t *bar)
+{
+    bar_expect(bar, row_bytes(nt));
+    issue_row_tma(map, x0, r, qy, zslice, raw, bar);
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1) tc_conv_kernel(const ConvArgs a, const TcArgs t,
+                                                                 const __grid_constant__ CUtensorMap in_map)
 {
     pdl_launch_dependents();
     pdl_wait();
@@ -239,13 +228,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_conv_kernel(const ConvArgs a
     const int BPL = bplane(D);
     unsigned char *sA = smem;                                  // NA x 2 planes of APLANE: BF16 A rows
     unsigned char *sB = sA + NA * 2 * APLANE;                  // 2 planes of BPL: BF16 B dy-blocks
-    unsigned char *rawA = sB + 2 * BPL;                        // 2 x RAWA: raw input rows
-    unsigned char *rawB = rawA + 2 * RAWA;                     // 2 x D x 1 KB: raw tap rows of one dy
-    __shared__ __align__(8) uint64_t full_bar[NST], empty_bar[NST], raw_bar[2], stat_bar[2], done_bar;
+    const int NRAW = tc_nraw(D);                               // raw steps in flight (2 or 3)
+    unsigned char *rawA = sB + 2 * BPL;                        // NRAW x RAWA: raw input rows
+    unsigned char *rawB = rawA + NRAW * RAWA;                  // NRAW x D x 1 KB: raw tap rows of one dy
+    __shared__ __align__(8) uint64_t full_bar[NST], empty_bar[NST], raw_bar[3], stat_bar[NSB], done_bar;
     __shared__ uint32_t s_tmem;
     __shared__ float s_alpha[TC_NT], s_rmax[TC_NT], s_c[TC_NT], s_tmx[TC_NT * TC_NT];
     __shared__ float s_part[TC_THREADS / 32][TC_NT];
-    __shared__ double s_red[TC_THREADS / 32][9];
+    __shared__ float s_red[TC_THREADS / 32][9];
     __shared__ float s_g[2];
     __shared__ int s_ok, s_abort;
 
@@ -261,10 +251,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_conv_kernel(const ConvArgs a
             bar_init(&full_bar[k], 1);
             bar_init(&empty_bar[k], 1);
         }
-        for (int k = 0; k < 2; ++k) {
-            bar_init(&raw_bar[k], 1);
-            bar_init(&stat_bar[k], 1);
-        }
+        for (int k = 0; k < 3; ++k) bar_init(&raw_bar[k], 1);
+        for (int k = 0; k < NSB; ++k) bar_init(&stat_bar[k], 1);
         bar_init(&done_bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_abort = 0;
@@ -273,20 +261,26 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_conv_kernel(const ConvArgs a
     // ---- 1. tilt plane: least squares of the previous outputs (the shifts) over the tile.
     //      sum_{p,o} (S(p,o) - c_o - gy Y_p - gx X_p)^2 with Y, X relative to the tile origin; the
     //      per-orientation intercepts drop out of the slopes because every valid position has all nt
-    //      orientations.  FP64 sums (positions up to 512, shifts up to ~1e4).
-    double q9[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};   // n, Y, X, YY, XX, XY, T, YT, XT (T = sum_o S)
+    //      orientations.  FP32 sums of values taken relative to one shift of the tile (the plane only
+    //      chooses the rescaling; A, B and the epilogue use the same P exactly, whatever it is).
+    const float sref = a.hint[((long)(b * nt) * ny + y0) * nx + x0];
+    const float ref = isfinite(sref) ? sref : 0.f;
+    float q9[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};   // n, Y, X, YY, XX, XY, T, YT, XT (T = sum_o (S - ref))
     bool finite = true;
     for (int e = tid; e < TC_S * TC_M; e += TC_THREADS) {
         const int s = e / TC_M, m = e - s * TC_M, y = y0 + s, x = x0 + m;
         if (y >= ny || x >= nx) continue;
-        double T = 0.0;
-        for (int o = 0; o < nt; ++o) {
-            const float h = a.hint[((long)(b * nt + o) * ny + y) * nx + x];
-            finite &= isfinite(h);
-            T += (double)h;
+        float h[TC_NT];
+#pragma unroll
+        for (int o = 0; o < TC_NT; ++o) h[o] = o < nt ? a.hint[((long)(b * nt + o) * ny + y) * nx + x] : ref;
+        float T = 0.f;
+#pragma unroll
+        for (int o = 0; o < TC_NT; ++o) {
+            finite &= isfinite(h[o]);
+            T += h[o] - ref;
         }
-        const double Y = s, X = m;
-        q9[0] += 1.0; q9[1] += Y; q9[2] += X; q9[3] += Y * Y; q9[4] += X * X; q9[5] += X * Y;
+        const float Y = (float)s - 1.5f, X = (float)m - 63.5f;   // centred on a full tile
+        q9[0] += 1.f; q9[1] += Y; q9[2] += X; q9[3] += Y * Y; q9[4] += X * X; q9[5] += X * Y;
         q9[6] += T; q9[7] += Y * T; q9[8] += X * T;
     }
 #pragma unroll
@@ -297,30 +291,29 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_conv_kernel(const ConvArgs a
         for (int k = 0; k < 9; ++k) s_red[warp][k] = q9[k];
     const int all_finite = __syncthreads_and(finite);   // also publishes the barrier initialisation
     if (tid == 0) {
-        double s9[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        float s9[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
         for (int w = 0; w < TC_THREADS / 32; ++w)
             for (int k = 0; k < 9; ++k) s9[k] += s_red[w][k];
-        const double n = s9[0];
-        const double syy = (s9[3] - s9[1] * s9[1] / n) * nt, sxx = (s9[4] - s9[2] * s9[2] / n) * nt;
-        const double sxy = (s9[5] - s9[1] * s9[2] / n) * nt;
-        const double syt = s9[7] - s9[1] * s9[6] / n, sxt = s9[8] - s9[2] * s9[6] / n;
-        double gy = 0.0, gx = 0.0;
-        const double det = syy * sxx - sxy * sxy;
-        if (det > 1e-9 * (syy * sxx + 1.0)) {
+        const float n = s9[0];
+        const float syy = (s9[3] - s9[1] * s9[1] / n) * nt, sxx = (s9[4] - s9[2] * s9[2] / n) * nt;
+        const float sxy = (s9[5] - s9[1] * s9[2] / n) * nt;
+        const float syt = s9[7] - s9[1] * s9[6] / n, sxt = s9[8] - s9[2] * s9[6] / n;
+        float gy = 0.f, gx = 0.f;
+        const float det = syy * sxx - sxy * sxy;
+        if (det > 1e-6f * (syy * sxx + 1.f)) {
             gy = (syt * sxx - sxt * sxy) / det;
             gx = (sxt * syy - syt * sxy) / det;
-        } else if (sxx > 0.0) {
+        } else if (sxx > 0.f) {
             gx = sxt / sxx;
-        } else if (syy > 0.0) {
+        } else if (syy > 0.f) {
             gy = syt / syy;
         }
-        s_g[0] = (float)gy;
-        s_g[1] = (float)gx;
-        s_ok = all_finite && n > 0.0;
-        if (s_ok) {   // the first two halo rows of the statistics pass
-            issue_row(a, in_b, y0 - r, x0, rawA, &stat_bar[0]);
-            if (HY > 1) issue_row(a, in_b, y0 - r + 1, x0, rawA + RAWA, &stat_bar[1]);
-        }
+        s_g[0] = isfinite(gy) ? gy : 0.f;
+        s_g[1] = isfinite(gx) ? gx : 0.f;
+        s_ok = all_finite && n > 0.f;
+        if (s_ok)   // the first halo rows of the statistics pass
+            for (int k = 0; k < NSB && k < HY; ++k)
+                issue_row(&in_map, nt, x0, r, y0 - r + k, b * nt, smem + k * RAWA, &stat_bar[k]);
     }
     __syncthreads();
     const float gy = s_g[0], gx = s_g[1];
@@ -334,11 +327,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_conv_kernel(const ConvArgs a
     bool bad = false;
     if (s_ok) {
         for (int hy = 0; hy < HY; ++hy) {
-            const bool got = bar_wait(&stat_bar[hy & 1], (hy >> 1) & 1);
+            const int sb = hy % NSB;
+            const bool got = bar_wait(&stat_bar[sb], (hy / NSB) & 1);
             if (!got) bad = true;
-            int qy = y0 - r + hy;
+            const int qy = y0 - r + hy;
             const bool row_in = a.periodic || (qy >= 0 && qy < ny);
-            const float *raw = reinterpret_cast<const float *>(rawA + (hy & 1) * RAWA);
+            const float *raw = reinterpret_cast<const float *>(smem + sb * RAWA);
             if (got && row_in) {
                 const float Py = gy * (float)(hy - r);
                 for (int hx = tid; hx < HX; hx += TC_THREADS) {
@@ -356,7 +350,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_conv_kernel(const ConvArgs a
                 }
             }
             __syncthreads();   // every thread is done with this buffer
-            if (tid == 0 && hy + 2 < HY) issue_row(a, in_b, y0 - r + hy + 2, x0, rawA + (hy & 1) * RAWA, &stat_bar[hy & 1]);
+            if (tid == 0 && hy + NSB < HY)
+                issue_row(&in_map, nt, x0, r, y0 - r + hy + NSB, b * nt, smem + sb * RAWA, &stat_bar[sb]);
         }
     }
 #pragma unroll
@@ -417,10 +412,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_conv_kernel(const ConvArgs a
             const int s = e / TC_M, m = e - s * TC_M, y = y0 + s, x = x0 + m;
             if (y >= ny || x >= nx) continue;
             const float P = gy * (float)s + gx * (float)m;
-            for (int o = 0; o < nt; ++o) {
-                const float h = a.hint[((long)(b * nt + o) * ny + y) * nx + x];
-                elig &= h - P - s_c[o] >= ELIG_MIN;
-            }
+            float h[TC_NT];
+#pragma unroll
+            for (int o = 0; o < TC_NT; ++o) h[o] = o < nt ? a.hint[((long)(b * nt + o) * ny + y) * nx + x] : 0.f;
+#pragma unroll
+            for (int o = 0; o < TC_NT; ++o)
+                if (o < nt) elig &= h[o] - P - s_c[o] >= ELIG_MIN;
         }
     }
     elig = __syncthreads_and(elig);
@@ -451,15 +448,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_conv_kernel(const ConvArgs a
     const int NQ = TC_S + 2 * r;   // input rows y0 - r .. y0 + S - 1 + r
     // raw data of step qi: input row y0 - r + qi and (qi <= 2r) the tap rows of dy = r - qi
     auto issue_step = [&](int qi) {
-        RowCopy rc;
+        const int k = qi % NRAW;
         const uint32_t tap_bytes = qi <= 2 * r ? (uint32_t)D * TC_NT * TC_NT * 4u : 0u;
-        bar_expect(&raw_bar[qi & 1], rc.plan(a, y0 - r + qi, x0) + tap_bytes);
-        rc.issue(a, in_b, rawA + (qi & 1) * RAWA, &raw_bar[qi & 1]);
+        bar_expect(&raw_bar[k], row_bytes(nt) + tap_bytes);
+        issue_row_tma(&in_map, x0, r, y0 - r + qi, b * nt, rawA + k * RAWA, &raw_bar[k]);
         if (tap_bytes)
-            bulk_g2s(rawB + (qi & 1) * (size_t)D * 1024, t.lk + (size_t)(2 * r - qi) * D * TC_NT * TC_NT, tap_bytes,
-                     &raw_bar[qi & 1]);
+            bulk_g2s(rawB + k * (size_t)D * 1024, t.lk + (size_t)(2 * r - qi) * D * TC_NT * TC_NT, tap_bytes, &raw_bar[k]);
     };
-    if (tid == 0) issue_step(0);
+    if (tid == 0)
+        for (int q = 0; q < NRAW - 1 && q < NQ; ++q) issue_step(q);
     if (warp < 4) {   // zero the accumulators (every MMA accumulates)
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     }
@@ -486,14 +483,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_conv_kernel(const ConvArgs a
         // the taps of dy = r - qi into B slot (dy + r) % NB.  Slots of step qi were last read by the
         // MMAs of step qi - 2 (B: dy + NB used up to step qi - NB + S - 1 = qi - 2; A: step qi - 3).
         // The raw data of step qi + 1 is copied (bulk, one thread) while step qi is converted.
-        if (tid == 0) issued = 1;
+        if (tid == 0) issued = min(NRAW - 1, NQ);
         for (int qi = 0; qi < NQ; ++qi) {
             bool gave_up = qi >= 2 && !bar_wait(&empty_bar[(qi - 2) % NST], ((qi - 2) / NST) & 1);
-            if (tid == 0 && qi + 1 < NQ && !gave_up) {
-                issue_step(qi + 1);
-                issued = qi + 2;
+            // the raw buffer of step qi + NRAW - 1 was last read by the converters of step qi - 1
+            if (tid == 0 && qi + NRAW - 1 < NQ && !gave_up) {
+                issue_step(qi + NRAW - 1);
+                issued = qi + NRAW;
             }
-            gave_up |= !bar_wait(&raw_bar[qi & 1], (qi >> 1) & 1);
+            gave_up |= !bar_wait(&raw_bar[qi % NRAW], (qi / NRAW) & 1);
             // every producer waits with the same bounds; the decision to stop is one vote of all
             // producers, so none is left behind in the named barrier below
             uint32_t any;
@@ -509,11 +507,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_conv_kernel(const ConvArgs a
                 break;
             }
             unsigned char *ar = sA + (qi % NA) * 2 * APLANE;
-            const float *raw = reinterpret_cast<const float *>(rawA + (qi & 1) * RAWA);
+            const float *raw = reinterpret_cast<const float *>(rawA + (qi % NRAW) * RAWA);
             const int qy = y0 - r + qi;
             const bool row_in = a.periodic || (qy >= 0 && qy < ny);
             const float Pq = gy * (float)(qi - r);
-            for (int e = tid; e < 2 * HX; e += TC_PRODUCERS) {
+#pragma unroll
+            for (int it = 0; it < (2 * (TC_M + 2 * MAX_RADIUS) + TC_PRODUCERS - 1) / TC_PRODUCERS; ++it) {
+                const int e = tid + it * TC_PRODUCERS;
+                if (e >= 2 * HX) break;
                 const int ih = e / HX, hx = e - ih * HX;
                 const int qx = x0 - r + hx;
                 const bool in = row_in && (a.periodic || (qx >= 0 && qx < nx));
@@ -534,8 +535,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_conv_kernel(const ConvArgs a
             if (qi <= 2 * r) {
                 const int dyi = 2 * r - qi, sl = (2 * r - qi) % NB;   // dy = r - qi, slot (dy + r) % NB
                 const float Py = gy * (float)(dyi - r);
-                const float *rb = reinterpret_cast<const float *>(rawB + (qi & 1) * (size_t)D * 1024);
-                for (int e = tid; e < D * TC_NT * 2; e += TC_PRODUCERS) {
+                const float *rb = reinterpret_cast<const float *>(rawB + (qi % NRAW) * (size_t)D * 1024);
+#pragma unroll
+                for (int it = 0; it < ((2 * MAX_RADIUS + 1) * TC_NT * 2 + TC_PRODUCERS - 1) / TC_PRODUCERS; ++it) {
+                    const int e = tid + it * TC_PRODUCERS;
+                    if (e >= D * TC_NT * 2) break;
                     const int ih = e & 1, o = (e >> 1) & (TC_NT - 1), dxi = e >> 5;
                     const float4 *src = reinterpret_cast<const float4 *>(rb + (dxi * TC_NT + o) * TC_NT + 8 * ih);
                     const float4 l0 = src[0], l1 = src[1];
@@ -554,7 +558,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_conv_kernel(const ConvArgs a
         }
         // after an abort, the copies tid 0 issued for a step not yet consumed may still be in flight
         if (tid == 0 && s_abort)
-            for (int q = 0; q < issued; ++q) bar_wait(&raw_bar[q & 1], (q >> 1) & 1);
+            for (int q = 0; q < issued; ++q) bar_wait(&raw_bar[q % NRAW], (q / NRAW) & 1);
     } else if (lane == 0) {
         // the MMA issuer: step qi covers output rows s in [max(0, qi - 2r), min(S - 1, qi)] with
         // dy = s - qi + r, B slots (s - qi + 2r) % NB ascending in s (split where the ring wraps)
@@ -569,69 +573,116 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_conv_kernel(const ConvArgs a
             const int s_lo = max(0, qi - 2 * r), s_hi = min(TC_S - 1, qi);
             const int sl_lo = (s_lo - qi + 2 * r) % NB;
             const int run1 = min(s_hi - s_lo + 1, NB - sl_lo);   // rows before the ring wraps
+            // descriptors advance by constants per tap: the start address field counts 16-byte units,
+            // A moves back one row (16 bytes) and B forward one dx block (NB x 256 bytes) per dx
             const uint32_t arow = a0 + (qi % NA) * 2 * APLANE;
+            uint64_t da = sdesc(arow + 2 * r * 16, APLANE, 128);
+            uint64_t db1 = sdesc(b0 + sl_lo * 256, BPL, 128), db2 = sdesc(b0, BPL, 128);
+            const uint32_t d1 = tmem + s_lo * TC_NT, d2 = tmem + (s_lo + run1) * TC_NT;
+            const uint32_t id1 = idesc(TC_NT * run1), id2 = idesc(TC_NT * (s_hi - s_lo + 1 - run1));
+            const bool split = run1 < s_hi - s_lo + 1;
             for (int dxi = 0; dxi < D; ++dxi) {
-                const uint64_t da = sdesc(arow + (2 * r - dxi) * 16, APLANE, 128);
-                mma(tmem + s_lo * TC_NT, da, sdesc(b0 + (dxi * NB + sl_lo) * 256, BPL, 128), idesc(TC_NT * run1));
-                if (run1 < s_hi - s_lo + 1)
-                    mma(tmem + (s_lo + run1) * TC_NT, da, sdesc(b0 + (dxi * NB) * 256, BPL, 128),
-                        idesc(TC_NT * (s_hi - s_lo + 1 - run1)));
+                mma(d1, da, db1, id1);
+                if (split) mma(d2, da, db2, id2);
+                da -= 1;
+                db1 += NB * 256 / 16;
+                db2 += NB * 256 / 16;
             }
             commit(&empty_bar[qi % NST]);
         }
         commit(&done_bar);
     }
 
-    // ---- 6. epilogue: warps 0-3 read their 32 lanes (positions) of every output row
-    float omax[TC_NT];
+    // ---- 6. epilogue: every warp reads the 32 lanes (positions) of quarter warp % 4 for the 8 output
+    //      orientations of half warp / 4, row by row; the 8 results of a row are computed together
+    //      (independent chains) before anything is stored.
+    constexpr int OH = TC_NT / 2;
+    const int oh = (warp >> 2) * OH;   // first orientation of this warp's half
+    float omax[OH];
 #pragma unroll
-    for (int o = 0; o < TC_NT; ++o) omax[o] = -INFINITY;
-    if (warp < 4) {
-        if (!bar_wait(&done_bar, 0)) {
-            s_abort = 1;
-            atomicExch(t.err, 1u);
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const int m = 32 * warp + lane, x = x0 + m;
-        for (int s = 0; s < TC_S; ++s) {
-            uint32_t v[16];
-            asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                         : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-                           "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-                           "=r"(v[14]), "=r"(v[15])
-                         : "r"(tmem + ((uint32_t)(32 * warp) << 16) + s * TC_NT));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    for (int o = 0; o < OH; ++o) omax[o] = -INFINITY;
+    __syncwarp();   // warp 7 arrives from the divergent MMA issue; the TMEM loads below are warp-wide
+    if (!bar_wait(&done_bar, 0)) {
+        s_abort = 1;
+        atomicExch(t.err, 1u);
+    }
+    __syncwarp();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const int m = 32 * (warp & 3) + lane, x = x0 + m;
+    const bool sink = a.epi == EPI_W || a.epi == EPI_D;
+    float2 auxr[TC_S][OH];   // every row's aux values in flight together
+#pragma unroll
+    for (int s = 0; s < TC_S; ++s)
+#pragma unroll
+        for (int k = 0; k < OH; ++k) {
             const int y = y0 + s;
-            if (y >= ny || x >= nx || s_abort) continue;
-            const float P = gy * (float)s + gx * (float)m;
+            const bool live = sink && y < ny && x < nx && oh + k < nt;
+            auxr[s][k] = live ? a.aux[((long)(b * nt + oh + k) * ny + y) * nx + x] : make_float2(0.f, 0.f);
+        }
 #pragma unroll
-            for (int o = 0; o < TC_NT; ++o) {
-                if (o >= nt) break;
-                const long flat = ((long)(b * nt + o) * ny + y) * nx + x;
-                const float C = __uint_as_float(v[o]);
-                const float lc = log2f(C);
-                if (!(lc >= ACCEPT_MIN && lc <= 127.f)) {
-                    const unsigned k = atomicAdd(a.redo_count, 1u);
-                    a.redo_list[k] = make_int2(0, (int)flat);
-                    omax[o] = INFINITY;
-                    continue;
-                }
-                epilogue_out(a, flat, b, o, y, x, P + s_c[o], lc);
-                if (a.tmax_out) omax[o] = fmaxf(omax[o], a.out2[flat].x);
+    for (int s = 0; s < TC_S; ++s) {
+        uint32_t v[OH];
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                     : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                     : "r"(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + s * TC_NT + oh));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        const int y = y0 + s;
+        const bool pos = y < ny && x < nx && !s_abort;
+        const float P = gy * (float)s + gx * (float)m;
+        const long flat0 = ((long)(b * nt + oh) * ny + y) * nx + x;   // orientation oh; + k plane for oh + k
+        const float2 *aux = auxr[s];
+        float lc[OH];
+        unsigned bad = 0;   // bit k: output oh + k goes to the exact recompute
+#pragma unroll
+        for (int k = 0; k < OH; ++k) {
+            const bool live = pos && oh + k < nt;
+            lc[k] = log2f(__uint_as_float(v[k]));
+            if (live && !(lc[k] >= ACCEPT_MIN && lc[k] <= 127.f)) bad |= 1u << k;
+        }
+        // rejected outputs: consecutive entries of the list, one atomic per warp and row
+        const unsigned nb = __popc(bad);
+        unsigned pre = nb;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const unsigned t2 = __shfl_up_sync(0xffffffffu, pre, off);
+            if (lane >= off) pre += t2;
+        }
+        const unsigned total = __shfl_sync(0xffffffffu, pre, 31);
+        unsigned base = 0;
+        if (lane == 31 && total) base = atomicAdd(a.redo_count, total);
+        base = __shfl_sync(0xffffffffu, base, 31) + pre - nb;
+#pragma unroll
+        for (int k = 0; k < OH; ++k) {
+            const bool live = pos && oh + k < nt;
+            if (!live) continue;
+            const long flat = flat0 + (long)k * plane;
+            if (bad >> k & 1u) {
+                a.redo_list[base++] = make_int2(0, (int)flat);
+                omax[k] = INFINITY;
+                continue;
+            }
+            if (sink) {   // w_i = mu_i / K v_i or d_i = v_i K w_i, and the shift of the next launch
+                const float2 c = df_add(make_float2(P + s_c[oh + k], 0.f), make_float2(lc[k], 0.f));
+                const float2 w = df_add(aux[k], a.epi == EPI_W ? df_neg(c) : c);
+                a.out2[flat] = w;
+                a.hint[flat] = c.x + c.y;
+                omax[k] = fmaxf(omax[k], w.x);
+            } else {
+                epilogue_out(a, flat, b, oh + k, y, x, P + s_c[oh + k], lc[k]);
             }
         }
-        if (a.tmax_out) {   // inner-tile maxima of the output for the FP32 kernel's 16 x 32 tiles
-            const int ntx = (nx + TILE_X - 1) / TILE_X, nty = (ny + TILE_Y - 1) / TILE_Y;
-            const int tx = (x0 + 32 * warp) / TILE_X, ty = y0 / TILE_Y;
+    }
+    if (a.tmax_out) {   // inner-tile maxima of the output for the FP32 kernel's 16 x 32 tiles
+        const int ntx = (nx + TILE_X - 1) / TILE_X, nty = (ny + TILE_Y - 1) / TILE_Y;
+        const int tx = (x0 + 32 * (warp & 3)) / TILE_X, ty = y0 / TILE_Y;
 #pragma unroll
-            for (int o = 0; o < TC_NT; ++o) {
-                if (o >= nt) break;
-                float mv = omax[o];
+        for (int k = 0; k < OH; ++k) {
+            if (oh + k >= nt) break;
+            float mv = omax[k];
 #pragma unroll
-                for (int off = 16; off; off >>= 1) mv = fmaxf(mv, __shfl_xor_sync(0xffffffffu, mv, off));
-                if (lane == 0 && tx < ntx && mv > -INFINITY)
-                    atomic_fmax(a.tmax_out + ((long)(b * nt + o) * nty + ty) * ntx + tx, mv);
-            }
+            for (int off = 16; off; off >>= 1) mv = fmaxf(mv, __shfl_xor_sync(0xffffffffu, mv, off));
+            if (lane == 0 && tx < ntx && mv > -INFINITY)
+                atomic_fmax(a.tmax_out + ((long)(b * nt + oh + k) * nty + ty) * ntx + tx, mv);
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -692,13 +743,13 @@ __global__ void fill_kernel(float *p, long n, float v)
 
 }  // namespace
 
-// Grids of the tensor-core path: ntheta <= 16 (the K and N slots of one tap), nx even (16-byte bulk
-// copies of double-float rows), at least half a tile wide, and on a periodic grid wide enough that a
-// halo row wraps at most once on each side.
+// Grids of the tensor-core path: ntheta <= 16 (the K and N slots of one tap), nx even (rows of the
+// tensor map start on 16-byte boundaries), at least half a tile wide, zero boundary (the TMA box does
+// not wrap).
 bool tc_supported(const se2ot_kernel_desc &d)
 {
-    if (d.ntheta > TC_NT || d.radius > MAX_RADIUS || d.nx < TC_M / 2 || (d.nx & 1)) return false;
-    return d.boundary != SE2OT_BOUNDARY_PERIODIC || d.nx >= TC_M + 2 * d.radius;
+    return d.ntheta <= TC_NT && d.radius <= MAX_RADIUS && d.nx >= TC_M / 2 && !(d.nx & 1) &&
+           d.boundary == SE2OT_BOUNDARY_ZERO;
 }
 
 size_t tc_taps_floats(const se2ot_kernel_desc &d)
@@ -725,6 +776,21 @@ cudaError_t launch_fill(float *p, long n, float v, cudaStream_t s)
 
 int tc_tiles(int nx, int ny) { return ((nx + TC_M - 1) / TC_M) * ((ny + TC_S - 1) / TC_S); }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link against libcuda).
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static std::once_flag once;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::call_once(once, []() {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
 cudaError_t launch_conv_tc(const ConvArgs &a, const TcArgs &t, cudaStream_t s)
 {
     const int D = 2 * a.r + 1;
@@ -734,9 +800,22 @@ cudaError_t launch_conv_tc(const ConvArgs &a, const TcArgs &t, cudaStream_t s)
         return cudaFuncSetAttribute(tc_conv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem(2 * MAX_RADIUS + 1));
     });
     if (e != cudaSuccess) return e;
+    // the input as a 3D tensor of 8-byte double-floats: x (nx), y (ny), slice (batch * nt); a box is one
+    // raw row of BOXW positions of every slice of one field
+    PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+    if (!encode) return cudaErrorNotSupported;
+    CUtensorMap map;
+    const cuuint64_t dims[3] = {(cuuint64_t)a.nx, (cuuint64_t)a.ny, (cuuint64_t)a.batch * a.nt};
+    const cuuint64_t strides[2] = {(cuuint64_t)a.nx * 8, (cuuint64_t)a.nx * a.ny * 8};
+    const cuuint32_t box[3] = {(cuuint32_t)BOXW, 1u, (cuuint32_t)a.nt};
+    const cuuint32_t estr[3] = {1u, 1u, 1u};
+    if (encode(&map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, const_cast<float2 *>(a.in), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
     dim3 grid((a.nx + TC_M - 1) / TC_M, (a.ny + TC_S - 1) / TC_S, a.batch);
     PdlLaunch L(grid, dim3(TC_THREADS), smem, s);
-    return cudaLaunchKernelEx(&L.cfg, tc_conv_kernel, a, t);
+    return cudaLaunchKernelEx(&L.cfg, tc_conv_kernel, a, t, map);
 }
 
 }  // namespace se2ot
