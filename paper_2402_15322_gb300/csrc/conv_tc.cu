@@ -7,18 +7,27 @@
 // input position and a part of the tap.  A tile of S = 4 output rows x 128 positions takes one
 // tilt plane P(y, x) = gy y + gx x (least squares on the previous outputs of the same
 // convolution), a shift alpha_i per input slice and c_o per output orientation:
-//   A(q, i)    = 2^(lf(q, i) - P(q) - alpha_i)                 (BF16, <= 2^55)
-//   B(i, d, o) = 2^(lk(o, i, d) - P(d) + alpha_i - c_o)        (BF16, <= 2^55)
+//   A(q, i)    = 2^(lf(q, i) - P(q) - alpha_i)                 (BF16, <= 2^top_i)
+//   B(i, d, o) = 2^(lk(o, i, d) - P(d) + alpha_i - c_o)        (BF16, <= 2^(110 - top_i))
 //   out(p, o)  = log2 C[p, o] + P(p) + c_o                     (q + d = p, so P(q) + P(d) = P(p))
-// with alpha_i = max_q (lf - P) - 55 over the tile's halo and c_o such that the largest possible
-// product is 2^110 (a sum of at most 2^13 terms stays below FP32's 2^128).  A product of two BF16
-// values >= 2^-126 each is exact in the FP32 accumulator, so a term is lost to underflow only when
-// one factor is below 2^-126, i.e. when the product is below 2^(55 - 126) = 2^-71.  An output with
-// log2 C >= -40 therefore loses only terms below 2^-31 of itself (at most 2^13 of them: < 4e-6
-// relative), far below the BF16 rounding of its operands (each within 2^-8, a product within
-// 2^-7 relative): such outputs are accepted; the others are queued for the exact recompute
-// (conv.cu).  A tile whose previous outputs predict log2 C < -30 anywhere is not computed here: its
-// 16 x 32 tiles of the FP32 kernel are queued in a work list that the FP32 kernel runs next.
+// with c_o such that the largest possible product is 2^110 (a sum of at most 2^13 terms stays below
+// FP32's 2^128) and alpha_i = R_i - top_i, R_i = max over the tile's halo of (lf - P) of slice i.
+// A product of two BF16 values >= 2^-126 each is exact in the FP32 accumulator.  For an output with
+// log2 C = l, a term that matters (product >= 2^(l - 31)) has B >= 2^(l - 31 - top_i), unflushed when
+// l >= top_i - 95; a term whose A flushed is below 2^(-126 + 110 - top_i), negligible when
+// l >= 15 - top_i.  With span_i = R_i minus the halo's minimum, the split of slice i is the best of:
+//   span_i <= 120: top_i = 0 (no A flushes: A >= 2^-120), threshold -90 (5 of margin);
+//   span_i < 175:  top_i = span_i - 120 (still no A flushes), threshold span_i - 210;
+//   else:          top_i = 55 (both sides), threshold -35.
+// A slice whose at most 2^9 terms for output orientation o are all below 2^(l - 40) (their bound is
+// 2^(R_i + Tmax(o, i) - c_o)) cannot matter to an output l, so the threshold of orientation o is
+// max_i min(threshold_i, that bound + 41).  An output with l >= its orientation's threshold loses only
+// terms below 2^-31 of itself (at most 2^13 of them: < 4e-6 relative), far below the BF16 rounding of
+// its operands (each within 2^-8, a product within 2^-7 relative): such outputs are accepted; the
+// others are queued for the exact recompute (conv.cu).  A tile whose previous outputs predict l below
+// that threshold + 10 anywhere is not computed here: its 16 x 32 tiles of the FP32 kernel are queued
+// in a work list that the FP32 kernel runs next.  The previous outputs alone already rule out tiles whose outputs, after the plane,
+// span more than 205 octaves (the gap c_o + 110 - (out - P) is at least that span minus 13).
 //
 // GEMM shape: M = 128 positions of one row (an MMA of the instruction shape 128 x N x 16), K = the
 // 16 input orientations of one tap, N = 16 output orientations x the output rows that one input row
@@ -51,8 +60,9 @@ constexpr int NA = 3;              // input-row slots
 constexpr int NB = TC_S + 1;       // dy-block slots
 constexpr int NST = 4;             // pipeline stages of the barriers
 constexpr int APLANE = (TC_M + 2 * MAX_RADIUS) * 16;   // bytes of one half (8 channels) of an input row
-constexpr float A_TOP = 55.f, PMAX = 110.f;
-constexpr float ELIG_MIN = -30.f, ACCEPT_MIN = -40.f;
+constexpr float PMAX = 110.f;      // log2 of the largest possible product (sums of < 2^13 terms stay < 2^127)
+constexpr float A_SPAN = 120.f;    // A keeps this many octaves below its top unflushed
+constexpr float ACCEPT_SLACK = 90.f, ELIG_MARGIN = 10.f;   // see the acceptance rule above
 constexpr long SPIN_LIMIT = 1L << 24;
 
 constexpr int BOXW = TC_M + 2 * MAX_RADIUS + 8;          // positions of a raw input row (TMA box width)
@@ -218,6 +228,22 @@ __device__ void issue_row(const CUtensorMap *map, int nt, int x0, int r, int qy,
     issue_row_tma(map, x0, r, qy, zslice, raw, bar);
 }
 
+// Queue the FP32 kernel's 16 x 32 tiles (every orientation) that cover tile (b, y0, x0), once each.
+__device__ void queue_fallback(const ConvArgs &a, const TcArgs &t, int b, int x0, int y0)
+{
+    const int nx = a.nx, ny = a.ny, nt = a.nt;
+    const int ntx = (nx + TILE_X - 1) / TILE_X, nty = (ny + TILE_Y - 1) / TILE_Y;
+    const int ty = y0 / TILE_Y;
+    for (int tx = x0 / TILE_X; tx < ntx && tx * TILE_X < x0 + TC_M; ++tx) {
+        unsigned *cl = t.fb_claim + ((long)b * nty + ty) * ntx + tx;
+        if (atomicMax(cl, t.seq) < t.seq) {
+            const unsigned k = atomicAdd(t.fb_count, (unsigned)nt);
+            for (int o = 0; o < nt; ++o) t.fb_items[k + o] = make_int4(0, b * nt + o, tx, ty);
+        }
+    }
+    atomicAdd(t.tiles + 1, 1ull);
+}
+
 __global__ void __launch_bounds__(TC_THREADS, 1) tc_conv_kernel(const ConvArgs a, const TcArgs t,
                                                                  const __grid_constant__ CUtensorMap in_map)
 {
@@ -236,7 +262,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_conv_kernel(const ConvArgs a
     __shared__ float s_alpha[TC_NT], s_rmax[TC_NT], s_c[TC_NT], s_tmx[TC_NT * TC_NT];
     __shared__ float s_part[TC_THREADS / 32][TC_NT];
     __shared__ float s_red[TC_THREADS / 32][9];
-    __shared__ float s_g[2];
+    __shared__ float s_g[2], s_thr[TC_NT], s_acc[TC_NT];
     __shared__ int s_ok, s_abort;
 
     const int x0 = blockIdx.x * TC_M, y0 = blockIdx.y * TC_S, b = blockIdx.z;
@@ -311,19 +337,74 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_conv_kernel(const ConvArgs a
         s_g[0] = isfinite(gy) ? gy : 0.f;
         s_g[1] = isfinite(gx) ? gx : 0.f;
         s_ok = all_finite && n > 0.f;
-        if (s_ok)   // the first halo rows of the statistics pass
-            for (int k = 0; k < NSB && k < HY; ++k)
-                issue_row(&in_map, nt, x0, r, y0 - r + k, b * nt, smem + k * RAWA, &stat_bar[k]);
     }
     __syncthreads();
     const float gy = s_g[0], gx = s_g[1];
 
+    // ---- 1b. span of the previous outputs after the plane, per orientation: more than 205 octaves
+    //      rules the tile out before any staging
+    {
+        float lo[TC_NT], hi[TC_NT];
+#pragma unroll
+        for (int o = 0; o < TC_NT; ++o) {
+            lo[o] = INFINITY;
+            hi[o] = -INFINITY;
+        }
+        if (s_ok)
+            for (int e = tid; e < TC_S * TC_M; e += TC_THREADS) {
+                const int s2 = e / TC_M, m = e - s2 * TC_M, y = y0 + s2, x = x0 + m;
+                if (y >= ny || x >= nx) continue;
+                const float P = gy * (float)s2 + gx * (float)m;
+                float h[TC_NT];
+#pragma unroll
+                for (int o = 0; o < TC_NT; ++o) h[o] = o < nt ? a.hint[((long)(b * nt + o) * ny + y) * nx + x] - P : 0.f;
+#pragma unroll
+                for (int o = 0; o < TC_NT; ++o) {
+                    lo[o] = fminf(lo[o], h[o]);
+                    hi[o] = fmaxf(hi[o], h[o]);
+                }
+            }
+        float span = 0.f;
+#pragma unroll
+        for (int o = 0; o < TC_NT; ++o) {
+#pragma unroll
+            for (int off = 16; off; off >>= 1) {
+                lo[o] = fminf(lo[o], __shfl_xor_sync(0xffffffffu, lo[o], off));
+                hi[o] = fmaxf(hi[o], __shfl_xor_sync(0xffffffffu, hi[o], off));
+            }
+            if (lane == 0) {
+                s_part[warp][o] = lo[o];
+                s_tmx[warp * TC_NT + o] = hi[o];
+            }
+        }
+        __syncthreads();
+        if (tid < TC_NT) {
+            float l2 = INFINITY, h2 = -INFINITY;
+            for (int w = 0; w < TC_THREADS / 32; ++w) {
+                l2 = fminf(l2, s_part[w][tid]);
+                h2 = fmaxf(h2, s_tmx[w * TC_NT + tid]);
+            }
+            span = h2 - l2;
+        }
+        const int too_wide = __syncthreads_or(tid < nt && s_ok && !(span <= 205.f));
+        if (too_wide || !s_ok) {
+            if (tid == 0) queue_fallback(a, t, b, x0, y0);
+            return;   // nothing staged yet
+        }
+        if (tid == 0)   // the first halo rows of the statistics pass
+            for (int k = 0; k < NSB && k < HY; ++k)
+                issue_row(&in_map, nt, x0, r, y0 - r + k, b * nt, smem + k * RAWA, &stat_bar[k]);
+    }
+
     // ---- 2. largest residual R_i = max (lf - P) of every input slice over the halo (hi parts), from
     //      the raw rows staged by bulk copies (two buffers).  A NaN or +inf input makes the tile
     //      ineligible.
-    float rm[TC_NT];
+    float rm[TC_NT], rn[TC_NT];   // largest and smallest finite residual
 #pragma unroll
-    for (int i = 0; i < TC_NT; ++i) rm[i] = -INFINITY;
+    for (int i = 0; i < TC_NT; ++i) {
+        rm[i] = -INFINITY;
+        rn[i] = INFINITY;
+    }
     bool bad = false;
     if (s_ok) {
         for (int hy = 0; hy < HY; ++hy) {
@@ -346,6 +427,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_conv_kernel(const ConvArgs a
                         bad |= !(h <= 3.0e38f) && h == h && h > 0.f;   // +inf
                         bad |= h != h;                                   // NaN
                         rm[i] = fmaxf(rm[i], h - P);
+                        if (h > -INFINITY) rn[i] = fminf(rn[i], h - P);
                     }
                 }
             }
@@ -357,15 +439,42 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_conv_kernel(const ConvArgs a
 #pragma unroll
     for (int i = 0; i < TC_NT; ++i) {
 #pragma unroll
-        for (int off = 16; off; off >>= 1) rm[i] = fmaxf(rm[i], __shfl_xor_sync(0xffffffffu, rm[i], off));
-        if (lane == 0) s_part[warp][i] = rm[i];
+        for (int off = 16; off; off >>= 1) {
+            rm[i] = fmaxf(rm[i], __shfl_xor_sync(0xffffffffu, rm[i], off));
+            rn[i] = fminf(rn[i], __shfl_xor_sync(0xffffffffu, rn[i], off));
+        }
+        if (lane == 0) {
+            s_part[warp][i] = rm[i];
+            s_tmx[warp * TC_NT + i] = rn[i];
+        }
     }
     const int any_bad = __syncthreads_or(bad);
     if (tid < TC_NT) {
-        float m = -INFINITY;
-        for (int w = 0; w < TC_THREADS / 32; ++w) m = fmaxf(m, s_part[w][tid]);
+        float m = -INFINITY, mn = INFINITY;
+        for (int w = 0; w < TC_THREADS / 32; ++w) {
+            m = fmaxf(m, s_part[w][tid]);
+            mn = fminf(mn, s_tmx[w * TC_NT + tid]);
+        }
+        // the split of slice tid and the threshold it imposes (see the header): A unflushed with A
+        // at the bottom of the range (span <= 120), A raised just enough to stay unflushed (span <
+        // 175), else the even split 55 / 55
+        const float span = m - mn;
+        float top = 0.f, thr = -ACCEPT_SLACK;
+        if (!isfinite(m) || !isfinite(span)) {
+            top = 0.f;
+            thr = -INFINITY;   // no term of this slice
+        } else if (span <= A_SPAN) {
+            top = 0.f;
+        } else if (span < 175.f) {
+            top = span - A_SPAN;
+            thr = span - 210.f;
+        } else {
+            top = 55.f;
+            thr = -35.f;
+        }
         s_rmax[tid] = m;
-        s_alpha[tid] = isfinite(m) ? m - A_TOP : 0.f;
+        s_alpha[tid] = isfinite(m) ? m - top : 0.f;
+        s_thr[tid] = tid < nt ? thr : -INFINITY;
     }
     if (tid == 0 && any_bad) s_ok = 0;
     __syncthreads();
@@ -402,10 +511,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_conv_kernel(const ConvArgs a
             if (isfinite(s_rmax[i])) c = fmaxf(c, s_rmax[i] + s_tmx[tid * TC_NT + i]);
         s_c[tid] = isfinite(c) ? c - PMAX : 0.f;
         if (tid < nt && !isfinite(c)) s_ok = 0;
+        // acceptance threshold of output orientation o = tid: slice i's at most 2^9 terms are each
+        // below 2^(R_i + Tmax(o, i) - c_o), negligible for an output l when that is below l - 40, so
+        // slice i constrains l only up to min(its threshold, that bound + 41)
+        float acc = -ACCEPT_SLACK;
+        for (int i = 0; i < nt; ++i) {
+            const float bound = s_rmax[i] + s_tmx[tid * TC_NT + i] - (c - PMAX);
+            if (isfinite(bound)) acc = fmaxf(acc, fminf(s_thr[i], bound + 41.f));
+        }
+        s_acc[tid] = acc;
     }
     __syncthreads();
 
-    // ---- 4. eligibility: the previous outputs predict log2 C = S - P(p) - c_o >= ELIG_MIN everywhere
+    // ---- 4. eligibility: the previous outputs predict log2 C = S - P(p) - c_o above the acceptance
+    //      threshold + ELIG_MARGIN everywhere
     bool elig = s_ok != 0;
     if (elig) {
         for (int e = tid; e < TC_S * TC_M; e += TC_THREADS) {
@@ -417,24 +536,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_conv_kernel(const ConvArgs a
             for (int o = 0; o < TC_NT; ++o) h[o] = o < nt ? a.hint[((long)(b * nt + o) * ny + y) * nx + x] : 0.f;
 #pragma unroll
             for (int o = 0; o < TC_NT; ++o)
-                if (o < nt) elig &= h[o] - P - s_c[o] >= ELIG_MIN;
+                if (o < nt) elig &= h[o] - P - s_c[o] >= s_acc[o] + ELIG_MARGIN;
         }
     }
     elig = __syncthreads_and(elig);
     if (!elig) {
-        // queue the FP32 kernel's 16 x 32 tiles (every orientation) that cover this tile, once each
-        if (tid == 0) {
-            const int ntx = (nx + TILE_X - 1) / TILE_X, nty = (ny + TILE_Y - 1) / TILE_Y;
-            const int ty = y0 / TILE_Y;
-            for (int tx = x0 / TILE_X; tx < ntx && tx * TILE_X < x0 + TC_M; ++tx) {
-                unsigned *cl = t.fb_claim + ((long)b * nty + ty) * ntx + tx;
-                if (atomicMax(cl, t.seq) < t.seq) {
-                    const unsigned k = atomicAdd(t.fb_count, (unsigned)nt);
-                    for (int o = 0; o < nt; ++o) t.fb_items[k + o] = make_int4(0, b * nt + o, tx, ty);
-                }
-            }
-            atomicAdd(t.tiles + 1, 1ull);
-        }
+        if (tid == 0) queue_fallback(a, t, b, x0, y0);
         return;   // no bulk copy is in flight: the statistics pass waited for every row
     }
 
@@ -637,7 +744,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_conv_kernel(const ConvArgs a
         for (int k = 0; k < OH; ++k) {
             const bool live = pos && oh + k < nt;
             lc[k] = log2f(__uint_as_float(v[k]));
-            if (live && !(lc[k] >= ACCEPT_MIN && lc[k] <= 127.f)) bad |= 1u << k;
+            if (live && !(lc[k] >= s_acc[oh + k] && lc[k] <= 127.f)) bad |= 1u << k;
         }
         // rejected outputs: consecutive entries of the list, one atomic per warp and row
         const unsigned nb = __popc(bad);

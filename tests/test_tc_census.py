@@ -3,7 +3,8 @@ factorisation in tc_emulation.py; no CUDA).
 
 The tensor-core kernel computes each tile of the log-domain convolution (Sec. 4.2) as a BF16 GEMM
 after rescaling by a tilt plane and per-slice / per-orientation shifts, and accepts an output only
-when log2 of its accumulator is >= -40.  These tests pin:
+when log2 of its accumulator clears the tile's threshold (max_i top_i - 90, see tc_emulation.py).
+These tests pin:
   (1) the accuracy claim: every accepted output is within log2((1 + 2^-8)^2) + 4e-6 < 0.0113 log2
       units of the oracle's exact convolution (each BF16 operand rounds within 2^-8 relative; the
       terms lost to underflow are below 2^-31 of an accepted output, at most 2^13 of them);
