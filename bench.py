@@ -544,7 +544,10 @@ def run_gpu(args):
             eval_terms_per_s = terms_per_launch / avg_conv_s
             peak_tc = peaks["bf16_tflops_sustained"]
             result["roofline"] = {
-                "bound": "tensor", "kernel": "conv_tile_kernel<%d, false>: log-domain group convolution" % r,
+                "bound": "tensor",
+                "kernel": ("one convolution on the tensor-core path: tc_conv_kernel (BF16 tcgen05) plus the "
+                           "conv_tile_kernel<%d> launches it leaves to FP32" % r) if args.precision == "bf16" else
+                          "conv_tile_kernel<%d, false>: log-domain group convolution" % r,
                 "achieved": achieved_tflops, "peak": peak_tc, "unit": "TFLOP/s",
                 "frac": achieved_tflops / peak_tc,
                 "traffic": conv_traffic() if args.config == "barycenter" else None,
