@@ -1,0 +1,117 @@
+"""The large grids in the regime the solve is timed in: several hundred Sinkhorn iterations of the
+Appendix A barycenter, then the convolution checked on that late state against the FP64 oracle at
+sampled outputs (the oracle cannot convolve these grids whole).
+
+After iteration T the exported state (natural logs) satisfies, with L = log mu:
+    lv_T = lv_{T-1} + L - ld,     ld = lv_{T-1} + log K (mu_in / K v_{T-1})
+so lv_{T-1} = lv_T - L + ld is recovered exactly (to ~1e-12), and two convolutions can be checked:
+  (1) se2ot_apply_log on lv_{T-1}, a scaling vector as steep as the solve makes them: 1024 seeded
+      outputs per measure within 5e-6 (natural log) of oracle.conv_log_points;
+  (2) the solver's own d-line convolution of the last iteration (history shifts, skipping, the
+      launch order the benchmark times): ld - lv_{T-1} = log K exp(lw) with lw = log mu_in -
+      log K v_{T-1}.  lw is rebuilt from (1)'s output, within 5e-6 of the solver's own lw, and a
+      log-sum-exp moves by at most the sup-norm of its input's change, so the bar is
+      5e-6 (this convolution) + 2 x 5e-6 (the two lw's) = 1.5e-5.
+The samples cover the whole grid uniformly, the boundary band of width r, the first and last
+row and column of the 16 x 32 convolution tiles, and outputs drawn in proportion to the
+barycenter's mass (where the transport is).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2402_15322_gb300 import build, se2ot, synth
+
+pytestmark = pytest.mark.gpu
+
+W = (1.0, 3.0, 0.5)
+TILE_Y, TILE_X = 16, 32
+APPLY_TOL = 5e-6
+DLINE_TOL = 1.5e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+    se2ot.lib()
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+
+
+def sample_outputs(nx, ny, nt, r, mass, seed, per_kind=264):
+    """Flat [y, x, k] output indices: uniform, boundary band, tile edges, mass-weighted."""
+    rng = np.random.default_rng(seed)
+    V = nx * ny * nt
+    uni = rng.choice(V, size=per_kind, replace=False)
+    ys, xs, ks = [], [], []
+    while len(ys) < per_kind:   # boundary band: within r of an edge of the grid
+        y, x = int(rng.integers(0, ny)), int(rng.integers(0, nx))
+        if min(y, ny - 1 - y, x, nx - 1 - x) < r:
+            ys.append(y), xs.append(x), ks.append(int(rng.integers(0, nt)))
+    band = (np.array(ys) * nx + np.array(xs)) * nt + np.array(ks)
+    ty = rng.integers(0, ny // TILE_Y, size=per_kind) * TILE_Y + rng.choice([0, TILE_Y - 1], size=per_kind)
+    tx = rng.integers(0, nx // TILE_X, size=per_kind) * TILE_X + rng.choice([0, TILE_X - 1], size=per_kind)
+    edge = (ty * nx + tx) * nt + rng.integers(0, nt, size=per_kind)
+    p = mass.reshape(-1).astype(np.float64)
+    heavy = rng.choice(V, size=per_kind, replace=False, p=p / p.sum())
+    return np.unique(np.concatenate([uni, band, edge, heavy]).astype(np.int64))
+
+
+def run_late_state(nx, ny, nt, r, eps, mu, lam, iters, seed):
+    n = mu.shape[0]
+    k = se2ot.se2ot_kernel_build(se2ot.make_desc(nx, ny, nt, r, W, eps))
+    g = oracle.Grid(nx, ny, nt, r, W, eps)
+    bary, st, _ = se2ot.se2ot_barycenter(k, torch.from_numpy(mu).cuda(), lam,
+                                         se2ot.solve_opts(iters, flags=se2ot.SE2OT_FLAG_TIME_CONV))
+    assert st["iters"] == iters
+    lv, ld, L = se2ot.se2ot_state_export(k, n)
+    lv_prev = lv - L[None] + ld                      # lv_{T-1}, on the device in FP64
+    conv_v = se2ot.se2ot_apply_log(k, lv_prev)       # log K v_{T-1}
+    lv_prev_h, conv_v_h, ld_h = (t.cpu().numpy() for t in (lv_prev, conv_v, ld))
+    bary_h = bary.cpu().numpy()
+    del lv, ld, L, lv_prev, conv_v
+    k.close()
+    idx = sample_outputs(nx, ny, nt, r, bary_h, seed)
+    assert idx.size >= 1024
+    worst_apply, worst_dline = 0.0, 0.0
+    for i in range(n):
+        flat = lv_prev_h[i].reshape(-1)
+        assert np.isfinite(flat).all()
+        want = oracle.conv_log_points(g, lv_prev_h[i][None], idx)
+        e1 = np.abs(conv_v_h[i].reshape(-1)[idx] - want).max()
+        lw = np.log(mu[i].astype(np.float64)) - conv_v_h[i]
+        want_d = oracle.conv_log_points(g, lw[None], idx)
+        e2 = np.abs((ld_h[i] - lv_prev_h[i]).reshape(-1)[idx] - want_d).max()
+        worst_apply, worst_dline = max(worst_apply, e1), max(worst_dline, e2)
+    span = float(lv_prev_h.max() - lv_prev_h.min())
+    print("\n%dx%dx%d r=%d eps=%g, %d iterations: %d sampled outputs per measure, log v span %.0f nats, "
+          "redo_outputs %d, max |err| apply_log %.2e, d-line %.2e, conv %.2f ms/launch"
+          % (nx, ny, nt, r, eps, iters, idx.size, span, st["redo_outputs"], worst_apply, worst_dline,
+             st["conv_ms"] / max(1, st["conv_launches"])))
+    return st, span, worst_apply, worst_dline
+
+
+def test_512x512x32_after_300_iterations_sampled_against_oracle():
+    """The large single solve (3 curve measures, kernel 31 x 31 x 32, eps = 2e-5) after 300 of its
+    iterations."""
+    nx = ny = 512
+    nt, r, eps = 32, 15, 2e-5
+    mu = synth.curve_measures(3, nx, ny, nt, config_seed=5, max_shift=r // 2).astype(np.float32)
+    st, span, e_apply, e_dline = run_late_state(nx, ny, nt, r, eps, mu, [1 / 3] * 3, 300, seed=512)
+    assert span > 100.0, "the state is not in the steep late regime"
+    assert e_apply <= APPLY_TOL
+    assert e_dline <= DLINE_TOL
+    assert st["redo_outputs"] < 0.01 * 2 * 300 * 3 * nx * ny * nt
+
+
+def test_256x256x32_after_400_iterations_sampled_against_oracle():
+    """A 256^2 x 32 interpolation of the batched workload's largest size at its smallest eps
+    (5e-5), kernel 31 x 31 x 32, after 400 iterations."""
+    nx = ny = 256
+    nt, r, eps = 32, 15, 5e-5
+    mu = synth.curve_measures(2, nx, ny, nt, config_seed=7, max_shift=r // 2).astype(np.float32)
+    st, span, e_apply, e_dline = run_late_state(nx, ny, nt, r, eps, mu, [0.5, 0.5], 400, seed=256)
+    assert span > 100.0
+    assert e_apply <= APPLY_TOL
+    assert e_dline <= DLINE_TOL
+    assert st["redo_outputs"] < 0.01 * 2 * 400 * 2 * nx * ny * nt
