@@ -29,9 +29,12 @@
 // a thread usually lie close to a line, S_j ~ T_j = S_0 + g j (g on a 2^-6 grid, |g| <= 32).  With
 // that shift the term splits exactly into a part of the input position alone and a part of the
 // tap alone,
-//   t = u_k + tp(dx),  u_k = in_k - (S_0 - lt) - g k,  tp(dx) = ls(dx) + g (2R - dx index),
-// since dx index = j - k + 2R: u_k is formed once per window position and tp once per kernel row,
-// and each term costs one add, one ex2 and the accumulation.  A warp takes this path when every
+//   t = u_k + tp(dx),  u_k = in_k - (S_0 - lt) - g (k - R),  tp(dx) = ls(dx) - g dx,
+// since dx = j - k + R: u_k is formed once per window position and tp once per kernel row, and
+// each term costs one add, one ex2 and the accumulation.  The tilt is centred on the window: the
+// dominant tap of a sloped input sits near dx = -g / (2 c) (c the tap's curvature), where |tp| ~
+// g^2 / (4 c) stays small, and u_k ~ -tp there, so the FP32 roundings of u_k and tp (the accuracy
+// of the term's exponent) are taken at small magnitudes.  A warp takes this path when every
 // shift of its threads is within DEV_MAX of the thread's line (the result of output j is then
 // T_j + log2 acc_j, accepted within the same window around S_j); otherwise it takes the
 // per-output form above.
@@ -61,6 +64,7 @@ constexpr float SKIP_MARGIN = 64.f;
 constexpr float ACC_LO = -24.f, ACC_HI = 16.f;   // accepted outputs c: S_j + ACC_LO <= c <= S_j + ACC_HI
 constexpr float G_MAX = 32.f;      // largest slope of an affine shift (log2 units per voxel)
 constexpr float DEV_MAX = 8.f;     // largest distance of a shift from its thread's line
+constexpr float LN2F = 0.693147180559945309f;
 
 __device__ __forceinline__ float ex2(float x)
 {
@@ -101,8 +105,48 @@ __device__ __forceinline__ void cp_async4(float *dst, const float *src)
     const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
 }
+__device__ __forceinline__ void cp_async8(float2 *dst, const float2 *src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Halo rows arrive by bulk copies (cp.async.bulk, one per row) that complete on an mbarrier.
+constexpr long STAGE_SPIN_LIMIT = 1L << 22;   // polls of a bounded wait (~0.3 s with the back-off)
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(unsigned long long *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+// Wait for the phase of parity par, at most STAGE_SPIN_LIMIT polls; false if it gave up.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned par)
+{
+    for (long it = 0; it < STAGE_SPIN_LIMIT; ++it) {
+        unsigned ok;
+        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+                     : "=r"(ok)
+                     : "r"(smem_u32(bar)), "r"(par)
+                     : "memory");
+        if (ok) return true;
+        if (it > 16) __nanosleep(64);
+    }
+    return false;
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 __device__ __forceinline__ int wrapi(int v, int n)
 {
@@ -113,27 +157,30 @@ __device__ __forceinline__ int wrapi(int v, int n)
 // Epilogue of one output, c = log2 (K * 2^in)(g, o) given exactly as sh + l (shift sh a
 // double-float, l = log2 of the accumulated sum).  flat indexes the slice-major arrays; the apply
 // epilogues write the caller's [b][y][x][o] in FP64 arithmetic (not on the Sinkhorn loop); the
-// Sinkhorn epilogues stay in FP32 double-floats.
-__device__ __forceinline__ void write_out(const ConvArgs &a, long flat, int b, int o, int y, int x, float2 sh, float l)
+// Sinkhorn epilogues stay in FP32 double-floats.  Returns the hi part of the double-float written
+// to out2 (the Sinkhorn epilogues; -inf for the apply epilogues).
+__device__ __forceinline__ float write_out(const ConvArgs &a, long flat, int b, int o, int y, int x, float2 sh, float l)
 {
     switch (a.epi) {
     case EPI_LOG_OUT:
         a.out64[(((long)b * a.ny + y) * a.nx + x) * a.nt + o] = ((double)sh.x + (double)sh.y + (double)l) * a.out_scale;
-        break;
+        return -INFINITY;
     case EPI_LIN_OUT:
         a.out32[(((long)b * a.ny + y) * a.nx + x) * a.nt + o] = (float)exp2((double)sh.x + (double)sh.y + (double)l);
-        break;
+        return -INFINITY;
     case EPI_W: {
         const float2 c = df_add(sh, make_float2(l, 0.f));
-        a.out2[flat] = df_add(a.aux[flat], df_neg(c));   // w_i = mu_i / K v_i
+        const float2 w = df_add(a.aux[flat], df_neg(c));   // w_i = mu_i / K v_i
+        a.out2[flat] = w;
         a.hint[flat] = c.x + c.y;
-        break;
+        return w.x;
     }
     default: {
         const float2 c = df_add(sh, make_float2(l, 0.f));
-        a.out2[flat] = df_add(a.aux[flat], c);           // d_i = v_i K w_i
+        const float2 d = df_add(a.aux[flat], c);           // d_i = v_i K w_i
+        a.out2[flat] = d;
         a.hint[flat] = c.x + c.y;
-        break;
+        return d.x;
     }
     }
 }
@@ -208,7 +255,7 @@ __global__ void __launch_bounds__(THREADS, 6) conv_tile_kernel(const ConvArgs a0
     float *rowmax = smem + NBUF * SF;      // [HY]
     float *red = rowmax + HY;              // [THREADS / 32]
     float2 *lts = (float2 *)(red + 8);     // [nt] orientation factors lt(o, i)
-    int *need = (int *)(lts + MAX_NT);     // [nt] slice i contributes
+    int *need = (int *)(lts + MAX_NT);     // [MAX_NT] scratch of the launch-order sort
     int *nlist = need + MAX_NT;            // [nt] contributing slices, in order; nlist[MAX_NT]: count
 
     const int nx = a.nx, ny = a.ny, nt = a.nt;
@@ -222,9 +269,45 @@ __global__ void __launch_bounds__(THREADS, 6) conv_tile_kernel(const ConvArgs a0
     const int gy = y0 + yl;
     const long obase = ((long)b * nt + o) * plane + (long)gy * nx + x0 + xl;
 
-    float S[XQ], acc[XQ];
+    // acc: the output's sum over all slices; sacc: over the current slice; racc: over the current
+    // kernel row.  Summing in three levels keeps the FP32 rounding of wide kernels (tens of
+    // thousands of significant terms: ~sqrt(N) 2^-24 relative when added one by one) near
+    // (sqrt(rows) + sqrt(slices) + sqrt(taps per row)) 2^-24.
+    float S[XQ], acc[XQ], sacc[XQ], racc[XQ];
     bool valid[XQ];
     float smin = INFINITY;
+    // Warp 0 loads, one lane per input slice (two chunks for up to 64 orientations), the orientation
+    // factor lt(o, i) and the largest input over the tile's halo of slice i (from the producers'
+    // tile maxima) while every thread loads its shifts: both loads are in flight together.
+    const long ntiles = (long)ntx * nty;
+    float2 lt_c[MAX_NT / 32];
+    float tm_c[MAX_NT / 32];
+    if (warp == 0) {
+#pragma unroll
+        for (int c = 0; c < MAX_NT / 32; ++c) {
+            const int i = lane + 32 * c;
+            lt_c[c] = make_float2(0.f, 0.f);
+            tm_c[c] = INFINITY;
+            if (i >= nt) continue;
+            lt_c[c] = a.ltheta[o * nt + i];
+            if (MAXPASS) continue;
+            const float *tmi = a.tmax + ((long)b * nt + i) * ntiles;
+            float tm;
+            if (a.periodic) {
+                tm = tmi[ty * ntx + tx];
+            } else {
+                tm = -INFINITY;
+#pragma unroll
+                for (int jy = -1; jy <= 1; ++jy)
+#pragma unroll
+                    for (int jx = -1; jx <= 1; ++jx) {
+                        const int ky = ty + jy, kx = tx + jx;
+                        if (ky >= 0 && ky < nty && kx >= 0 && kx < ntx) tm = fmaxf(tm, tmi[ky * ntx + kx]);
+                    }
+            }
+            tm_c[c] = tm;
+        }
+    }
 #pragma unroll
     for (int j = 0; j < XQ; ++j) {
         valid[j] = gy < ny && x0 + xl + j < nx;
@@ -269,75 +352,85 @@ __global__ void __launch_bounds__(THREADS, 6) conv_tile_kernel(const ConvArgs a0
         for (int w = 1; w < THREADS / 32; ++w) smin = fminf(smin, red[w]);
     }
 
-    // which input slices can contribute: one thread per slice, from the tile-max pre-pass
-    const long ntiles = (long)ntx * nty;
-    for (int i = tid; i < nt; i += THREADS) {
-        const float2 lt = a.ltheta[o * nt + i];
-        lts[i] = lt;
-        int nd = 1;
-        if (!MAXPASS) {
-            // largest input over the tile's halo of slice i
-            const float *tmi = a.tmax + ((long)b * nt + i) * ntiles;
-            float tm;
-            if (a.periodic) {
-                tm = tmi[ty * ntx + tx];
-            } else {
-                tm = -INFINITY;
-                for (int jy = ty - 1; jy <= ty + 1; ++jy)
-                    for (int jx = tx - 1; jx <= tx + 1; ++jx)
-                        if (jy >= 0 && jy < nty && jx >= 0 && jx < ntx) tm = fmaxf(tm, tmi[jy * ntx + jx]);
-            }
-            nd = !(lt.x + tm + 1.0f < smin - SKIP_MARGIN);
-        }
-        need[i] = nd;
-    }
-    // cells the copies never write: the taps' padding columns and (zero boundary) the halo cells
-    // outside the grid, in both buffers
+    // Staged halo: row hy of a buffer holds its hi plane [HXP] then its lo plane [HXP] (RP floats),
+    // and the taps of the pair follow the HY rows.  A slice lands as the raw double-floats of the
+    // global layout (a float2 per position, from position x0 - R - PAD: PAD = R & 1 puts every row
+    // copy on a 16-byte boundary; a raw row of HX + 2 positions fits the RP floats) and one warp per
+    // row splits it in place into the two planes, writing 2^-inf outside a zero-boundary grid.
+    constexpr int RP = 2 * HXP, PAD = R & 1;
+    static_assert(HX + 2 * PAD <= HXP, "a raw halo row fits its row of the staging buffer");
+    __shared__ unsigned long long bars[2];
+    // the taps' padding columns, which no copy writes, in both buffers
     for (int idx = tid; idx < D * (TP - D); idx += THREADS) {
         const int dy = idx / (TP - D), dx = D + idx - dy * (TP - D);
 #pragma unroll
-        for (int q = 0; q < NBUF; ++q) smem[q * SF + 2 * HY * HXP + dy * TP + dx] = -INFINITY;
+        for (int q = 0; q < NBUF; ++q) smem[q * SF + HY * RP + dy * TP + dx] = -INFINITY;
     }
-    if (!a.periodic && (x0 < R || y0 < R || x0 + TX + R > nx || y0 + TY + R > ny)) {
-        for (int idx = tid; idx < HY * HX; idx += THREADS) {
-            const int hy = idx / HX, hx = idx - hy * HX;
-            const int sy = y0 - R + hy, sx = x0 - R + hx;
-            if (sy >= 0 && sy < ny && sx >= 0 && sx < nx) continue;
-#pragma unroll
-            for (int q = 0; q < NBUF; ++q) {
-                smem[q * SF + hy * HXP + hx] = -INFINITY;
-                smem[q * SF + HY * HXP + hy * HXP + hx] = 0.f;
-            }
-        }
-    }
-    __syncthreads();
     if (tid == 0) {
-        int c = 0;
-        for (int i = 0; i < nt; ++i)
-            if (need[i]) nlist[c++] = i;
-        nlist[MAX_NT] = c;
+        mbar_init(&bars[0], THREADS / 32);   // one arrival per warp and buffer use
+        mbar_init(&bars[1], THREADS / 32);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // Row copies: whole rows by bulk copies when the grid width is even (every row then starts on
+    // a 16-byte boundary), the input is 16-byte aligned and no row wraps around a periodic grid;
+    // else 8-byte cp.async per position.  Copied positions: [cx0, cx1), even, inside the grid.
+    const int hx_org = x0 - R - PAD;   // global x of raw element 0
+    const int cx0 = max(hx_org, 0), cx1 = min(x0 + TX + R + PAD, nx);
+    const bool bulk = !(nx & 1) && !(reinterpret_cast<uintptr_t>(a.in) & 15) &&
+                      (!a.periodic || (hx_org >= 0 && x0 + TX + R + PAD <= nx));
+    // which input slices can contribute (a pair is skipped when even its largest term is 2^-64 below
+    // the CTA's smallest shift), listed in order by a ballot of warp 0
+    if (warp == 0) {
+        int count = 0;
+#pragma unroll
+        for (int c = 0; c < MAX_NT / 32; ++c) {
+            const int i = lane + 32 * c;
+            const bool nd = i < nt && (MAXPASS || !(lt_c[c].x + tm_c[c] + 1.0f < smin - SKIP_MARGIN));
+            const unsigned m = __ballot_sync(0xffffffffu, nd);
+            if (i < nt) lts[i] = lt_c[c];
+            if (nd) nlist[count + __popc(m & ((1u << lane) - 1u))] = i;
+            count += __popc(m);
+        }
+        if (lane == 0) nlist[MAX_NT] = count;
     }
     __syncthreads();
     const int nn = nlist[MAX_NT];
 
-    // asynchronous copy of slice i and its taps into buffer q: one warp per halo row
+    // asynchronous copy of slice i and its taps into buffer q: row hy by lane (hy - warp) / 4 of
+    // warp hy % 4; every warp arrives once on the buffer's mbarrier with the bytes it copies
     auto stage = [&](int i, int q) {
-        float *bh = smem + q * SF, *bl = bh + HY * HXP, *bt = bl + HY * HXP;
-        const float *src = reinterpret_cast<const float *>(in_b + (long)i * plane);
-        for (int hy = warp; hy < HY; hy += THREADS / 32) {
+        float *buf = smem + q * SF, *bt = buf + HY * RP;
+        const float2 *src = in_b + (long)i * plane;
+        if (bulk) {
+            const int hy = warp + (THREADS / 32) * lane;
             int sy = y0 - R + hy;
             if (a.periodic) sy = wrapi(sy, ny);
-            else if (sy < 0 || sy >= ny) continue;
-            const float *srow = src + 2 * (long)sy * nx;
+            const bool row = hy < HY && sy >= 0 && sy < ny;
+            const unsigned bytes = (unsigned)(cx1 - cx0) * 8u;
+            const unsigned rows = __popc(__ballot_sync(0xffffffffu, row));
+            if (lane == 0) mbar_arrive_tx(&bars[q], rows * bytes);
+            __syncwarp();
+            if (row) {
+                fence_proxy_async();   // this buffer's earlier reads and writes come first
+                bulk_g2s(buf + hy * RP + 2 * (cx0 - hx_org), src + (long)sy * nx + cx0, bytes, &bars[q]);
+            }
+        } else {
+            if (lane == 0) mbar_arrive_tx(&bars[q], 0u);
+            for (int hy = warp; hy < HY; hy += THREADS / 32) {
+                int sy = y0 - R + hy;
+                if (a.periodic) sy = wrapi(sy, ny);
+                else if (sy < 0 || sy >= ny) continue;
+                const float2 *srow = src + (long)sy * nx;
+                float2 *drow = reinterpret_cast<float2 *>(buf + hy * RP);
 #pragma unroll
-            for (int c = 0; c < (HX + 31) / 32; ++c) {
-                const int hx = lane + 32 * c;
-                if (hx >= HX) continue;
-                int sx = x0 - R + hx;
-                if (a.periodic) sx = wrapi(sx, nx);
-                else if (sx < 0 || sx >= nx) continue;
-                cp_async4(bh + hy * HXP + hx, srow + 2 * sx);
-                cp_async4(bl + hy * HXP + hx, srow + 2 * sx + 1);
+                for (int c = 0; c < (HX + 31) / 32; ++c) {
+                    const int e = PAD + lane + 32 * c;   // raw element of halo position e - PAD
+                    if (e >= HX + PAD) continue;
+                    int sx = hx_org + e;
+                    if (a.periodic) sx = wrapi(sx, nx);
+                    else if (sx < 0 || sx >= nx) continue;
+                    cp_async8(drow + e, srow + sx);
+                }
             }
         }
         const float *tsrc = a.ls + ((long)o * nt + i) * D * D;
@@ -347,33 +440,61 @@ __global__ void __launch_bounds__(THREADS, 6) conv_tile_kernel(const ConvArgs a0
         }
         cp_async_commit();
     };
-    if (NBUF == 2 && nn > 0) stage(nlist[0], 0);
+    if (NBUF == 2 && nn > 0) stage(nlist[0], 0);   // (the mbarriers were initialised before the last barrier)
 
     unsigned rows_eval = 0;
+    bool abandon = false;   // a bounded wait gave up: every output goes to the exact recompute
     for (int qi = 0; qi < nn; ++qi) {
         const int i = nlist[qi];
         const float2 lt = lts[i];
-        const float *hhi = smem + (NBUF == 2 ? (qi & 1) * SF : 0), *hlo = hhi + HY * HXP, *ts = hlo + HY * HXP;
+        const int q = NBUF == 2 ? (qi & 1) : 0;
+        float *buf = smem + q * SF;
+        const float *hhi = buf, *ts = buf + HY * RP;
         if (NBUF == 1) {
             __syncthreads();   // nobody reads slice qi - 1 any more
             stage(i, 0);
         }
         cp_async_wait_all();
-        __syncthreads();   // slice qi has landed; nobody reads the other buffer (slice qi - 1) any more
+        const bool landed = mbar_wait(&bars[q], (unsigned)((NBUF == 2 ? qi >> 1 : qi) & 1));
+        // slice qi has landed; nobody reads the other buffer (slice qi - 1) any more
+        if (__syncthreads_or(!landed)) {
+            abandon = true;
+            mbar_wait(&bars[q], (unsigned)((NBUF == 2 ? qi >> 1 : qi) & 1));   // copies still in flight
+            break;
+        }
         if (NBUF == 2 && qi + 1 < nn) stage(nlist[qi + 1], (qi + 1) & 1);
-        if (!MAXPASS) {
-            // row maxima of the staged halo: one warp per row, lanes across the row
-            for (int hy = warp; hy < HY; hy += THREADS / 32) {
-                float m = -INFINITY;
+        // split the raw rows into the hi and lo planes, and their row maxima: one warp per row
+        for (int hy = warp; hy < HY; hy += THREADS / 32) {
+            int sy = y0 - R + hy;
+            if (a.periodic) sy = wrapi(sy, ny);
+            const bool rowin = sy >= 0 && sy < ny;
+            float *row = buf + hy * RP;
+            float2 v[(HX + 31) / 32];
 #pragma unroll
-                for (int c = 0; c < (HX + 31) / 32; ++c)
-                    if (lane + 32 * c < HX) m = fmaxf(m, hhi[hy * HXP + lane + 32 * c]);
+            for (int c = 0; c < (HX + 31) / 32; ++c) {
+                const int hx = lane + 32 * c, sx = x0 - R + hx;
+                v[c] = make_float2(-INFINITY, 0.f);
+                if (hx < HX && rowin && (a.periodic || (sx >= 0 && sx < nx)))
+                    v[c] = reinterpret_cast<const float2 *>(row)[hx + PAD];
+            }
+            __syncwarp();
+            float m = -INFINITY;
+#pragma unroll
+            for (int c = 0; c < (HX + 31) / 32; ++c) {
+                const int hx = lane + 32 * c;
+                if (hx >= HX) continue;
+                row[hx] = v[c].x;
+                row[HXP + hx] = v[c].y;
+                m = fmaxf(m, v[c].x);
+            }
+            if (!MAXPASS) {
 #pragma unroll
                 for (int off = 16; off; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
                 if (lane == 0) rowmax[hy] = m;
             }
-            __syncthreads();
         }
+        fence_proxy_async();   // the planes are written before any later bulk copy into this buffer
+        __syncthreads();
 
         // per-slice shift with the orientation factor folded in: S'_j = S_j - lt as hi + lo
         float Shi[XQ], Slo[XQ], mi[XQ];
@@ -384,7 +505,12 @@ __global__ void __launch_bounds__(THREADS, 6) conv_tile_kernel(const ConvArgs a0
             Slo[j] = e - lt.y;
             mi[j] = -INFINITY;
         }
-    
+        // per-output path: the low parts enter as factors, 2^(in_lo - S'_lo) = 2^in_lo 2^-S'_lo with
+        // 2^x ~ 1 + x ln 2 (|x| < 2^-10: error below 3e-7 relative, far below that of the term's
+        // FP32 exponent); 2^-S'_lo is per output and slice and scales the slice's sum.
+#pragma unroll
+        for (int j = 0; j < XQ; ++j) sacc[j] = 0.f;
+
         for (int dyi = 0; dyi < D; ++dyi) {
             int klo = 0, khi = WIN - 1;
             if (!MAXPASS) {
@@ -408,8 +534,8 @@ __global__ void __launch_bounds__(THREADS, 6) conv_tile_kernel(const ConvArgs a0
                 khi = 2 * R - lo + XQ - 1;
             }
             rows_eval += (unsigned)(min(WIN4 - 1, khi >> 2) - (klo >> 2) + 1);
-            const float *rh = hhi + (yl + 2 * R - dyi) * HXP + xl;
-            const float *rl = hlo + (yl + 2 * R - dyi) * HXP + xl;
+            const float *rh = hhi + (yl + 2 * R - dyi) * RP + xl;
+            const float *rl = rh + HXP;
             // taps of the row, tilted by the affine shift (g = 0: the plain taps, exactly)
             float th[D];
 #pragma unroll
@@ -418,8 +544,10 @@ __global__ void __launch_bounds__(THREADS, 6) conv_tile_kernel(const ConvArgs a0
                 const float tv[4] = {t4.x, t4.y, t4.z, t4.w};
 #pragma unroll
                 for (int c = 0; c < 4; ++c)
-                    if (4 * d4 + c < D) th[4 * d4 + c] = fmaf(g, (float)(2 * R - 4 * d4 - c), tv[c]);
+                    if (4 * d4 + c < D) th[4 * d4 + c] = fmaf(g, (float)(R - 4 * d4 - c), tv[c]);
             }
+#pragma unroll
+            for (int j = 0; j < XQ; ++j) racc[j] = 0.f;
             if (!MAXPASS && fast) {   // uniform over the warp
 #pragma unroll
                 for (int k4 = 0; k4 < WIN4; ++k4) {
@@ -432,18 +560,17 @@ __global__ void __launch_bounds__(THREADS, 6) conv_tile_kernel(const ConvArgs a0
                     for (int kk = 0; kk < 4; ++kk) {
                         const int k = 4 * k4 + kk;
                         if (k >= WIN) continue;
-                        // u_k = in_k - (S_0 - lt) - g k
-                        const float u = fmaf(-(float)k, g, wh4[kk] - Shi[0]) + (wl4[kk] - Slo[0]);
+                        // u_k = in_k - (S_0 - lt) - g (k - R)
+                        const float u = fmaf((float)(R - k), g, wh4[kk] - Shi[0]) + (wl4[kk] - Slo[0]);
 #pragma unroll
                         for (int j = 0; j < XQ; ++j) {
                             const int dxi = j - k + 2 * R;
                             if (dxi < 0 || dxi >= D) continue;
-                            acc[j] += ex2(u + th[dxi]);
+                            racc[j] += ex2(u + th[dxi]);
                         }
                     }
                 }
-                continue;
-            }
+            } else {
 #pragma unroll
             for (int k4 = 0; k4 < WIN4; ++k4) {
                 if (4 * k4 + 3 < klo || 4 * k4 > khi) continue;   // uniform over the CTA
@@ -462,16 +589,21 @@ __global__ void __launch_bounds__(THREADS, 6) conv_tile_kernel(const ConvArgs a0
                         if (MAXPASS) {
                             mi[j] = fmaxf(mi[j], wh4[kk] + th[dxi]);
                         } else {
-                            const float t = ((wh4[kk] - Shi[j]) + th[dxi]) + (wl4[kk] - Slo[j]);
-                            acc[j] += ex2(t);
+                            racc[j] = fmaf(ex2((wh4[kk] - Shi[j]) + th[dxi]), fmaf(wl4[kk], LN2F, 1.f), racc[j]);
                         }
                     }
                 }
             }
+            }
+#pragma unroll
+            for (int j = 0; j < XQ; ++j) sacc[j] += racc[j];
         }
         if (MAXPASS) {
 #pragma unroll
             for (int j = 0; j < XQ; ++j) acc[j] = fmaxf(acc[j], mi[j] + lt.x);
+        } else {
+#pragma unroll
+            for (int j = 0; j < XQ; ++j) acc[j] = fmaf(sacc[j], fast ? 1.f : fmaf(-Slo[j], LN2F, 1.f), acc[j]);
         }
     }
 
@@ -492,15 +624,14 @@ __global__ void __launch_bounds__(THREADS, 6) conv_tile_kernel(const ConvArgs a0
         const float lacc = log2f(acc[j]);
         // the output relative to S_j: lacc on the per-output path, lacc + (T_j - S_j) on the affine one
         const float rel = fast ? lacc + (fmaf((float)j, g, S0) - S[j]) : lacc;
-        if (!(rel >= ACC_LO && rel <= ACC_HI)) {
+        if (abandon || !(rel >= ACC_LO && rel <= ACC_HI)) {
             const unsigned k = atomicAdd(a.redo_count, 1u);
             a.redo_list[k] = make_int2(p, (int)flat);
             omax = INFINITY;          // value unknown until the exact recompute: no skipping on it
             continue;
         }
         const float2 sh = fast ? df_two_sum(S0, g * (float)j) : make_float2(S[j], 0.f);   // g j is exact
-        write_out(a, flat, b, o, gy, x0 + xl + j, sh, lacc);
-        if (a.tmax_out) omax = fmaxf(omax, a.out2[flat].x);
+        omax = fmaxf(omax, write_out(a, flat, b, o, gy, x0 + xl + j, sh, lacc));
     }
     if (!MAXPASS && a.tmax_out) {   // uniform over the CTA
 #pragma unroll
