@@ -80,6 +80,35 @@ SERVE = dict(requests=300, rate=25.0, slots=16, budget=16 << 30, sizes=[(64, 64,
                       "tol 1e-3 on the marginal violation (checked every 20 iterations, cap 2000)")
 
 
+# The literal serving mix: grids 64^2 .. 512^2 with 16 or 32 orientations, 2..8 measures, the batched
+# workload's radii and eps range; run at about 70% of the one-at-a-time capacity and at 200 req/s.
+SERVE_LITERAL = dict(requests=40, rate=200.0, slots=16, budget=96 << 30, nx=[64, 128, 256, 512], nt=[16, 32],
+                     workload="Poisson stream of barycenter requests, n ~ U{2..8} measures, lambda ~ Dirichlet(1), "
+                              "grids N^2 x Ntheta with N in {64, 128, 256, 512} and Ntheta in {16, 32}, "
+                              "r ~ U{7..15}, eps log-uniform [5e-5, 5e-4], coupled inputs (shift <= r/2), tol 1e-3 "
+                              "on the marginal violation (checked every 20 iterations, cap 2000)")
+
+
+def serve_literal_requests(seed=9, count=None):
+    """Seeded literal-mix stream: (unit-rate arrival, nx, ny, nt, r, eps, lambda, mu[n])."""
+    from paper_2402_15322_gb300 import synth
+    rng = synth.SplitMix64(synth.stream_seed(seed, 0, 1 << 23))
+    t = 0.0
+    out = []
+    for k in range(count or SERVE_LITERAL["requests"]):
+        t += -math.log(1.0 - rng.uniform())
+        nx = SERVE_LITERAL["nx"][rng.randint(0, 3)]
+        nt = SERVE_LITERAL["nt"][rng.randint(0, 1)]
+        n = rng.randint(2, 8)
+        r = rng.randint(7, 15)
+        eps = 10 ** rng.uniform(math.log10(5e-5), math.log10(5e-4))
+        g = [-math.log(1.0 - rng.uniform()) for _ in range(n)]
+        lam = [x / sum(g) for x in g]
+        mu = synth.coupled_measures(n, nx, nx, nt, config_seed=seed, problem=k, max_shift=r // 2, nbumps=3)
+        out.append((t, nx, nx, nt, r, eps, lam, mu.astype(np.float32)))
+    return out
+
+
 def serve_requests(seed=6, rate=None, count=None):
     """Seeded request stream: (arrival s, nx, ny, nt, r, eps, lambda, mu[n])."""
     from paper_2402_15322_gb300 import synth
@@ -100,36 +129,28 @@ def serve_requests(seed=6, rate=None, count=None):
     return out
 
 
-def run_serve(args):
-    """Serving latency (p50/p99) and throughput under continuous batching, against serving the
-    same stream one request at a time through se2ot_barycenter."""
+def serve_pass(sv_args, reqs, arrivals, descs, mus, opts):
+    """Submit every request at its arrival time (a producer thread) to one server and wait for all.
+    Latency is counted from the scheduled arrival, so a submit that starts late is charged too."""
     import threading
 
     import torch
 
-    from paper_2402_15322_gb300 import build, se2ot
-    build.build()
-    torch.cuda.set_device(0)
-    rate = args.rate or SERVE["rate"]
-    count = args.requests or SERVE["requests"]
-    reqs = serve_requests(rate=rate, count=count)
-    opts = se2ot.solve_opts(2000, 20, 1e-3)
-    descs = [se2ot.make_desc(nx, ny, nt, r, W, eps) for (_, nx, ny, nt, r, eps, _, _) in reqs]
-    mus = [torch.from_numpy(q[7]) for q in reqs]
-    # warm-up: one request of each size
-    sv = se2ot.Server(SERVE["budget"], SERVE["slots"])
-    for k in range(min(4, len(reqs))):
-        out = torch.empty(mus[k].shape[1:], dtype=torch.float32)
-        sv.wait(sv.submit(descs[k], mus[k], reqs[k][6], opts), out)
-    tickets = [None] * len(reqs)
+    from paper_2402_15322_gb300 import se2ot
+    sv = se2ot.Server(*sv_args)
+    for k in range(min(2, len(reqs))):   # warm-up on the smallest requests
+        j = sorted(range(len(reqs)), key=lambda q: reqs[q][1] * reqs[q][3])[k]
+        sv.wait(sv.submit(descs[j], mus[j], reqs[j][6], opts), torch.empty(mus[j].shape[1:], dtype=torch.float32))
+    tickets, late = [None] * len(reqs), [0.0] * len(reqs)
     t0 = time.perf_counter()
 
     def producer():
-        for k, q in enumerate(reqs):
-            delay = q[0] - (time.perf_counter() - t0)
+        for k in range(len(reqs)):
+            delay = arrivals[k] - (time.perf_counter() - t0)
             if delay > 0:
                 time.sleep(delay)
-            tickets[k] = sv.submit(descs[k], mus[k], q[6], opts)
+            late[k] = max(0.0, time.perf_counter() - t0 - arrivals[k])
+            tickets[k] = sv.submit(descs[k], mus[k], reqs[k][6], opts)
 
     th = threading.Thread(target=producer)
     th.start()
@@ -138,14 +159,21 @@ def run_serve(args):
     for k, q in enumerate(reqs):
         out = torch.empty(mus[k].shape[1:], dtype=torch.float32)
         st, status = sv.wait(tickets[k], out)
-        lat.append(st["ms"])
+        lat.append(st["ms"] + late[k] * 1e3)
         vox_it += q[1] * q[2] * q[3] * st["iters"]
         statuses.append(status)
     wall = time.perf_counter() - t0
     sv.close()
-    # one at a time (FP32 single-solve path), same stream, same options: latency by a virtual clock
-    clock, slat, svox = 0.0, [], 0
-    kernels = {}
+    return lat, vox_it, wall, statuses
+
+
+def sequential_service(reqs, descs, mus, opts):
+    """One request at a time through se2ot_barycenter (FP32 single-solve path): service seconds and
+    voxel-iterations of each request."""
+    import torch
+
+    from paper_2402_15322_gb300 import se2ot
+    kernels, service, voxit = {}, [], []
     for k, q in enumerate(reqs):
         key = (q[1], q[2], q[3], q[4], q[5])
         if key not in kernels:
@@ -154,20 +182,80 @@ def run_serve(args):
         torch.cuda.synchronize()
         s0 = time.perf_counter()
         _, st, _ = se2ot.se2ot_barycenter(kernels[key], mu_d, q[6], opts, raise_on_error=False)
-        dt = time.perf_counter() - s0
-        clock = max(clock, q[0]) + dt
-        slat.append((clock - q[0]) * 1e3)
-        svox += q[1] * q[2] * q[3] * st["iters"]
+        service.append(time.perf_counter() - s0)
+        voxit.append(q[1] * q[2] * q[3] * st["iters"])
+        del mu_d
     for kern in kernels.values():
         kern.close()
+    return service, voxit
+
+
+def virtual_clock(arrivals, service):
+    """Latencies (ms) and makespan of serving one request at a time in arrival order."""
+    clock, lat = 0.0, []
+    for a, d in zip(arrivals, service):
+        clock = max(clock, a) + d
+        lat.append((clock - a) * 1e3)
+    return lat, clock
+
+
+def run_serve(args):
+    """Serving latency (p50/p99) and throughput under continuous batching, against serving the
+    same stream one request at a time through se2ot_barycenter."""
+    import torch
+
+    from paper_2402_15322_gb300 import build, se2ot
+    build.build()
+    torch.cuda.set_device(0)
     p = lambda a, f: float(np.percentile(np.asarray(a), f))
+    opts = se2ot.solve_opts(2000, 20, 1e-3)
+    if args.mix == "literal":
+        count = args.requests or SERVE_LITERAL["requests"]
+        reqs = serve_literal_requests(count=count)
+        descs = [se2ot.make_desc(nx, ny, nt, r, W, eps) for (_, nx, ny, nt, r, eps, _, _) in reqs]
+        mus = [torch.from_numpy(q[7]) for q in reqs]
+        service, voxit = sequential_service(reqs, descs, mus, opts)
+        unit = [q[0] for q in reqs]
+        rate70 = 0.7 / (sum(service) / len(service))
+        lines = {}
+        for tag, rate in (("load_70pct", rate70), ("overload_200_per_s", args.rate or SERVE_LITERAL["rate"])):
+            arrivals = [u / rate for u in unit]
+            lat, vox_it, wall, statuses = serve_pass((SERVE_LITERAL["budget"], SERVE_LITERAL["slots"]), reqs,
+                                                     arrivals, descs, mus, opts)
+            slat, clock = virtual_clock(arrivals, service)
+            lines[tag] = {"rate_per_s": rate, "offered_load": rate * sum(service) / len(service),
+                          "serve": {"p50_ms": p(lat, 50), "p99_ms": p(lat, 99), "voxel_iters_per_s": vox_it / wall,
+                                    "wall_s": wall, "ok": statuses.count(0), "not_converged": statuses.count(5)},
+                          "one_at_a_time": {"p50_ms": p(slat, 50), "p99_ms": p(slat, 99),
+                                            "voxel_iters_per_s": sum(voxit) / clock, "wall_s": clock}}
+        sizes = {}
+        for q in reqs:
+            key = "%dx%dx%d" % (q[1], q[2], q[3])
+            sizes[key] = sizes.get(key, 0) + 1
+        main = lines["load_70pct"]
+        return {"metric": "SE(2) serving latency p50/p99 ms", "value": main["serve"]["p50_ms"], "unit": "ms",
+                "n_gpus": 1, "steps": 1, "warmup": 2, "higher_is_better": False, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": SERVE_LITERAL["workload"], "requests": count, "slots": SERVE_LITERAL["slots"],
+                           "budget_bytes": SERVE_LITERAL["budget"], "sizes_drawn": sizes,
+                           "one_at_a_time_service_s": {"mean": sum(service) / len(service), "max": max(service)}},
+                **lines}
+    rate = args.rate or SERVE["rate"]
+    count = args.requests or SERVE["requests"]
+    reqs = serve_requests(rate=rate, count=count)
+    descs = [se2ot.make_desc(nx, ny, nt, r, W, eps) for (_, nx, ny, nt, r, eps, _, _) in reqs]
+    mus = [torch.from_numpy(q[7]) for q in reqs]
+    arrivals = [q[0] for q in reqs]
+    lat, vox_it, wall, statuses = serve_pass((SERVE["budget"], SERVE["slots"]), reqs, arrivals, descs, mus, opts)
+    service, voxit = sequential_service(reqs, descs, mus, opts)
+    slat, clock = virtual_clock(arrivals, service)
     return {"metric": "SE(2) serving latency p50/p99 ms", "value": p(lat, 50), "unit": "ms", "n_gpus": 1,
-            "steps": 1, "warmup": 4, "higher_is_better": False, "dtype": "f32", "data": "synthetic",
+            "steps": 1, "warmup": 2, "higher_is_better": False, "dtype": "f32", "data": "synthetic",
             "config": {"workload": SERVE["workload"], "rate_per_s": rate, "requests": count, "slots": SERVE["slots"],
-                       "budget_bytes": SERVE["budget"]},
+                       "budget_bytes": SERVE["budget"],
+                       "offered_load": rate * sum(service) / len(service)},
             "serve": {"p50_ms": p(lat, 50), "p99_ms": p(lat, 99), "voxel_iters_per_s": vox_it / wall,
                       "wall_s": wall, "ok": statuses.count(0), "not_converged": statuses.count(5)},
-            "one_at_a_time": {"p50_ms": p(slat, 50), "p99_ms": p(slat, 99), "voxel_iters_per_s": svox / clock,
+            "one_at_a_time": {"p50_ms": p(slat, 50), "p99_ms": p(slat, 99), "voxel_iters_per_s": sum(voxit) / clock,
                               "wall_s": clock}}
 
 
@@ -635,6 +723,8 @@ def main(argv=None):
                     help="Sinkhorn iterations per solve (profiling runs only; default: the workload's)")
     ap.add_argument("--rate", type=float, default=0.0, help="serve: Poisson arrival rate (req/s)")
     ap.add_argument("--requests", type=int, default=0, help="serve: number of requests")
+    ap.add_argument("--mix", default="served", choices=["served", "literal"],
+                    help="serve: the 64^2/128^2 mix (default) or the literal 64^2..512^2 x 16/32 mix")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"],
                     help="bf16: the convolutions on the tcgen05 tensor cores (SE2OT_BF16TC)")
     ap.add_argument("--refine", type=int, default=20, help="bf16: last iterations on the FP32 path")

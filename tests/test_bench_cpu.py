@@ -91,3 +91,26 @@ def test_reference_arm_prints_the_contract_keys():
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"] and cb["sample"]
     assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
+
+
+def test_literal_serving_mix_draws_the_stated_ranges(monkeypatch):
+    """The literal serving stream: sizes from {64, 128, 256, 512}^2 x {16, 32}, n in 2..8, r in 7..15,
+    eps in [5e-5, 5e-4], Dirichlet weights, equal-mass coupled measures, increasing arrivals."""
+    from paper_2402_15322_gb300 import synth
+    # the stream's parameters only: skip building the measures themselves (seconds at 512^2)
+    monkeypatch.setattr(synth, "coupled_measures",
+                        lambda n, nx, ny, nt, **kw: np.full((n, ny, nx, nt), 1.0 / (nx * ny * nt)))
+    reqs = bench.serve_literal_requests(count=64)
+    t = [q[0] for q in reqs]
+    assert all(b > a for a, b in zip(t, t[1:]))
+    for (_, nx, ny, nt, r, eps, lam, mu) in reqs:
+        assert nx == ny and nx in (64, 128, 256, 512) and nt in (16, 32)
+        assert 7 <= r <= 15 and 5e-5 <= eps <= 5e-4
+        assert 2 <= len(lam) <= 8 and abs(sum(lam) - 1.0) < 1e-12 and min(lam) > 0
+        assert mu.shape == (len(lam), ny, nx, nt)
+    assert {q[1] for q in reqs} == {64, 128, 256, 512} and {q[3] for q in reqs} == {16, 32}
+
+
+def test_virtual_clock_serves_in_arrival_order():
+    lat, clock = bench.virtual_clock([0.0, 0.5, 0.6, 5.0], [1.0, 1.0, 0.5, 0.25])
+    assert np.allclose(lat, [1000.0, 1500.0, 1900.0, 250.0]) and clock == 5.25

@@ -8,6 +8,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 from paper_2402_15322_gb300 import build, se2ot, synth
 
 pytestmark = pytest.mark.gpu
@@ -70,6 +71,38 @@ def test_mix_equals_alone_and_single_solves():
         if o.tol_viol > 0:
             assert mixed[k][1]["viol"] <= o.tol_viol
         kern.close()
+
+
+# A sample of the literal serving mix (grids up to 512^2, 32 orientations, the radii and eps range
+# of the batched workload), served together; 20 iterations each so that the oracle can run the
+# small ones in full.  nx, nt, r, eps, n
+LITERAL_SAMPLE = [(64, 16, 7, 3.2e-4, 3), (64, 32, 7, 5e-5, 2), (256, 32, 15, 1.1e-4, 2), (512, 16, 8, 2.4e-4, 2),
+                  (128, 32, 11, 7e-5, 4)]
+
+
+def test_literal_mix_sample_matches_oracle_and_single_solves():
+    """Served together, each request of the sample equals its single solve bit for bit, and the two
+    smallest match the FP64 oracle's barycenter within 1e-5 rel L1 (Appendix A)."""
+    reqs = []
+    for k, (nx, nt, r, eps, n) in enumerate(LITERAL_SAMPLE):
+        mu = synth.coupled_measures(n, nx, nx, nt, config_seed=70 + k, max_shift=r // 2, nbumps=3).astype(np.float32)
+        lam = np.linspace(1.0, 3.0, n)
+        reqs.append((se2ot.make_desc(nx, nx, nt, r, W, eps), torch.from_numpy(mu), (lam / lam.sum()).tolist(),
+                     se2ot.solve_opts(20)))
+    mixed = serve(reqs, budget=32 << 30, slots=8)
+    for k, (d, mu, lam, o) in enumerate(reqs):
+        assert mixed[k][2] == se2ot.SE2OT_OK
+        kern = se2ot.se2ot_kernel_build(d)
+        single, _, status = se2ot.se2ot_barycenter(kern, mu.cuda(), lam, o)
+        assert status == se2ot.SE2OT_OK
+        assert torch.equal(single.cpu(), mixed[k][0]), k
+        kern.close()
+    for k in (0, 1):
+        nx, nt, r, eps, n = LITERAL_SAMPLE[k]
+        d, mu, lam, _ = reqs[k]
+        want = oracle.barycenter_log(oracle.Grid(nx, nx, nt, r, W, eps), mu.numpy().astype(np.float64), lam, 20)
+        got = mixed[k][0].numpy().astype(np.float64)
+        assert np.abs(got - want).sum() / np.abs(want).sum() <= 1e-5, k
 
 
 def test_budget_admits_as_memory_frees_up():
