@@ -173,6 +173,7 @@ __global__ void order_init_kernel(unsigned *order, unsigned *cost, long n)
 
 cudaError_t launch_order_init(unsigned *order, unsigned *cost, unsigned *done, long count, cudaStream_t s)
 {
+    if (!order) return cudaSuccess;   // launches too large for a launch order keep none
     if (count > 0) order_init_kernel<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(order, cost, count);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? cudaMemsetAsync(done, 0, sizeof(unsigned), s) : e;

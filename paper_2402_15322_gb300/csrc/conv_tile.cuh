@@ -10,10 +10,10 @@
 // contribute (see skipping), the CTA stages slice i of the input halo ((TY + 2R) x (TX + 2R)
 // double-floats, split into an FP32 hi and a lo plane) and the (2R+1)^2 spatial taps of the pair
 // in shared memory, then each thread walks the rows of the window; the (2R+1)-tap row is fully
-// unrolled (R is a template parameter).  Staging is asynchronous (cp.async) and, where shared
-// memory allows (stage_buffers), double-buffered: the next contributing slice is copied while the
-// current one is summed.  Halo cells outside the grid (zero boundary) are set to 2^-inf once per
-// CTA; the copies only write cells inside it.
+// unrolled (R is a template parameter).  Staging is asynchronous (a bulk copy per halo row, see
+// stage() below) and, where shared memory allows (stage_buffers), double-buffered: the next
+// contributing slice is copied while the current one is summed.  The split of the raw rows into the
+// two planes writes 2^-inf over the halo cells outside a zero-boundary grid.
 //
 // Shift and precision: output j of a thread is evaluated as
 //   S_j + log2 sum 2^t,  t = ((in_hi - S'_j,hi) + ls) + (in_lo - S'_j,lo),   S'_j = S_j - lt(o, i)

@@ -216,8 +216,17 @@ void worker_main(se2ot_server_s *sv)
         bool progressed = !to_admit.empty();
         for (size_t k = 0; k < sv->active.size();) {
             ReqPtr r = sv->active[k];
-            if (r->in_flight && cudaEventQuery(r->ev) == cudaSuccess) {
+            const cudaError_t q = r->in_flight ? cudaEventQuery(r->ev) : cudaErrorNotReady;
+            if (q == cudaSuccess) {
                 step(sv, r);
+                progressed = true;
+            } else if (r->in_flight && q != cudaErrorNotReady) {
+                // a device error (the context is then unusable): the request fails instead of
+                // being polled for ever
+                cudaGetLastError();
+                r->in_flight = false;
+                release(sv, r);
+                complete(sv, r, SE2OT_ECUDA);
                 progressed = true;
             } else if (r->in_flight) {
                 cudaGetLastError();   // cudaErrorNotReady is not an error here
