@@ -621,6 +621,11 @@ def run_gpu(args):
         elif args.config == "batched":
             result["e2e"] = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
                              "note": "device-resident batch (the batched entry point takes device buffers)"}
+            form, ms_per, ms_one = se2ot.se2ot_batch_tuning()
+            result["launch_form"] = {"chosen": {1: "per radius", 2: "one launch"}.get(form, "none"),
+                                     "ms_per_iteration": {"per_radius": ms_per, "one_launch": ms_one},
+                                     "note": "timed by the library on the first call (a few iterations of each "
+                                             "form from the initial state); the faster form is kept"}
         else:
             result["e2e"] = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(n * vox * 4),
                              "d2h_bytes_per_step": int(vox * 4)}

@@ -109,6 +109,10 @@ typedef struct {
 } se2ot_solve_opts;
 
 #define SE2OT_FLAG_TIME_CONV 1   /* time every convolution launch with CUDA events (stats.conv_ms) */
+/* se2ot_interpolate_batched only: the form of the convolution launches (see there); neither flag:
+ * the form is chosen by timing both on the first call with a given set of descriptors. */
+#define SE2OT_FLAG_BATCH_ONE_LAUNCH 2    /* one launch per convolution line, every radius in it */
+#define SE2OT_FLAG_BATCH_PER_RADIUS 4    /* one launch per radius class and convolution line */
 
 /* Results of a solve (written after the call's internal synchronisation).
  *   iters            iterations performed
@@ -293,16 +297,29 @@ SE2OT_API se2ot_status se2ot_interpolate_signed(se2ot_kernel k, const float *U0,
  * naming the problem otherwise), out[p]: V_p floats, device.  opts: max_iters >= 1, tol_viol must be 0 (no early stop in a batch), NULL =
  * 100 iterations.  stats: NULL or an array of nprob entries (ms and kernel_launches are for the
  * whole batch).
- * One iteration of the batch is one convolution launch per distinct radius for each of the two
- * convolution lines (a work list over all tiles of all problems with that radius), one exact
- * recompute pass per line and one update launch, recorded once as a CUDA graph and replayed.
- * Each problem's result is bit-identical to se2ot_interpolate on that problem alone.  The
- * workspace and the graph are kept for the next call with the same descriptors; calls are
- * serialised by a library-wide lock.  Synchronises `stream` before returning. */
+ * One iteration of the batch is, for each of the two convolution lines, the convolution of every
+ * tile of every problem and one exact recompute pass, then one update launch, recorded once as a
+ * CUDA graph and replayed.  The convolution of a line takes one of two forms:
+ *   per radius:  one launch per distinct radius (a work list over that radius's tiles);
+ *   one launch:  a single launch over every tile, the largest radius first, each tile running the
+ *                code specialised for its problem's radius.
+ * opts->flags may force one (SE2OT_FLAG_BATCH_PER_RADIUS, SE2OT_FLAG_BATCH_ONE_LAUNCH; both:
+ * EINVAL); otherwise the first call with a set of descriptors times a few iterations of each
+ * (se2ot_batch_tuning reports them), keeps the faster for the calls that follow, and starts the
+ * iteration again from the inputs.  Each tile runs the same code in either form, so each problem's
+ * result is bit-identical to se2ot_interpolate on that problem alone.  The workspace, the graphs
+ * and the choice are kept for the next call with the same descriptors; calls are serialised by a
+ * library-wide lock.  Synchronises `stream` before returning. */
 SE2OT_API se2ot_status se2ot_interpolate_batched(int nprob, const se2ot_kernel_desc *descs, const float *const *mu0,
                                                  const float *const *mu1, const double *t,
                                                  const se2ot_solve_opts *opts, float *const *out,
                                                  se2ot_stats *stats, void *stream);
+
+/* The launch form of the last tuned batch (the paper has no counterpart: a property of this
+ * library's batched launches).  form: 1 per radius, 2 one launch, 0 no batch tuned yet (or every
+ * call so far forced a form); ms_per_radius, ms_one_launch: the measured milliseconds per batch
+ * iteration of each form (0 if not measured).  Host pointers; EINVAL if one is NULL. */
+SE2OT_API se2ot_status se2ot_batch_tuning(int *form, double *ms_per_radius, double *ms_one_launch);
 
 /* Serving: a request loop for barycenter solves with continuous batching (no counterpart in the
  * paper; the solve of every request is se2ot_barycenter's).  A server owns one worker thread on

@@ -16,7 +16,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libse2ot.so")
 SOURCES = ["taps.cu", "conv.cu", "conv_r_a.cu", "conv_r_b.cu", "conv_r_c.cu", "elementwise.cu", "state.cu", "solver.cu", "batch.cu",
-           "server.cu", "noalloc.cu", "lift.cu", "peaks.cu", "conv_tc.cu"]
+           "server.cu", "noalloc.cu", "lift.cu", "peaks.cu", "conv_tc.cu", "conv_multi.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr", "-I" + INCLUDE, "-I" + CSRC]

@@ -2,10 +2,15 @@
 // operator: barycenters of 2 measures with weights (1 - t, t)) of uneven grid sizes, radii and
 // regularisations, iterated in lockstep.
 //
-// One Sinkhorn iteration of the whole batch is: for every radius class, one convolution launch
-// over a work list that covers all tiles of all problems of that radius (w-line), one exact
-// recompute pass shared by all problems, the same for the d-line, and one update launch over the
-// tiles of all problems.  That sequence is captured once as a CUDA graph and replayed.
+// One Sinkhorn iteration of the whole batch is: the w-line convolution of every tile of every
+// problem, one exact recompute pass shared by all problems, the same for the d-line, and one update
+// launch over the tiles of all problems.  That sequence is captured once as a CUDA graph and
+// replayed.  The convolution of a line is issued in one of two forms:
+//   per radius:  one launch per radius class present (the per-radius kernels of conv_r_*.cu);
+//   one launch:  a single launch over all work items, heaviest radius first, each item running
+//                the body of its radius (conv_multi.cu).
+// The form is chosen on the first solve with a given set of descriptors by timing a few iterations
+// of both graphs (the state is then initialised again), unless the caller forces one.
 //
 // Every problem is computed by exactly the same tile code as a single solve, so each result is
 // bit-identical to se2ot_interpolate on that problem alone.
@@ -118,6 +123,8 @@ struct BatchCtx {
     ConvArgs *dW = nullptr, *dD = nullptr;      // per-problem conv arguments (device)
     UpdArgs *dU = nullptr;
     int4 *items = nullptr, *uitems = nullptr;
+    int4 *items_one = nullptr;                                   // every item, largest radius first
+    int nitems = 0;
     std::vector<std::pair<int, std::pair<int, int>>> classes;   // radius -> (offset, count) in items
     std::vector<UpdArgs> hU;                                     // host copy of dU
     int nuitems = 0;
@@ -125,20 +132,27 @@ struct BatchCtx {
     unsigned *count = nullptr;
     unsigned long long *totals = nullptr;
     cudaStream_t cs = nullptr;
-    cudaGraphExec_t graph = nullptr;
-    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaGraphExec_t graph = nullptr;       // per-radius launches
+    cudaGraphExec_t graph_one = nullptr;   // one launch per convolution line
+    long long launches_one = 0;
+    int form = 0;                          // chosen form: 1 per radius, 2 one launch, 0 not yet tuned
+    double tune_ms[2] = {0.0, 0.0};        // measured ms per iteration of each form (0: not measured)
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_t0 = nullptr, ev_t1 = nullptr;   // t0/t1: tuning
     int sms = 152;
     long long launches_per_iter = 0;
 
     void release()
     {
         if (graph) cudaGraphExecDestroy(graph);
-        for (void *p : {(void *)arena, (void *)dW, (void *)dD, (void *)dU, (void *)items, (void *)uitems,
+        if (graph_one) cudaGraphExecDestroy(graph_one);
+        for (void *p : {(void *)arena, (void *)dW, (void *)dD, (void *)dU, (void *)items, (void *)uitems, (void *)items_one,
                         (void *)redo, (void *)count, (void *)totals})
             if (p) cudaFree(p);
         if (cs) cudaStreamDestroy(cs);
         if (ev_in) cudaEventDestroy(ev_in);
         if (ev_out) cudaEventDestroy(ev_out);
+        if (ev_t0) cudaEventDestroy(ev_t0);
+        if (ev_t1) cudaEventDestroy(ev_t1);
         *this = BatchCtx();
     }
 };
@@ -223,6 +237,8 @@ se2ot_status setup(BatchCtx &B, int nprob, const se2ot_kernel_desc *descs)
     BCK(cudaStreamCreateWithFlags(&B.cs, cudaStreamNonBlocking), "cudaStreamCreate");
     BCK(cudaEventCreateWithFlags(&B.ev_in, cudaEventDisableTiming), "cudaEventCreate");
     BCK(cudaEventCreateWithFlags(&B.ev_out, cudaEventDisableTiming), "cudaEventCreate");
+    BCK(cudaEventCreate(&B.ev_t0), "cudaEventCreate");
+    BCK(cudaEventCreate(&B.ev_t1), "cudaEventCreate");
 
     // taps
     for (int p = 0; p < nprob; ++p) BCK(build_taps(B.probs[p].d, B.probs[p].taps, B.cs), "tap build");
@@ -287,6 +303,15 @@ se2ot_status setup(BatchCtx &B, int nprob, const se2ot_kernel_desc *descs)
         items.insert(items.end(), kv.second.begin(), kv.second.end());
     }
     B.nuitems = (int)uitems.size();
+    B.nitems = (int)items.size();
+    // the one-launch work list: the classes from the largest radius down (the heaviest items first)
+    std::vector<int4> items_one;
+    for (auto it = B.classes.rbegin(); it != B.classes.rend(); ++it)
+        items_one.insert(items_one.end(), items.begin() + it->second.first,
+                         items.begin() + it->second.first + it->second.second);
+    BCK(cudaMalloc((void **)&B.items_one, sizeof(int4) * items_one.size()), "cudaMalloc");
+    BCK(cudaMemcpyAsync(B.items_one, items_one.data(), sizeof(int4) * items_one.size(), cudaMemcpyHostToDevice,
+                        B.cs), "cudaMemcpy");
     BCK(cudaMalloc((void **)&B.dW, sizeof(ConvArgs) * nprob), "cudaMalloc");
     BCK(cudaMalloc((void **)&B.dD, sizeof(ConvArgs) * nprob), "cudaMalloc");
     BCK(cudaMalloc((void **)&B.dU, sizeof(UpdArgs) * nprob), "cudaMalloc");
@@ -302,37 +327,53 @@ se2ot_status setup(BatchCtx &B, int nprob, const se2ot_kernel_desc *descs)
     BCK(cudaStreamSynchronize(B.cs), "cudaStreamSynchronize");
 
     B.hU = hU;
-    // record one Sinkhorn iteration of the whole batch as a graph (kernel attributes are set
-    // before the capture: a zero-item launch only configures the kernel)
+    // record one Sinkhorn iteration of the whole batch as a graph, in either form (kernel attributes
+    // are set before the capture: a zero-item launch only configures the kernel)
     ConvArgs shared = hW[0];
-    // the recompute pass of the w-line is followed by the first class's convolution of the d-line
-    shared.release_early = pdl_release_early(B.classes.empty() ? 0 : B.classes[0].second.second, B.sms);
     for (auto &c : B.classes) BCK(launch_conv_batch(c.first, shared, B.dW, B.items, 0, B.cs), "conv attributes");
-    cudaGraph_t g = nullptr;
-    BCK(cudaStreamBeginCapture(B.cs, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
-    long long launches = 0;
-    cudaError_t e = cudaSuccess;
-    for (int line = 0; line < 2 && e == cudaSuccess; ++line) {
-        const ConvArgs *probs = line == 0 ? B.dW : B.dD;
-        e = cudaMemsetAsync(B.count, 0, sizeof(unsigned), B.cs);
-        for (auto &c : B.classes)
-            if (e == cudaSuccess) {
-                e = launch_conv_batch(c.first, shared, probs, B.items + c.second.first, c.second.second, B.cs);
+    BCK(launch_conv_multi(shared, B.dW, B.items_one, 0, B.cs), "conv attributes");
+    auto record = [&](bool one, cudaGraphExec_t *exec, long long *count) -> cudaError_t {
+        // the recompute pass of the w-line is followed by the d-line's first convolution launch
+        ConvArgs sh = shared;
+        sh.release_early = pdl_release_early(
+            one ? B.nitems : (B.classes.empty() ? 0 : B.classes[0].second.second), B.sms);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(B.cs, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return e;
+        long long launches = 0;
+        for (int line = 0; line < 2 && e == cudaSuccess; ++line) {
+            const ConvArgs *probs = line == 0 ? B.dW : B.dD;
+            e = cudaMemsetAsync(B.count, 0, sizeof(unsigned), B.cs);
+            if (one) {
+                if (e == cudaSuccess) e = launch_conv_multi(sh, probs, B.items_one, B.nitems, B.cs);
                 ++launches;
+            } else {
+                for (auto &c : B.classes)
+                    if (e == cudaSuccess) {
+                        e = launch_conv_batch(c.first, sh, probs, B.items + c.second.first, c.second.second, B.cs);
+                        ++launches;
+                    }
             }
-        if (e == cudaSuccess) e = launch_redo_batch(shared, probs, 2 * B.sms, B.cs);
-        ++launches;
-    }
-    if (e == cudaSuccess) {
-        PdlLaunch L(dim3(B.nuitems), dim3(256), 0, B.cs);
-        e = cudaLaunchKernelEx(&L.cfg, batch_update_kernel, (const UpdArgs *)B.dU, (const int4 *)B.uitems);
-        ++launches;
-    }
-    cudaError_t e2 = cudaStreamEndCapture(B.cs, &g);
-    if (e == cudaSuccess) e = e2;
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&B.graph, g, 0);
-    if (g) cudaGraphDestroy(g);
-    BCK(e, "batch iteration graph");
+            if (e == cudaSuccess) e = launch_redo_batch(sh, probs, 2 * B.sms, B.cs);
+            ++launches;
+        }
+        if (e == cudaSuccess) {
+            PdlLaunch L(dim3(B.nuitems), dim3(256), 0, B.cs);
+            e = cudaLaunchKernelEx(&L.cfg, batch_update_kernel, (const UpdArgs *)B.dU, (const int4 *)B.uitems);
+            ++launches;
+        }
+        cudaError_t e2 = cudaStreamEndCapture(B.cs, &g);
+        if (e == cudaSuccess) e = e2;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(exec, g, 0);
+        if (g) cudaGraphDestroy(g);
+        *count = launches;
+        return e;
+    };
+    long long launches = 0;
+    BCK(record(false, &B.graph, &launches), "batch iteration graph (per radius)");
+    BCK(record(true, &B.graph_one, &B.launches_one), "batch iteration graph (one launch)");
+    B.form = 0;
+    B.tune_ms[0] = B.tune_ms[1] = 0.0;
     B.launches_per_iter = launches;
     return SE2OT_OK;
 }
@@ -351,6 +392,10 @@ extern "C" se2ot_status se2ot_interpolate_batched(int nprob, const se2ot_kernel_
     }
     se2ot_solve_opts o = {100, 0, 0.0, SE2OT_FP32, 0};
     if (opts) o = *opts;
+    if ((o.flags & SE2OT_FLAG_BATCH_ONE_LAUNCH) && (o.flags & SE2OT_FLAG_BATCH_PER_RADIUS)) {
+        set_last_error("SE2OT_FLAG_BATCH_ONE_LAUNCH and SE2OT_FLAG_BATCH_PER_RADIUS exclude each other");
+        return SE2OT_EINVAL;
+    }
     if (o.max_iters < 1 || o.precision != SE2OT_FP32 || o.tol_viol != 0.0) {
         set_last_error("batched solves run a fixed number (>= 1) of FP32 iterations (tol_viol must be 0)");
         return SE2OT_EINVAL;
@@ -386,19 +431,26 @@ extern "C" se2ot_status se2ot_interpolate_batched(int nprob, const se2ot_kernel_
     // inputs, weights, first shifts
     std::vector<UpdArgs> &hU = B.hU;
     long long launches = 0;
+    auto init_state = [&]() -> cudaError_t {   // the iteration's starting state of every problem
+        for (int p = 0; p < nprob; ++p) {
+            Prob &q = B.probs[p];
+            cudaError_t e = launch_init(q.mu, q.lmu, q.lv, q.h1, q.h2, 2, q.d.nx, q.d.ny, q.d.ntheta, B.cs);
+            if (e == cudaSuccess)
+                e = cudaMemsetAsync(q.tmax, 0, sizeof(float) * 2 * q.d.ntheta * q.tiles, B.cs);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaMemsetAsync(B.totals, 0, 2 * sizeof(unsigned long long), B.cs);
+    };
     for (int p = 0; p < nprob; ++p) {
         Prob &q = B.probs[p];
         BCK(cudaMemcpyAsync(q.mu, mu0[p], q.V * sizeof(float), cudaMemcpyDeviceToDevice, B.cs), "cudaMemcpy(mu0)");
         BCK(cudaMemcpyAsync(q.mu + q.V, mu1[p], q.V * sizeof(float), cudaMemcpyDeviceToDevice, B.cs),
             "cudaMemcpy(mu1)");
-        BCK(launch_init(q.mu, q.lmu, q.lv, q.h1, q.h2, 2, q.d.nx, q.d.ny, q.d.ntheta, B.cs), "init");
-        BCK(cudaMemsetAsync(q.tmax, 0, sizeof(float) * 2 * q.d.ntheta * q.tiles, B.cs), "cudaMemset(tmax)");
         const double lam[2] = {1.0 - t[p], t[p]};
         for (int i = 0; i < 2; ++i) {
             const float hi = (float)lam[i];
             hU[p].lam[i] = make_float2(hi, (float)(lam[i] - (double)hi));
         }
-        ++launches;
     }
     // the inputs of every problem are measures of equal mass (Appendix A): checked on the device
     // before any iteration is enqueued
@@ -418,9 +470,31 @@ extern "C" se2ot_status se2ot_interpolate_batched(int nprob, const se2ot_kernel_
     }
     launches += 2LL * nprob;
     BCK(cudaMemcpyAsync(B.dU, hU.data(), sizeof(UpdArgs) * nprob, cudaMemcpyHostToDevice, B.cs), "cudaMemcpy");
-    BCK(cudaMemsetAsync(B.totals, 0, 2 * sizeof(unsigned long long), B.cs), "cudaMemset");
-    for (int it = 0; it < o.max_iters; ++it) BCK(cudaGraphLaunch(B.graph, B.cs), "cudaGraphLaunch");
-    launches += B.launches_per_iter * o.max_iters;
+    BCK(init_state(), "init");
+    launches += nprob;
+    // the form of the convolution launches: forced by the caller, else tuned once per descriptor set
+    int form = (o.flags & SE2OT_FLAG_BATCH_ONE_LAUNCH) ? 2 : (o.flags & SE2OT_FLAG_BATCH_PER_RADIUS) ? 1 : B.form;
+    if (form == 0) {
+        constexpr int WARM = 1, TIMED = 4;
+        for (int f = 0; f < 2; ++f) {
+            cudaGraphExec_t gx = f == 0 ? B.graph : B.graph_one;
+            for (int it = 0; it < WARM; ++it) BCK(cudaGraphLaunch(gx, B.cs), "cudaGraphLaunch");
+            BCK(cudaEventRecord(B.ev_t0, B.cs), "cudaEventRecord");
+            for (int it = 0; it < TIMED; ++it) BCK(cudaGraphLaunch(gx, B.cs), "cudaGraphLaunch");
+            BCK(cudaEventRecord(B.ev_t1, B.cs), "cudaEventRecord");
+            BCK(cudaEventSynchronize(B.ev_t1), "cudaEventSynchronize");
+            float ms = 0.f;
+            BCK(cudaEventElapsedTime(&ms, B.ev_t0, B.ev_t1), "cudaEventElapsedTime");
+            B.tune_ms[f] = ms / TIMED;
+            launches += (f == 0 ? B.launches_per_iter : B.launches_one) * (WARM + TIMED);
+        }
+        B.form = form = B.tune_ms[1] < B.tune_ms[0] ? 2 : 1;
+        BCK(init_state(), "init");   // the timed iterations moved the state: start again
+        launches += nprob;
+    }
+    cudaGraphExec_t gx = form == 2 ? B.graph_one : B.graph;
+    for (int it = 0; it < o.max_iters; ++it) BCK(cudaGraphLaunch(gx, B.cs), "cudaGraphLaunch");
+    launches += (form == 2 ? B.launches_one : B.launches_per_iter) * o.max_iters;
     for (int p = 0; p < nprob; ++p) {
         Prob &q = B.probs[p];
         Lambdas lam;
@@ -462,5 +536,18 @@ extern "C" se2ot_status se2ot_interpolate_batched(int nprob, const se2ot_kernel_
         set_last_error("non-finite iterate in the batch");
         return SE2OT_ENONFINITE;
     }
+    return SE2OT_OK;
+}
+
+extern "C" se2ot_status se2ot_batch_tuning(int *form, double *ms_per_radius, double *ms_one_launch)
+{
+    if (!form || !ms_per_radius || !ms_one_launch) {
+        set_last_error("se2ot_batch_tuning: NULL argument");
+        return SE2OT_EINVAL;
+    }
+    std::lock_guard<std::mutex> lock(g_batch_mu);
+    *form = g_batch.form;
+    *ms_per_radius = g_batch.tune_ms[0];
+    *ms_one_launch = g_batch.tune_ms[1];
     return SE2OT_OK;
 }

@@ -220,9 +220,11 @@ __device__ __forceinline__ void lpt_order(unsigned *order, const unsigned *cost,
 // Single problem (BATCHED false): tile (blockIdx.x, blockIdx.y) of field*orientation blockIdx.z of
 // a0, read from the kernel parameters.  Batch: CTA k works on items[k] = (problem, field * nt +
 // orientation, tile x, tile y), the problem's arguments read from probs.
+// The body of the kernel for radius R: a single problem (tile from the grid indices) or one work
+// item of a batch (item slot blockIdx.x).  conv_tile_kernel runs it for one radius; the batched
+// multi-radius kernel (conv_multi.cu) dispatches each item to the body of its problem's radius.
 template <int R, bool MAXPASS, bool BATCHED>
-__global__ void __launch_bounds__(THREADS, 6) conv_tile_kernel(const ConvArgs a0, const ConvArgs *probs,
-                                                               const int4 *items)
+__device__ __forceinline__ void conv_tile_body(const ConvArgs &a0, const ConvArgs *probs, const int4 *items)
 {
     pdl_launch_dependents();
     pdl_wait();   // everything below may read the previous kernel's results
@@ -660,6 +662,13 @@ __global__ void __launch_bounds__(THREADS, 6) conv_tile_kernel(const ConvArgs a0
             if (tid == 0) *a0.done = 0;
         }
     }
+}
+
+template <int R, bool MAXPASS, bool BATCHED>
+__global__ void __launch_bounds__(THREADS, 6) conv_tile_kernel(const ConvArgs a0, const ConvArgs *probs,
+                                                               const int4 *items)
+{
+    conv_tile_body<R, MAXPASS, BATCHED>(a0, probs, items);
 }
 
 template <int R, bool MAXPASS>

@@ -145,6 +145,10 @@ cudaError_t launch_redo(const ConvArgs &a, int max_blocks, cudaStream_t s);
 // recompute of the list shared by the problems of probs.
 cudaError_t launch_conv_batch(int r, const ConvArgs &shared, const ConvArgs *probs, const int4 *items, int nitems,
                               cudaStream_t s);
+// One launch for a batch of mixed radii: item k (of nitems, heaviest first) runs the body of its
+// problem's radius (conv_multi.cu).  nitems == 0 only sets the kernel's attributes.
+cudaError_t launch_conv_multi(const ConvArgs &shared, const ConvArgs *probs, const int4 *items, int nitems,
+                              cudaStream_t s);
 cudaError_t launch_redo_batch(const ConvArgs &shared, const ConvArgs *probs, int max_blocks, cudaStream_t s);
 int conv_tiles(int nx, int ny);          // spatial tiles of one slice (size of tmax per slice)
 // Tensor-core convolution (conv_tc.cu): supported grids (ntheta <= 16), its tap table size and

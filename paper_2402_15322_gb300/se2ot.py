@@ -29,6 +29,8 @@ SE2OT_BOUNDARY_ZERO = 0
 SE2OT_BOUNDARY_PERIODIC = 1
 SE2OT_DIST_RHO_B, SE2OT_DIST_RHO_C = 0, 1
 SE2OT_FLAG_TIME_CONV = 1
+SE2OT_FLAG_BATCH_ONE_LAUNCH = 2
+SE2OT_FLAG_BATCH_PER_RADIUS = 4
 
 
 class se2ot_kernel_desc(ctypes.Structure):
@@ -116,12 +118,14 @@ def lib():
     L.se2ot_serve_wait.argtypes = [vp, ctypes.c_uint64, vp, ctypes.POINTER(se2ot_stats), i]
     L.se2ot_serve_destroy.argtypes = [vp]
     L.se2ot_sfu_ex2_rate.argtypes = [ctypes.POINTER(d), vp]
+    L.se2ot_batch_tuning.argtypes = [ctypes.POINTER(i), ctypes.POINTER(d), ctypes.POINTER(d)]
     L.se2ot_last_error.restype = ctypes.c_char_p
     L.se2ot_version.restype = ctypes.c_char_p
     for name in ("se2ot_kernel_build", "se2ot_kernel_destroy", "se2ot_kernel_taps", "se2ot_apply",
                  "se2ot_apply_log", "se2ot_barycenter", "se2ot_interpolate", "se2ot_barycenter_noalloc",
                  "se2ot_state_export", "se2ot_interpolate_batched", "se2ot_serve_create", "se2ot_serve_submit",
-                 "se2ot_serve_poll", "se2ot_serve_wait", "se2ot_serve_destroy", "se2ot_sfu_ex2_rate"):
+                 "se2ot_serve_poll", "se2ot_serve_wait", "se2ot_serve_destroy", "se2ot_sfu_ex2_rate",
+                 "se2ot_batch_tuning"):
         getattr(L, name).restype = ctypes.c_int
     _LIB = L
     return L
@@ -437,6 +441,14 @@ def se2ot_interpolate_batched(descs, mu0s, mu1s, ts, opts=None, outs=None, strea
     if raise_on_error:
         _check(status)
     return outs, [s.as_dict() for s in st], status
+
+
+def se2ot_batch_tuning():
+    """(form, ms per iteration per radius, ms per iteration in one launch) of the last tuned batch;
+    form 1 = per radius, 2 = one launch, 0 = none tuned."""
+    f, a, b = ctypes.c_int(), ctypes.c_double(), ctypes.c_double()
+    _check(lib().se2ot_batch_tuning(ctypes.byref(f), ctypes.byref(a), ctypes.byref(b)))
+    return f.value, a.value, b.value
 
 
 SE2OT_ETIMEOUT = 6

@@ -64,6 +64,34 @@ def test_batch_equals_single_solves_and_oracle():
         assert np.abs(got - want).sum() / want.sum() <= 1e-5
 
 
+def test_both_launch_forms_are_bit_identical_and_the_tuner_measures_them():
+    """The batch's convolutions as one launch per radius class or as one launch per line (every
+    radius in it) give the same bits; an unforced first call times both and keeps the faster."""
+    iters = 12
+    descs = [se2ot.make_desc(nx, ny, nt, r, W, eps) for (nx, ny, nt, r, eps, t) in PROBLEMS]
+    ts = [p[5] for p in PROBLEMS]
+    mus = inputs(7)
+    mu0 = [torch.from_numpy(m[0]).cuda() for m in mus]
+    mu1 = [torch.from_numpy(m[1]).cuda() for m in mus]
+    res = {}
+    for flag in (se2ot.SE2OT_FLAG_BATCH_PER_RADIUS, se2ot.SE2OT_FLAG_BATCH_ONE_LAUNCH, 0):
+        outs, stats, _ = se2ot.se2ot_interpolate_batched(descs, mu0, mu1, ts, se2ot.solve_opts(iters, flags=flag))
+        res[flag] = ([o.clone() for o in outs], stats)
+    for k in range(len(descs)):
+        assert torch.equal(res[se2ot.SE2OT_FLAG_BATCH_PER_RADIUS][0][k], res[se2ot.SE2OT_FLAG_BATCH_ONE_LAUNCH][0][k]), k
+        assert torch.equal(res[0][0][k], res[se2ot.SE2OT_FLAG_BATCH_PER_RADIUS][0][k]), k
+    # 6 problems of 4 distinct radii: 4 + 4 convolution launches per iteration against 2
+    per, one = (res[f][1][0]["kernel_launches"] for f in (se2ot.SE2OT_FLAG_BATCH_PER_RADIUS,
+                                                          se2ot.SE2OT_FLAG_BATCH_ONE_LAUNCH))
+    assert per - one == 6 * iters
+    form, ms_per, ms_one = se2ot.se2ot_batch_tuning()
+    assert form in (1, 2) and ms_per > 0 and ms_one > 0
+    assert form == (2 if ms_one < ms_per else 1)
+    _, _, st = se2ot.se2ot_interpolate_batched(descs, mu0, mu1, ts, se2ot.solve_opts(
+        iters, flags=se2ot.SE2OT_FLAG_BATCH_PER_RADIUS | se2ot.SE2OT_FLAG_BATCH_ONE_LAUNCH), raise_on_error=False)
+    assert st == se2ot.SE2OT_EINVAL
+
+
 def test_batch_rejects_what_it_does_not_support():
     d = se2ot.make_desc(32, 32, 8, 3, W, 5e-4, periodic=True)
     mu = torch.full((32, 32, 8), 1.0 / 8192, device="cuda")
