@@ -747,6 +747,12 @@ def main(argv=None):
     if args.config == "serve":
         print(json.dumps(run_serve(args)), flush=True)
         return 0
+    if args.precision == "bf16" and args.config in ("large", "w2", "jko", "batched"):
+        # the tensor-core path covers the barycenter at up to 16 orientations (the large grid has 32)
+        print(json.dumps({"config": args.config, "precision": "bf16",
+                          "unavailable": "the BF16 tensor-core path supports ntheta <= 16 and the barycenter "
+                                         "entry point only; this workload runs on the FP32 path"}), flush=True)
+        return 0
     res = run_gpu(args)
     rank, world, _ = dist_env()
     if rank == 0:
