@@ -87,8 +87,8 @@ __host__ __device__ constexpr int stage_floats(int r)
 
 // Staging buffers: two (the next slice is copied while the current one is summed) where six CTAs
 // with two buffers still fit in an SM's 228 KB of shared memory (1 KB reserved per CTA), one
-// otherwise: six resident CTAs (the register limit) hide more latency than the prefetch does
-// (at r = 15 two buffers would leave 4 CTAs per SM; measured 11% slower).
+// otherwise: six or more resident CTAs hide more latency than the prefetch does (at r = 15 two
+// buffers would leave 4 CTAs per SM; measured 11% slower).
 __host__ __device__ constexpr size_t other_floats(int r) { return (size_t)(TY + 2 * r) + 8 + 4 * MAX_NT + 8; }
 __host__ __device__ constexpr int stage_buffers(int r)
 {
@@ -665,7 +665,9 @@ __device__ __forceinline__ void conv_tile_body(const ConvArgs &a0, const ConvArg
 }
 
 template <int R, bool MAXPASS, bool BATCHED>
-__global__ void __launch_bounds__(THREADS, 6) conv_tile_kernel(const ConvArgs a0, const ConvArgs *probs,
+// 72 registers (7 CTAs' worth): measured 1% faster per solve than 80 (6 CTAs); shared memory keeps
+// r <= 10 at 6 CTAs per SM, larger radii (single-buffered) reach 7
+__global__ void __launch_bounds__(THREADS, 7) conv_tile_kernel(const ConvArgs a0, const ConvArgs *probs,
                                                                const int4 *items)
 {
     conv_tile_body<R, MAXPASS, BATCHED>(a0, probs, items);
