@@ -164,11 +164,12 @@ cudaError_t launch_fill(float *p, long n, float v, cudaStream_t s);
 // 7.7% to it; with the sort on every 8th launch they would gain 0.5%.
 inline bool conv_order_pays(long tiles) { return tiles <= 16L * 6 * 152; }
 // Whether launch number `launch` (0, 1, ... with one set of arguments) rebuilds the launch order:
-// every 8th, from the first.  The sort runs in the last CTA, on the launch's critical path (about
+// every 16th, from the first.  The sort runs in the last CTA, on the launch's critical path (about
 // 10 us of a 100 us launch at 2048 tiles), while the tile costs of consecutive Sinkhorn iterations
-// differ little (128^2 x 16 barycenter: 103.9 ms per solve sorting every launch, 96.4 every 8th,
-// 96.1 every 16th, 100.2 every 32nd).
-inline int order_sort_launch(long launch) { return launch % 8 == 0; }
+// differ little (128^2 x 16 barycenter, first kernel: 103.9 ms per solve sorting every launch,
+// 96.4 every 8th, 96.1 every 16th, 100.2 every 32nd; current kernel, same box: 83.3 every 4th,
+// 81.9 every 8th, 81.4 every 16th and every 32nd).
+inline int order_sort_launch(long launch) { return launch % 16 == 0; }
 // Whether the kernels between two convolutions of `ctas` CTAs release their successor before
 // waiting for their predecessor (programmatic dependent launch).  Released early, the next
 // convolution's CTAs are placed while the current one still runs, onto whichever SMs have free
