@@ -636,6 +636,7 @@ def run_gpu(args):
             terms_per_launch = evaluated / max(1, 2 * iters * args.steps)
             eval_terms_per_s = terms_per_launch / avg_conv_s
             peak_tc = peaks["bf16_tflops_sustained"]
+            traffic = conv_traffic() if args.config == "barycenter" and args.precision == "fp32" else None
             result["roofline"] = {
                 "bound": "tensor",
                 "kernel": ("one convolution on the tensor-core path: tc_conv_kernel (BF16 tcgen05) plus the "
@@ -643,7 +644,11 @@ def run_gpu(args):
                           "conv_tile_kernel<%d, false>: log-domain group convolution" % r,
                 "achieved": achieved_tflops, "peak": peak_tc, "unit": "TFLOP/s",
                 "frac": achieved_tflops / peak_tc,
-                "traffic": conv_traffic() if args.config == "barycenter" else None,
+                "traffic": traffic,
+                # DRAM bytes of one launch (the committed ncu count) over the measured launch time,
+                # against the measured copy bandwidth
+                "dram_gbs": traffic / avg_conv_s / 1e9 if traffic else None,
+                "dram_frac_of_hbm": traffic / avg_conv_s / 1e9 / peaks["hbm_gbs"] if traffic else None,
                 "avg_launch_ms": avg_conv_s * 1e3, "launches": int(conv_launches),
                 "flop_per_launch": flop_per_launch,
                 "peak_basis": "dense BF16 tensor peak, sustained, %s; achieved = the algorithmic flops of "
