@@ -205,7 +205,7 @@ cudaError_t launch_update(float2 *lv, const float2 *ld, float2 *L, const Lambdas
 constexpr int CHECK_BLOCKS = 64, CHECK_Q = 4;
 constexpr size_t check_partial_doubles(int n) { return (size_t)CHECK_Q * n * CHECK_BLOCKS; }
 cudaError_t launch_input_check(const float *mu, int n, long V, double *partial, double *out, cudaStream_t s);
-// The verdict on launch_input_check's out (host copy): OK, or EINVAL with a message when an entry
+// The result of launch_input_check's out (host copy): OK, or EINVAL with a message when an entry
 // is negative or not finite, a measure has zero mass (strictly positive entries required when
 // positive_entries is set), or two masses differ by more than 1e-6 relative to the largest.
 se2ot_status check_inputs(const double *out, int n, bool positive_entries, long V, const char *what);

@@ -314,7 +314,7 @@ se2ot_status se2ot_serve_submit(se2ot_server sv, const se2ot_kernel_desc *desc, 
         return SE2OT_ECUDA;
     }
     {
-        // the inputs are measures of equal mass (Appendix A); the same verdict as the solves' device
+        // the inputs are measures of equal mass (Appendix A); the same result as the solves' device
         // check, on the request's host copy
         std::vector<double> q((size_t)CHECK_Q * n, 0.0);
         const size_t V = (size_t)desc->nx * desc->ny * desc->ntheta;

@@ -255,7 +255,7 @@ se2ot_status run_conv(se2ot_kernel k, const ConvArgs &a0, cudaStream_t s, long l
 }
 
 // Enqueue the input check of n measures (device memory, [n][V]) on the handle's buffers, wait for it
-// and return check_inputs' verdict.
+// and return check_inputs' result.
 se2ot_status run_input_check(se2ot_kernel k, const float *mu_dev, int n, bool positive_entries, cudaStream_t s,
                              const char *what)
 {

@@ -65,7 +65,8 @@ def test_500_iterations_bf16_tensor_cores_against_stored_oracle(golden, refine, 
     """The same solve with the convolutions on the tensor cores (SE2OT_BF16TC): the BF16 target is
     1e-3 relative L1 before refinement; with the last 20 of the 500 iterations on the FP32 path the
     FP32 target 1e-5 holds again.  At this eps the per-tile rescaling represents the tiles of the
-    early iterations only (the census in the design doc); the rest run on the FP32 path."""
+    early iterations fully (late in the solve the potentials' curvature defeats it on most of the
+    mass, see tests/test_tc_census.py); the rest run on the FP32 path."""
     nx, ny, nt = golden["grid"]
     n = golden["measures"]
     mu = synth.coupled_measures(n, nx, ny, nt, config_seed=2, max_shift=golden["radius"] // 2, nbumps=5)
